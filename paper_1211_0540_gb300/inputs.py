@@ -1,0 +1,116 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module holds only input recipes (where the distribution f is sampled and
+with which random parameters). It contains none of the method's arithmetic and
+imports neither the CUDA library nor the oracle, so both sides can be fed the
+same arrays. Random numbers come from numpy's PCG64 generator with an explicit
+seed; nothing here depends on the platform.
+
+Velocity nodes follow the paper's mesh (Sec. 3.1, Eq. meshpoints):
+v_j = dv (j - N/2), dv = 2L/N, j in [0, N)^3, cell layout k3 fastest.
+"""
+import math
+
+import numpy as np
+
+__all__ = [
+    "velocity_nodes", "maxwellian", "bi_maxwellian", "bkw", "random_bi_maxwellian_params",
+    "homogeneous_cells", "wall_heating_initial", "precision_sweep_cells", "uneven_batch",
+    "training_states",
+]
+
+
+def velocity_nodes(N, L):
+    """(v1, v2, v3) arrays of shape (N, N, N) at the grid nodes."""
+    dv = 2.0 * L / N
+    g = dv * (np.arange(N) - N // 2)
+    return np.meshgrid(g, g, g, indexing="ij")
+
+
+def maxwellian(N, L, rho=1.0, u=(0.0, 0.0, 0.0), T=1.0):
+    v1, v2, v3 = velocity_nodes(N, L)
+    r2 = (v1 - u[0]) ** 2 + (v2 - u[1]) ** 2 + (v3 - u[2]) ** 2
+    return (rho * (2.0 * math.pi * T) ** -1.5 * np.exp(-r2 / (2.0 * T))).reshape(-1)
+
+
+def bi_maxwellian(N, L, rho1, u1, T1, rho2, u2, T2):
+    return maxwellian(N, L, rho1, u1, T1) + maxwellian(N, L, rho2, u2, T2)
+
+
+def bkw(N, L, K):
+    """Bobylev-Krook-Wu profile at parameter K (density 1, zero mean):
+    (2 pi K)^{-3/2} exp(-|v|^2/(2K)) [(5K-3)/(2K) + (1-K)|v|^2/(2K^2)]."""
+    v1, v2, v3 = velocity_nodes(N, L)
+    r2 = v1 ** 2 + v2 ** 2 + v3 ** 2
+    g = (2.0 * math.pi * K) ** -1.5 * np.exp(-r2 / (2.0 * K))
+    return (g * ((5.0 * K - 3.0) / (2.0 * K) + (1.0 - K) * r2 / (2.0 * K * K))).reshape(-1)
+
+
+def random_bi_maxwellian_params(rng, mean_mode="x"):
+    """rho1 ~ U(0.3, 0.7), rho2 = 1 - rho1, temperatures ~ U(0.5, 2).
+    mean_mode "x": means +-U e_x with U ~ U(0.5, 1.5);
+    mean_mode "cube": two independent means ~ U(-1.5, 1.5)^3."""
+    rho1 = rng.uniform(0.3, 0.7)
+    T1, T2 = rng.uniform(0.5, 2.0, size=2)
+    if mean_mode == "x":
+        U = rng.uniform(0.5, 1.5)
+        u1, u2 = (U, 0.0, 0.0), (-U, 0.0, 0.0)
+    else:
+        u1 = tuple(rng.uniform(-1.5, 1.5, size=3))
+        u2 = tuple(rng.uniform(-1.5, 1.5, size=3))
+    return rho1, u1, T1, 1.0 - rho1, u2, T2
+
+
+def homogeneous_cells(N, L, ncells, seed, mean_mode="x"):
+    """ncells seeded bi-Maxwellians, shape (ncells, N^3), float64."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((ncells, N ** 3))
+    for c in range(ncells):
+        out[c] = bi_maxwellian(N, L, *random_bi_maxwellian_params(rng, mean_mode))
+    return out
+
+
+def wall_heating_initial(N, L, nx):
+    """Gas at rest, rho = 1, T = 1 in every cell (sudden wall heating, Sec. 5)."""
+    m = maxwellian(N, L, 1.0, (0.0, 0.0, 0.0), 1.0)
+    return np.tile(m, (nx, 1))
+
+
+def precision_sweep_cells(N, L, ncells, seed):
+    """Bi-Maxwellians with means ~ U(-1.5, 1.5)^3 and temperatures ~ U(0.5, 2)."""
+    return homogeneous_cells(N, L, ncells, seed, mean_mode="cube")
+
+
+def uneven_batch(ninst, seed, L=6.0, Ns=(12, 16, 24, 32), pN=(0.4, 0.3, 0.2, 0.1),
+                 lams=(0.0, 1.0), plam=(0.5, 0.5)):
+    """Uneven batch of space-homogeneous instances: per instance N and lambda
+    drawn with the given weights; lambda = 0 instances are BKW profiles
+    (K ~ U(0.6, 0.95)) with probability 1/2, otherwise bi-Maxwellians.
+    Returns a list of (N, lam, f) with f float64 of length N^3."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(ninst):
+        N = int(rng.choice(Ns, p=pN))
+        lam = float(rng.choice(lams, p=plam))
+        if lam == 0.0 and rng.uniform() < 0.5:
+            f = bkw(N, L, rng.uniform(0.6, 0.95))
+        else:
+            f = bi_maxwellian(N, L, *random_bi_maxwellian_params(rng, "x"))
+        out.append((N, lam, f))
+    return out
+
+
+def training_states(N, L, nstates, seed):
+    """Seeded bi- and tri-Maxwellians (means ~ U(-1.5, 1.5)^3, T ~ U(0.5, 2),
+    weights from a Dirichlet(1) draw), normalised to density 1."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((nstates, N ** 3))
+    for s in range(nstates):
+        nb = 2 if rng.uniform() < 0.5 else 3
+        w = rng.dirichlet(np.ones(nb))
+        f = np.zeros(N ** 3)
+        for b in range(nb):
+            u = tuple(rng.uniform(-1.5, 1.5, size=3))
+            f += maxwellian(N, L, w[b], u, rng.uniform(0.5, 2.0))
+        out[s] = f
+    return out

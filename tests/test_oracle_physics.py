@@ -1,0 +1,106 @@
+"""Physics pins for the oracle's collision operator and time stepping.
+
+- Q(Maxwellian) = 0 for the continuous operator; the discrete one must tend to 0
+  as N grows (Sec. 3.2: the trapezoid rule is spectrally accurate).
+- Maxwell molecules (lambda = 0, b = 1/(4 pi)) have the Bobylev-Krook-Wu exact
+  solution f(K(t)), K = 1 - exp(-t/6); so Q(f_BKW) = (df/dK) (1 - K)/6. The
+  derivative is written out analytically here.
+- Conservation after the projection of Sec. 3.3, per stage and over RK2 steps.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_0540_gb300 import inputs
+
+L = 6.0
+
+
+def dbkw_dK(N, K):
+    v1, v2, v3 = inputs.velocity_nodes(N, L)
+    r2 = (v1 ** 2 + v2 ** 2 + v3 ** 2).ravel()
+    g = (2 * math.pi * K) ** -1.5 * np.exp(-r2 / (2 * K))
+    h = (5 * K - 3) / (2 * K) + (1 - K) * r2 / (2 * K * K)
+    dg = g * (-1.5 / K + r2 / (2 * K * K))
+    dh = 1.5 / K ** 2 - r2 / K ** 3 + r2 / (2 * K * K)
+    return dg * h + g * dh
+
+
+def test_maxwellian_is_an_equilibrium_in_the_limit():
+    errs = []
+    for N in (8, 12, 16):
+        M = inputs.maxwellian(N, L, 1.0, (0.3, 0.0, 0.0), 1.0)
+        errs.append(np.linalg.norm(oracle.collide(N, L, 1.0, M)) / np.linalg.norm(M))
+    # measured 0.25, 1.7e-2, 3.7e-4
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-3
+
+
+def test_bkw_exact_solution_for_maxwell_molecules():
+    K = 0.7
+    errs = []
+    for N in (8, 12, 16):
+        f = inputs.bkw(N, L, K)
+        ref = dbkw_dK(N, K) * (1 - K) / 6.0
+        errs.append(np.linalg.norm(oracle.collide(N, L, 0.0, f) - ref) / np.linalg.norm(ref))
+    # measured 0.56, 3.8e-2, 6.1e-3 (7e-5 at N = 24): a wrong rate or constant plateaus
+    assert errs[0] > 5 * errs[1] > 25 * errs[2]
+    assert errs[2] < 1e-2
+
+
+def abs_moment_scale(N, Q):
+    """sum_j |C_ij Q_j| per cell and moment: the scale of each conservation sum."""
+    v1, v2, v3 = inputs.velocity_nodes(N, L)
+    dv3 = (2 * L / N) ** 3
+    C = dv3 * np.stack([np.ones(N ** 3), v1.ravel(), v2.ravel(), v3.ravel(),
+                        (v1 ** 2 + v2 ** 2 + v3 ** 2).ravel()])
+    return np.abs(Q.reshape(-1, N ** 3)) @ np.abs(C).T
+
+
+def test_projected_operator_conserves_per_cell():
+    N = 12
+    f = inputs.homogeneous_cells(N, L, 3, seed=21)
+    Q = oracle.collide(N, L, 1.0, f)
+    m = oracle.moments(N, L, Q)
+    assert np.all(np.abs(m) <= 1e-12 * abs_moment_scale(N, Q))
+
+
+@pytest.mark.slow
+def test_rk2_conserves_and_relaxes_bimaxwellian():
+    """20 Heun steps dt = 0.01 (the 1-cell workload at reduced N): mass, momentum
+    and energy constant to 1e-12 relative; the x-temperature anisotropy decays."""
+    N = 12
+    f = inputs.homogeneous_cells(N, L, 1, seed=1)
+    m0 = oracle.moments(N, L, f)[0]
+    v1, v2, v3 = inputs.velocity_nodes(N, L)
+    dv3 = (2 * L / N) ** 3
+
+    def aniso(g):
+        g = g.reshape(-1)
+        rho = g.sum() * dv3
+        u1 = (g * v1.ravel()).sum() * dv3 / rho
+        t1 = (g * (v1.ravel() - u1) ** 2).sum() * dv3 / rho
+        t2 = (g * v2.ravel() ** 2).sum() * dv3 / rho
+        return t1 - t2
+
+    a0 = aniso(f)
+    for _ in range(20):
+        f = oracle.rk2_homogeneous(N, L, 1.0, f, 0.01)
+    m1 = oracle.moments(N, L, f)[0]
+    scale = max(abs(m0[0]), abs(m0[4]))
+    assert np.all(np.abs(m1 - m0) <= 1e-12 * scale)
+    assert abs(aniso(f)) < abs(a0)
+
+
+def test_heun_step_matches_explicit_stages():
+    """rk2_homogeneous == f + dt/(2 eps) (Q(f) + Q(f + dt/eps Q(f)))."""
+    N = 8
+    f = inputs.homogeneous_cells(N, L, 2, seed=3)
+    dt, eps = 0.02, 0.5
+    q1 = oracle.collide(N, L, 1.0, f)
+    q2 = oracle.collide(N, L, 1.0, f + dt / eps * q1)
+    ref = f + 0.5 * dt / eps * (q1 + q2)
+    got = oracle.rk2_homogeneous(N, L, 1.0, f, dt, eps)
+    assert np.abs(got - ref).max() <= 1e-15 * np.abs(f).max() * 10
