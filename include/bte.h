@@ -1,0 +1,163 @@
+/*
+ * bte.h — C ABI of libbte, the GB300 (sm_103a) implementation of the
+ * conservative spectral collision operator of Haack & Gamba,
+ * "High Performance Computing with a Conservative Spectral Boltzmann Solver"
+ * (arXiv:1211.0540).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Velocity grid (Sec. 3.1, Eq. meshpoints): N points per dimension on [-L, L)^3,
+ *   v_j = dv (j - N/2), dv = 2L/N; Fourier grid zeta_k = dz (k - N/2), dz = pi/L.
+ *   N must be even; this build supports N in {8, 12, 16, 24, 32}.
+ * - A "cell" is one distribution f on that grid: M = N^3 doubles, index
+ *   (j1*N + j2)*N + j3 (j3 fastest). Arrays of cells are cell-major.
+ * - f and Q pointers are DEVICE pointers (cudaMalloc / torch tensors) owned by
+ *   the caller, unless a call says otherwise. The context owns everything it
+ *   allocates (weight tables, scratch) and frees it in bte_destroy.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls enqueue work on the stream and return without synchronising, unless
+ *   stated. Errors detected inside kernels (non-finite input, a bounded wait
+ *   that ran out) are recorded in a device status word, read by
+ *   bte_sync_status.
+ * - Every call returns a bte_status; on failure bte_last_error() describes it.
+ *   No call traps the GPU on bad input: shapes are checked on the host.
+ * - A context is not thread-safe; use one context per host thread.
+ *
+ * Instances (uneven batches)
+ * --------------------------
+ * `inst == NULL` means `ninst` uniform cells of table 0 stored back to back
+ * (cell c at f + c*M). Otherwise inst[i] names the weight table of instance i
+ * (its grid, hence its M) and the element offset of its data inside f and Q.
+ */
+#ifndef BTE_H
+#define BTE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bte_ctx bte_ctx;
+
+typedef enum {
+    BTE_OK = 0,
+    BTE_EINVAL = -1,      /* bad argument, shape or state of the arguments      */
+    BTE_ENOMEM = -2,      /* device or host allocation failed                  */
+    BTE_ECUDA = -3,       /* a CUDA runtime call failed                         */
+    BTE_ETIMEOUT = -4,    /* a bounded in-kernel wait ran out (device status)   */
+    BTE_ENONFINITE = -5,  /* NaN/Inf found in an input (device status)          */
+    BTE_ESTATE = -6       /* call made in the wrong state (e.g. no tables yet)  */
+} bte_status;
+
+typedef enum {
+    BTE_FP64_PLAIN = 0,   /* plain FP64 operator: direct sums, FP64 weights     */
+    BTE_FP32 = 1,         /* FP32 compensated convolution, FP64 projection      */
+    BTE_LEARNED = 2       /* MLP surrogate + FP64 projection + exact fallback   */
+} bte_mode;
+
+typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1 } bte_bc;
+
+/* bte_collide_ex flags */
+#define BTE_FLAG_RAW 1u        /* return Qt (skip the conservation projection)   */
+#define BTE_FLAG_LOSS_ONLY 2u  /* FP64_PLAIN only: loss term of Ghat alone, raw   */
+
+/* Velocity grid and collision kernel of one weight table: B = |u|^lambda / (4 pi)
+ * (isotropic, Sec. 2.2). lambda = 0: Maxwell molecules, 1: hard spheres. */
+typedef struct {
+    int N;
+    double L;
+    double lambda;
+} bte_grid;
+
+typedef struct {
+    int32_t table;   /* id returned by bte_init_weights                        */
+    int32_t pad_;
+    int64_t offset;  /* element offset of the instance inside f and Q           */
+} bte_instance;
+
+/* 1-D slab [x0, x1] of nx uniform cells with a wall at each end (Sec. 2.1,
+ * Eq. BC; Sec. 3.4). bc_*: BTE_BC_DIFFUSE (wall temperature Tw_*, zero wall
+ * velocity) or BTE_BC_SPECULAR. */
+typedef struct {
+    int nx;
+    double x0, x1;
+    int bc_left, bc_right;
+    double Tw_left, Tw_right;
+} bte_transport;
+
+/* Create a context on CUDA device `device`. *ctx receives the handle.
+ * Errors: BTE_EINVAL (ctx NULL, bad device), BTE_ECUDA. */
+bte_status bte_create(bte_ctx **ctx, int device);
+
+/* Release everything the context owns. Safe on NULL. Synchronises the device. */
+void bte_destroy(bte_ctx *ctx);
+
+/* Message for the last failing call of this context ("" if none). The string
+ * belongs to the context. */
+const char *bte_last_error(const bte_ctx *ctx);
+
+/* Tabulate the convolution weights Ghat(xi_m, zeta_k) of Sec. 2.2,
+ * Eq. GHat_calc (beta = 1, isotropic b, radial integral cut off at r0 = L,
+ * Sec. 3.1) in FP64 on the host for each grid, and store them on the device:
+ * the FP32 pair-symmetrised table of the fast path and the moment/projection
+ * constants of Sec. 3.3. The FP64 table of the plain operator is built on the
+ * first BTE_FP64_PLAIN call that needs it. table_ids[i] (host array of
+ * ngrids ints) receives the id of grid i. Synchronous.
+ * Errors: BTE_EINVAL (N unsupported, L <= 0, lambda not in [0, 1] with a closed
+ * form or quadrature), BTE_ENOMEM. */
+bte_status bte_init_weights(bte_ctx *ctx, const bte_grid *grids, int ngrids, int *table_ids);
+
+/* Collision operator Q = P_N Qt(f) of Sec. 3.2-3.3 for a batch of cells:
+ * forward transform of f, weighted convolution
+ * Qhat(zeta_k) = dz^3 sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m)
+ * with zero extension, inverse transform (real part), conservation projection.
+ * f, Q: device FP64 arrays (see Instances); inst: HOST array or NULL.
+ * f and Q must not overlap. mode: bte_mode. Asynchronous on `stream`.
+ * Errors: BTE_EINVAL, BTE_ESTATE (no tables / no trained surrogate), BTE_ECUDA,
+ * BTE_ENOMEM (scratch). */
+bte_status bte_collide(bte_ctx *ctx, const double *f, double *Q, const bte_instance *inst,
+                       int64_t ninst, int mode, void *stream);
+
+/* bte_collide with flags (BTE_FLAG_RAW returns the unprojected Qt). */
+bte_status bte_collide_ex(bte_ctx *ctx, const double *f, double *Q, const bte_instance *inst,
+                          int64_t ninst, int mode, unsigned flags, void *stream);
+
+/* Conservation projection of Sec. 3.3 in place on device array Q:
+ * Q <- Q - C^T (C C^T)^{-1} C Q, C = dv^3 (1, v1, v2, v3, |v|^2) per grid
+ * point, FP64. (The paper prints "+ C"; the Lagrange solution of the stated
+ * minimisation has "- C^T".) Asynchronous. Errors: BTE_EINVAL, BTE_ESTATE. */
+bte_status bte_project(bte_ctx *ctx, double *Q, const bte_instance *inst, int64_t ninst,
+                       void *stream);
+
+/* One time step on device array f, in place.
+ * tr == NULL: space-homogeneous Heun (RK2) step of df/dt = Q(f,f)/eps with the
+ *   projection at each stage (Sec. 3.1): Q1 = P Qt(f); f* = f + dt/eps Q1;
+ *   Q2 = P Qt(f*); f <- f + dt/(2 eps) (Q1 + Q2).
+ * tr != NULL: Strang step T(dt/2) C(dt) T(dt/2) (Sec. 3.1) of the 1-D slab,
+ *   T = Heun step of the second-order upwind / minmod finite-volume transport
+ *   (Sec. 3.4, Eq. upwind) with diffuse (Eq. BC, sigma_w balancing the
+ *   discrete outgoing flux) or specular walls, C = the homogeneous step above
+ *   over all tr->nx cells (inst must be NULL and ninst == tr->nx).
+ * The homogeneous and Strang steps are replayed from a CUDA graph captured on
+ * the first call with a given shape. Asynchronous. Errors as bte_collide. */
+bte_status bte_step(bte_ctx *ctx, double *f, const bte_instance *inst, int64_t ninst, double dt,
+                    double eps, const bte_transport *tr, int mode, void *stream);
+
+/* Synchronise `stream`, read and clear the device status word.
+ * Returns BTE_OK, BTE_ETIMEOUT, BTE_ENONFINITE or BTE_ECUDA. */
+bte_status bte_sync_status(bte_ctx *ctx, void *stream);
+
+/* Moments (C f)_i, i = mass, momentum 1..3, energy, per cell: out is a DEVICE
+ * array of 5*ninst doubles. FP64. Asynchronous. */
+bte_status bte_moments(bte_ctx *ctx, const double *f, double *out, const bte_instance *inst,
+                       int64_t ninst, void *stream);
+
+/* Library build identification (static string). */
+const char *bte_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTE_H */

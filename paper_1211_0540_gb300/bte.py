@@ -1,0 +1,195 @@
+"""Thin ctypes binding of libbte (include/bte.h).
+
+Argument marshalling only: every step of the collision operator, projection
+and time stepping runs in libbte's CUDA kernels. Tensors are torch CUDA
+tensors (float64, contiguous); pointers and the current CUDA stream are handed
+to the C ABI unchanged. There is no CPU fallback: if libbte.so is missing or no
+GPU is visible, the calls raise.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+FP64_PLAIN = 0
+FP32 = 1
+LEARNED = 2
+BC_DIFFUSE = 0
+BC_SPECULAR = 1
+FLAG_RAW = 1
+
+STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: "BTE_ETIMEOUT",
+          -5: "BTE_ENONFINITE", -6: "BTE_ESTATE"}
+
+# Every symbol include/bte.h declares (checked by the ABI tests).
+EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
+           "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
+           "bte_version"]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("lambda_", ctypes.c_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_int32), ("pad_", ctypes.c_int32), ("offset", ctypes.c_int64)]
+
+
+class Transport(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int),
+                ("Tw_left", ctypes.c_double), ("Tw_right", ctypes.c_double)]
+
+
+class BteError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, str(code)), msg))
+        self.code = code
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libbte.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError("libbte.so is not built (%s): run __graft_entry__.build()" % path)
+    L = ctypes.CDLL(path)
+    c_int, c_i64, c_u, vp, c_d = ctypes.c_int, ctypes.c_int64, ctypes.c_uint, ctypes.c_void_p, ctypes.c_double
+    sig = {
+        "bte_create": (c_int, [ctypes.POINTER(vp), c_int]),
+        "bte_destroy": (None, [vp]),
+        "bte_last_error": (ctypes.c_char_p, [vp]),
+        "bte_init_weights": (c_int, [vp, ctypes.POINTER(Grid), c_int, ctypes.POINTER(c_int)]),
+        "bte_collide": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, c_int, vp]),
+        "bte_collide_ex": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, c_int, c_u, vp]),
+        "bte_project": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
+        "bte_step": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_d, c_d,
+                             ctypes.POINTER(Transport), c_int, vp]),
+        "bte_sync_status": (c_int, [vp, vp]),
+        "bte_moments": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
+        "bte_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check_f64(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+
+
+class Context:
+    """One libbte context on one CUDA device (owns weight tables and scratch)."""
+
+    def __init__(self, device=0):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        rc = self._lib.bte_create(ctypes.byref(h), int(device))
+        if rc != 0:
+            raise BteError(rc, "bte_create(device=%d) failed" % device)
+        self._h = h
+        self.device = int(device)
+        self.grids = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.bte_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _rc(self, rc, what):
+        if rc != 0:
+            msg = self._lib.bte_last_error(self._h)
+            raise BteError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def init_weights(self, grids):
+        """grids: list of (N, L, lambda). Returns the table ids."""
+        arr = (Grid * len(grids))(*[Grid(int(N), float(L), float(lam)) for (N, L, lam) in grids])
+        ids = (ctypes.c_int * len(grids))()
+        self._rc(self._lib.bte_init_weights(self._h, arr, len(grids), ids), "bte_init_weights")
+        self.grids += list(grids)
+        return list(ids)
+
+    def _inst(self, inst, f):
+        if inst is None:
+            N = self.grids[0][0]
+            M = N ** 3
+            if f.numel() % M:
+                raise ValueError("f size is not a multiple of N^3 of table 0")
+            return None, f.numel() // M
+        arr = (Instance * len(inst))(*[Instance(int(t), 0, int(o)) for (t, o) in inst])
+        return arr, len(inst)
+
+    def collide(self, f, Q=None, inst=None, mode=FP32, raw=False, stream=None):
+        _check_f64(f, "f")
+        if Q is None:
+            import torch
+            Q = torch.empty_like(f)
+        _check_f64(Q, "Q")
+        arr, n = self._inst(inst, f)
+        self._rc(self._lib.bte_collide_ex(self._h, _ptr(f), _ptr(Q), arr, n, int(mode),
+                                          FLAG_RAW if raw else 0, _stream(stream)), "bte_collide")
+        return Q
+
+    def project(self, Q, inst=None, stream=None):
+        _check_f64(Q, "Q")
+        arr, n = self._inst(inst, Q)
+        self._rc(self._lib.bte_project(self._h, _ptr(Q), arr, n, _stream(stream)), "bte_project")
+        return Q
+
+    def moments(self, f, inst=None, stream=None):
+        import torch
+        _check_f64(f, "f")
+        arr, n = self._inst(inst, f)
+        out = torch.zeros((n, 5), dtype=torch.float64, device=f.device)
+        self._rc(self._lib.bte_moments(self._h, _ptr(f), _ptr(out), arr, n, _stream(stream)),
+                 "bte_moments")
+        return out
+
+    def step(self, f, dt, eps=1.0, transport=None, inst=None, mode=FP32, stream=None):
+        """One RK2 (homogeneous) or Strang (transport dict given) step, in place."""
+        _check_f64(f, "f")
+        arr, n = self._inst(inst, f)
+        tr = None
+        if transport is not None:
+            t = transport
+            tr = Transport(int(t.get("nx", n)), float(t.get("x0", 0.0)), float(t.get("x1", 1.0)),
+                           int(t.get("bc_left", BC_DIFFUSE)), int(t.get("bc_right", BC_SPECULAR)),
+                           float(t.get("Tw_left", 1.0)), float(t.get("Tw_right", 1.0)))
+            tr = ctypes.byref(tr)
+        self._rc(self._lib.bte_step(self._h, _ptr(f), arr, n, float(dt), float(eps), tr, int(mode),
+                                    _stream(stream)), "bte_step")
+        return f
+
+    def sync_status(self, stream=None):
+        rc = self._lib.bte_sync_status(self._h, _stream(stream))
+        self._rc(rc, "device status")

@@ -1,0 +1,530 @@
+// C ABI of libbte (include/bte.h): contexts, weight tables, batches and the
+// orchestration of the collision operator, projection and time steps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "kernels.h"
+
+namespace bte {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// A batch: the instance layout of one (inst, ninst) argument, mapped onto
+// slots. Instances are grouped by weight table into segments; a segment's
+// slots are padded to a multiple of 32 (one warp lane per cell).
+struct Segment {
+    int table;
+    int s0, nslots, nvalid;
+    int64_t eoff;  // complex-element offset of the segment in the scratch buffers
+};
+struct Batch {
+    std::vector<Segment> segs;
+    int nslots = 0;
+    int64_t n_celem = 0;  // sum over slots of M
+    int64_t extent = 0;   // max(offset + M) over instances
+    int64_t *d_slot_off = nullptr;
+    int64_t *d_slot_out = nullptr;
+    ConvItem *d_items = nullptr;
+    int nitems = 0;
+    unsigned kinds_mask = 0;
+    bool uniform = false;
+    int uniform_table = 0;
+};
+
+bool GraphKey::operator<(const GraphKey &o) const {
+    return std::tie(ninst, table, mode, transport, dt, eps, f, stream) <
+           std::tie(o.ninst, o.table, o.mode, o.transport, o.dt, o.eps, o.f, o.stream);
+}
+
+}  // namespace bte
+
+using namespace bte;
+
+namespace {
+
+enum ScratchId { SC_T1 = 0, SC_T2, SC_F, SC_QH, SC_FS, SC_Q1, SC_Q2, SC_MISC };
+
+bte_status fail(bte_ctx *c, bte_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+bte_status cuda_fail(bte_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, BTE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bte_status ensure_scratch(bte_ctx *c, int id, size_t bytes) {
+    if (c->scratch_bytes[id] >= bytes) return BTE_OK;
+    cudaFree(c->scratch[id]);
+    c->scratch[id] = nullptr;
+    c->scratch_bytes[id] = 0;
+    cudaError_t e = cudaMalloc(&c->scratch[id], bytes);
+    if (e != cudaSuccess) return fail(c, BTE_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    c->scratch_bytes[id] = bytes;
+    return BTE_OK;
+}
+
+uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+int64_t cell_M(const Table *t) { return (int64_t)t->N * t->N * t->N; }
+
+// Build (or fetch) the batch for an instance layout.
+bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch **out) {
+    if (c->tables.empty()) return fail(c, BTE_ESTATE, "no weight tables: call bte_init_weights first");
+    if (ninst <= 0) return fail(c, BTE_EINVAL, "ninst must be > 0");
+    if (ninst > (1 << 24)) return fail(c, BTE_EINVAL, "ninst too large");
+    std::string key;
+    if (!inst) {
+        key = "u:" + std::to_string(ninst);
+    } else {
+        key = "i:" + std::to_string(ninst) + ":" +
+              std::to_string(fnv1a(inst, sizeof(bte_instance) * (size_t)ninst));
+    }
+    auto it = c->batches.find(key);
+    if (it != c->batches.end()) {
+        *out = it->second;
+        return BTE_OK;
+    }
+    // instance -> (table, offset)
+    std::vector<int> tab(ninst);
+    std::vector<int64_t> off(ninst);
+    const int64_t M0 = cell_M(c->tables[0]);
+    for (int64_t i = 0; i < ninst; ++i) {
+        if (inst) {
+            if (inst[i].table < 0 || inst[i].table >= (int)c->tables.size())
+                return fail(c, BTE_EINVAL, "instance " + std::to_string(i) + ": unknown table id");
+            if (inst[i].offset < 0) return fail(c, BTE_EINVAL, "instance " + std::to_string(i) + ": negative offset");
+            tab[i] = inst[i].table;
+            off[i] = inst[i].offset;
+        } else {
+            tab[i] = 0;
+            off[i] = i * M0;
+        }
+    }
+    // non-overlap of instance ranges
+    {
+        std::vector<int64_t> order(ninst);
+        std::iota(order.begin(), order.end(), 0);
+        std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return off[a] < off[b]; });
+        for (int64_t k = 1; k < ninst; ++k) {
+            int64_t a = order[k - 1], b = order[k];
+            if (off[a] + cell_M(c->tables[tab[a]]) > off[b])
+                return fail(c, BTE_EINVAL, "instances " + std::to_string(a) + " and " + std::to_string(b) + " overlap");
+        }
+    }
+    Batch *B = new Batch();
+    B->uniform = inst == nullptr;
+    std::vector<int64_t> slot_off, slot_out;
+    for (int t = 0; t < (int)c->tables.size(); ++t) {
+        std::vector<int64_t> members;
+        for (int64_t i = 0; i < ninst; ++i)
+            if (tab[i] == t) members.push_back(i);
+        if (members.empty()) continue;
+        Segment s;
+        s.table = t;
+        s.s0 = B->nslots;
+        s.nvalid = (int)members.size();
+        s.nslots = (s.nvalid + kLanes - 1) / kLanes * kLanes;
+        s.eoff = B->n_celem;
+        const int64_t M = cell_M(c->tables[t]);
+        for (int k = 0; k < s.nslots; ++k) {
+            if (k < s.nvalid) {
+                slot_off.push_back(off[members[k]]);
+                slot_out.push_back(members[k]);
+                B->extent = std::max(B->extent, off[members[k]] + M);
+            } else {
+                slot_off.push_back(-1);
+                slot_out.push_back(-1);
+            }
+        }
+        B->nslots += s.nslots;
+        B->n_celem += (int64_t)s.nslots * M;
+        B->segs.push_back(s);
+    }
+    // convolution work items, costliest first
+    std::vector<ConvItem> items;
+    std::vector<uint64_t> cost;
+    for (const Segment &s : B->segs) {
+        const Table *t = c->tables[s.table];
+        const int N = t->N;
+        const int64_t M = cell_M(t);
+        for (int g = 0; g < s.nslots / kLanes; ++g)
+            for (int tile = 0; tile < t->ntiles; ++tile)
+                for (int kk = 0; kk < N * N; ++kk) {
+                    ConvItem ci;
+                    ci.fofs = (uint64_t)(s.eoff + (int64_t)g * M * kLanes);
+                    ci.wofs = t->wofs[(size_t)tile * N * N + kk];
+                    ci.desc_off = t->desc_off[kk];
+                    ci.nblocks = t->nblocks[kk];
+                    ci.k1 = (uint16_t)(kk / N);
+                    ci.k2 = (uint16_t)(kk % N);
+                    ci.kind = (uint16_t)(t->kind0 + tile);
+                    ci.table = (uint16_t)s.table;
+                    if (ci.nblocks == 0) continue;
+                    items.push_back(ci);
+                    cost.push_back((uint64_t)ci.nblocks * t->cpad[tile]);
+                    B->kinds_mask |= 1u << ci.kind;
+                }
+    }
+    std::vector<size_t> order(items.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<ConvItem> sorted(items.size());
+    for (size_t i = 0; i < items.size(); ++i) sorted[i] = items[order[i]];
+    B->nitems = (int)sorted.size();
+    cudaError_t e = cudaMalloc(&B->d_slot_off, sizeof(int64_t) * slot_off.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_slot_out, sizeof(int64_t) * slot_out.size());
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(ConvItem) * std::max<size_t>(sorted.size(), 1));
+    if (e != cudaSuccess) {
+        cudaFree(B->d_slot_off);
+        cudaFree(B->d_slot_out);
+        cudaFree(B->d_items);
+        delete B;
+        return fail(c, BTE_ENOMEM, std::string("batch allocation: ") + cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(B->d_slot_off, slot_off.data(), sizeof(int64_t) * slot_off.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(B->d_slot_out, slot_out.data(), sizeof(int64_t) * slot_out.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !sorted.empty())
+        e = cudaMemcpy(B->d_items, sorted.data(), sizeof(ConvItem) * sorted.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        delete B;
+        return cuda_fail(c, e, "batch upload");
+    }
+    c->batches[key] = B;
+    *out = B;
+    return BTE_OK;
+}
+
+ProjArgs proj_args(const Table *t) {
+    ProjArgs pa;
+    pa.N = t->N;
+    pa.dv = t->dv;
+    std::memcpy(pa.ainv, t->ainv, sizeof(pa.ainv));
+    return pa;
+}
+
+// Allocate everything a collide/step on this batch needs (never inside capture).
+bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
+    bte_status s;
+    const size_t ce = (size_t)B->n_celem;
+    const size_t csz = mode == BTE_FP64_PLAIN ? sizeof(double2) : sizeof(float2);
+    for (int id : {SC_T1, SC_T2, SC_F, SC_QH})
+        if ((s = ensure_scratch(c, id, ce * csz)) != BTE_OK) return s;
+    if (step || transport) {
+        for (int id : {SC_FS, SC_Q1, SC_Q2})
+            if ((s = ensure_scratch(c, id, sizeof(double) * (size_t)B->extent)) != BTE_OK) return s;
+    }
+    if (mode == BTE_FP64_PLAIN) {
+        for (const Segment &sg : B->segs) {
+            int r = build_table_fp64(*c->tables[sg.table], c->err);
+            if (r != BTE_OK) return (bte_status)r;
+        }
+    } else if (mode == BTE_FP32) {
+        ConvLaunch L;
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, &L);
+        if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
+    }
+    return BTE_OK;
+}
+
+// Enqueue Qt (raw) or Q = P Qt for the batch: f -> Q. Scratch must be ready.
+bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, bool project,
+                           cudaStream_t st) {
+    const bool fp64 = mode == BTE_FP64_PLAIN;
+    for (const Segment &sg : B->segs) {
+        const Table *t = c->tables[sg.table];
+        DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
+        const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+        if (fp64)
+            launch_dft_forward<double2>(f, B->d_slot_off, ds, t->d_root64, sf, (double2 *)c->scratch[SC_T1],
+                                        (double2 *)c->scratch[SC_T2], (double2 *)c->scratch[SC_F], c->d_status, st);
+        else
+            launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
+                                       (float2 *)c->scratch[SC_T2], (float2 *)c->scratch[SC_F], c->d_status, st);
+    }
+    if (fp64) {
+        for (const Segment &sg : B->segs) {
+            const Table *t = c->tables[sg.table];
+            launch_conv64((const double2 *)c->scratch[SC_F], (double2 *)c->scratch[SC_QH], t->d_w64, t->d_w64_off,
+                          t->N, sg.eoff, sg.nslots / kLanes, st);
+        }
+    } else {
+        ConvLaunch L;
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, &L);
+        if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
+        ConvParams p{};
+        p.items = B->d_items;
+        p.nitems = B->nitems;
+        p.counter = c->d_counter;
+        p.F = (const float2 *)c->scratch[SC_F];
+        p.Qh = (float2 *)c->scratch[SC_QH];
+        for (size_t i = 0; i < c->tables.size() && i < (size_t)kMaxTables; ++i) {
+            p.W[i] = c->tables[i]->d_w32;
+            p.D[i] = c->tables[i]->d_desc;
+        }
+        p.status = c->d_status;
+        p.merge = c->conv_merge;
+        e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "queue reset");
+        e = conv32_launch(L, p, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "convolution launch");
+    }
+    for (const Segment &sg : B->segs) {
+        const Table *t = c->tables[sg.table];
+        DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
+        const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
+        if (fp64)
+            launch_dft_inverse<double2>((const double2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root64, si,
+                                        (double2 *)c->scratch[SC_T1], (double2 *)c->scratch[SC_T2], Q, st);
+        else
+            launch_dft_inverse<float2>((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si,
+                                       (float2 *)c->scratch[SC_T1], (float2 *)c->scratch[SC_T2], Q, st);
+        if (project)
+            launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(t), 0, nullptr, nullptr, nullptr, 0.0, st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return BTE_OK;
+}
+
+// Heun step of the homogeneous problem on f (in place).
+bte_status enqueue_rk2(bte_ctx *c, Batch *B, double *f, double dt, double eps, int mode, cudaStream_t st) {
+    double *fs = (double *)c->scratch[SC_FS];
+    double *q1 = (double *)c->scratch[SC_Q1];
+    double *q2 = (double *)c->scratch[SC_Q2];
+    bte_status s = enqueue_collide(c, B, f, q1, mode, false, st);
+    if (s != BTE_OK) return s;
+    for (const Segment &sg : B->segs)
+        launch_project(q1, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 1, f, fs, nullptr,
+                       dt / eps, st);
+    if ((s = enqueue_collide(c, B, fs, q2, mode, false, st)) != BTE_OK) return s;
+    for (const Segment &sg : B->segs)
+        launch_project(q2, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 2, nullptr, f, q1,
+                       0.5 * dt / eps, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return BTE_OK;
+}
+
+bte_status check_mode(bte_ctx *c, int mode) {
+    if (mode == BTE_FP64_PLAIN || mode == BTE_FP32) return BTE_OK;
+    if (mode == BTE_LEARNED) return fail(c, BTE_ESTATE, "learned mode: no trained surrogate is loaded");
+    return fail(c, BTE_EINVAL, "unknown mode");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bte_version(void) { return "libbte 0.1 (sm_103a)"; }
+
+bte_status bte_create(bte_ctx **ctx, int device) {
+    if (!ctx) return BTE_EINVAL;
+    *ctx = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) return BTE_ECUDA;
+    if (device < 0 || device >= n) return BTE_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return BTE_ECUDA;
+    bte_ctx *c = new bte_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess ||
+        cudaMalloc(&c->d_wall, 2 * sizeof(double)) != cudaSuccess) {
+        bte_destroy(c);
+        return BTE_ENOMEM;
+    }
+    cudaMemset(c->d_status, 0, sizeof(int));
+    cudaMemset(c->d_counter, 0, 64);
+    *ctx = c;
+    return BTE_OK;
+}
+
+void bte_destroy(bte_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : c->batches) {
+        cudaFree(kv.second->d_slot_off);
+        cudaFree(kv.second->d_slot_out);
+        cudaFree(kv.second->d_items);
+        delete kv.second;
+    }
+    for (Table *t : c->tables) {
+        free_table(*t);
+        delete t;
+    }
+    for (int i = 0; i < 8; ++i) cudaFree(c->scratch[i]);
+    cudaFree(c->d_status);
+    cudaFree(c->d_counter);
+    cudaFree(c->d_wall);
+    delete c;
+}
+
+const char *bte_last_error(const bte_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+bte_status bte_init_weights(bte_ctx *c, const bte_grid *grids, int ngrids, int *table_ids) {
+    if (!c || !grids || !table_ids || ngrids <= 0) return fail(c, BTE_EINVAL, "bte_init_weights: bad arguments");
+    if ((int)c->tables.size() + ngrids > kMaxTables)
+        return fail(c, BTE_EINVAL, "too many weight tables (max " + std::to_string(kMaxTables) + ")");
+    cudaSetDevice(c->device);
+    for (int i = 0; i < ngrids; ++i) {
+        Table *t = new Table();
+        t->N = grids[i].N;
+        t->L = grids[i].L;
+        t->lam = grids[i].lambda;
+        int r = build_table(*t, c->err);
+        if (r != BTE_OK) {
+            delete t;
+            return (bte_status)r;
+        }
+        table_ids[i] = (int)c->tables.size();
+        c->tables.push_back(t);
+        // batches built before this call stay valid (they name tables by id)
+    }
+    return BTE_OK;
+}
+
+bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_instance *inst, int64_t ninst,
+                          int mode, unsigned flags, void *stream) {
+    if (!c) return BTE_EINVAL;
+    if (!f || !Q) return fail(c, BTE_EINVAL, "bte_collide: null f or Q");
+    if (f == Q) return fail(c, BTE_EINVAL, "bte_collide: f and Q must not overlap");
+    bte_status s = check_mode(c, mode);
+    if (s != BTE_OK) return s;
+    cudaSetDevice(c->device);
+    Batch *B = nullptr;
+    if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
+    if ((s = prepare(c, B, mode, false, false)) != BTE_OK) return s;
+    return enqueue_collide(c, B, f, Q, mode, !(flags & BTE_FLAG_RAW), (cudaStream_t)stream);
+}
+
+bte_status bte_collide(bte_ctx *c, const double *f, double *Q, const bte_instance *inst, int64_t ninst, int mode,
+                       void *stream) {
+    return bte_collide_ex(c, f, Q, inst, ninst, mode, 0u, stream);
+}
+
+bte_status bte_project(bte_ctx *c, double *Q, const bte_instance *inst, int64_t ninst, void *stream) {
+    if (!c) return BTE_EINVAL;
+    if (!Q) return fail(c, BTE_EINVAL, "bte_project: null Q");
+    cudaSetDevice(c->device);
+    Batch *B = nullptr;
+    bte_status s = get_batch(c, inst, ninst, &B);
+    if (s != BTE_OK) return s;
+    for (const Segment &sg : B->segs)
+        launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 0, nullptr, nullptr,
+                       nullptr, 0.0, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "projection launch");
+}
+
+bte_status bte_moments(bte_ctx *c, const double *f, double *out, const bte_instance *inst, int64_t ninst,
+                       void *stream) {
+    if (!c) return BTE_EINVAL;
+    if (!f || !out) return fail(c, BTE_EINVAL, "bte_moments: null pointer");
+    cudaSetDevice(c->device);
+    Batch *B = nullptr;
+    bte_status s = get_batch(c, inst, ninst, &B);
+    if (s != BTE_OK) return s;
+    for (const Segment &sg : B->segs) {
+        const Table *t = c->tables[sg.table];
+        launch_moments(f, B->d_slot_off, sg.s0, sg.nslots, t->N, t->dv, B->d_slot_out, out, (cudaStream_t)stream);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "moments launch");
+}
+
+bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t ninst, double dt, double eps,
+                    const bte_transport *tr, int mode, void *stream) {
+    if (!c) return BTE_EINVAL;
+    if (!f) return fail(c, BTE_EINVAL, "bte_step: null f");
+    if (!(dt > 0.0) || !(eps > 0.0) || !std::isfinite(dt) || !std::isfinite(eps))
+        return fail(c, BTE_EINVAL, "bte_step: dt and eps must be finite and > 0");
+    bte_status s = check_mode(c, mode);
+    if (s != BTE_OK) return s;
+    cudaSetDevice(c->device);
+    TransportArgs ta{};
+    if (tr) {
+        if (inst) return fail(c, BTE_EINVAL, "bte_step: transport needs uniform cells (inst == NULL)");
+        if (tr->nx != ninst || tr->nx < 2) return fail(c, BTE_EINVAL, "bte_step: tr->nx must equal ninst (>= 2)");
+        if (!(tr->x1 > tr->x0)) return fail(c, BTE_EINVAL, "bte_step: x1 must exceed x0");
+        for (int bc : {tr->bc_left, tr->bc_right})
+            if (bc != BTE_BC_DIFFUSE && bc != BTE_BC_SPECULAR) return fail(c, BTE_EINVAL, "bte_step: unknown wall type");
+        if ((tr->bc_left == BTE_BC_DIFFUSE && !(tr->Tw_left > 0.0)) ||
+            (tr->bc_right == BTE_BC_DIFFUSE && !(tr->Tw_right > 0.0)))
+            return fail(c, BTE_EINVAL, "bte_step: wall temperatures must be > 0");
+        const Table *t0 = c->tables.empty() ? nullptr : c->tables[0];
+        if (!t0) return fail(c, BTE_ESTATE, "no weight tables: call bte_init_weights first");
+        ta.N = t0->N;
+        ta.nx = tr->nx;
+        ta.dv = t0->dv;
+        ta.dx = (tr->x1 - tr->x0) / tr->nx;
+        ta.bc_left = tr->bc_left;
+        ta.bc_right = tr->bc_right;
+        ta.Tw_left = tr->Tw_left;
+        ta.Tw_right = tr->Tw_right;
+    }
+    Batch *B = nullptr;
+    if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
+    if ((s = prepare(c, B, mode, true, tr != nullptr)) != BTE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto body = [&]() -> bte_status {
+        if (tr) launch_transport_half(f, (double *)c->scratch[SC_FS], c->d_wall, ta, 0.5 * dt, st);
+        bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st);
+        if (r != BTE_OK) return r;
+        if (tr) launch_transport_half(f, (double *)c->scratch[SC_FS], c->d_wall, ta, 0.5 * dt, st);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "kernel launch");
+    };
+    if (st == nullptr) return body();  // the legacy stream cannot be captured
+    GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
+                 tr ? 1 : 0, dt, eps, f, stream};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream capture");
+        bte_status r = body();
+        e = cudaStreamEndCapture(st, &g);
+        if (r != BTE_OK) {
+            if (g) cudaGraphDestroy(g);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream capture end");
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        it = c->graphs.emplace(key, ex).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, st);
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "graph launch");
+}
+
+bte_status bte_sync_status(bte_ctx *c, void *stream) {
+    if (!c) return BTE_EINVAL;
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    int st = 0;
+    e = cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+    if (st) cudaMemset(c->d_status, 0, sizeof(int));
+    if (st & ST_TIMEOUT) return fail(c, BTE_ETIMEOUT, "a bounded wait in a kernel ran out");
+    if (st & ST_BADDESC) return fail(c, BTE_ECUDA, "a convolution block descriptor was out of range");
+    if (st & ST_NONFINITE) return fail(c, BTE_ENONFINITE, "non-finite value in the input f");
+    return BTE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal declarations of libbte (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/bte.h"
+
+namespace bte {
+
+// Device status bits (atomicOr'ed by kernels, read by bte_sync_status).
+enum : int { ST_TIMEOUT = 1, ST_NONFINITE = 2, ST_BADDESC = 4 };
+
+constexpr int kLanes = 32;  // cells per group: one warp lane per cell
+
+// ----------------------------------------------------------------------------
+// Convolution kernel variants: N, k3-tile size T and tile origin K0.
+// ----------------------------------------------------------------------------
+struct ConvKind {
+    int N, T, K0;
+};
+constexpr int kNumKinds = 7;
+// kind ids: 0:(8,8,0) 1:(12,12,0) 2:(16,16,0) 3:(24,12,0) 4:(24,12,12) 5:(32,16,0) 6:(32,16,16)
+inline ConvKind conv_kind(int id) {
+    static const ConvKind k[kNumKinds] = {{8, 8, 0},    {12, 12, 0},  {16, 16, 0}, {24, 12, 0},
+                                          {24, 12, 12}, {32, 16, 0},  {32, 16, 16}};
+    return k[id];
+}
+int first_kind_for_N(int N);  // -1 if unsupported
+int tiles_for_N(int N);
+
+// One warp-sized unit of convolution work: cell group g (32 lanes), pencil
+// (k1, k2), k3 tile. Sorted by cost (descending) before upload.
+struct ConvItem {
+    uint64_t fofs;       // float2 offset of the group's fhat ([m][lane]) == qhat offset
+    uint64_t wofs;       // float offset of the first weight block
+    uint32_t desc_off;   // first (m1, m2) descriptor of the pencil
+    uint32_t nblocks;    // kept (m1, m2) blocks of the pencil
+    uint16_t k1, k2;
+    uint16_t kind;       // ConvKind id
+    uint16_t table;      // weight table index
+};
+static_assert(sizeof(ConvItem) == 32, "ConvItem layout");
+
+// Per-grid weight table and constants.
+struct Table {
+    int N = 0;
+    double L = 0, lam = 0;
+    int ntiles = 0;
+    int kind0 = 0;
+    double dv = 0, dz = 0;
+    // FP32 pair-symmetrised weights (times dz^3): [tile][k1][k2][block][cpad]
+    std::vector<uint64_t> wofs;          // per (tile, k1, k2)
+    std::vector<uint32_t> desc_off;      // per (k1, k2)
+    std::vector<uint32_t> nblocks;       // per (k1, k2)
+    int cpad[2] = {0, 0};
+    size_t n_w32 = 0, n_desc = 0;
+    float *d_w32 = nullptr;
+    uint32_t *d_desc = nullptr;          // m1 | (m2 << 16)
+    // FP64 plain table (times dz^3), valid boxes, zeta-major; built lazily.
+    double *d_w64 = nullptr;
+    uint64_t *d_w64_off = nullptr;       // per k (M + 1 entries)
+    size_t n_w64 = 0;
+    // DFT roots exp(2 pi i t / N), t in [0, N)
+    float2 *d_root32 = nullptr;
+    double2 *d_root64 = nullptr;
+    // Projection: (C C^T)^{-1}, row-major 5x5 (C without the dv^3 factor folded in)
+    double ainv[25];
+    // Host FP64 radial tables on integer invariants (kept for the lazy FP64 table)
+    std::vector<double> I, J;            // I[p * nq + q], J[s]
+    int np = 0, nq = 0, ns = 0;
+    double ghat(int k1, int k2, int k3, int m1, int m2, int m3) const;  // FP64, no dz^3
+};
+
+struct GraphKey {
+    int64_t ninst;
+    int table, mode, transport;
+    double dt, eps;
+    const void *f;
+    void *stream;
+    bool operator<(const GraphKey &o) const;
+};
+
+struct Batch;  // device-side description of one instance layout (defined in api.cu)
+
+}  // namespace bte
+
+struct bte_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    std::vector<bte::Table *> tables;
+    int *d_status = nullptr;
+    unsigned *d_counter = nullptr;
+    // grow-only scratch
+    void *scratch[8] = {nullptr};
+    size_t scratch_bytes[8] = {0};
+    std::map<std::string, bte::Batch *> batches;
+    std::map<bte::GraphKey, cudaGraphExec_t> graphs;
+    double *d_wall = nullptr;  // sigma_w of the diffuse walls (2 doubles)
+    int conv_warps = 8;        // warps per CTA of the convolution kernel
+    int conv_stages = 2;       // pipeline depth (weight/row blocks in flight per warp)
+    int conv_merge = 4;        // blocks per compensated (TwoSum) merge
+};
+
+namespace bte {
+
+// tables.cpp
+int build_table(Table &t, std::string &err);
+int build_table_fp64(Table &t, std::string &err);
+void free_table(Table &t);
+
+}  // namespace bte

@@ -1,0 +1,338 @@
+// FP32 weighted convolution of Sec. 3.2 (the O(N^6) hot loop):
+//   Qhat(zeta_k) = dz^3 sum_m Ghat(xi_m, zeta_k) fhat(xi_m) fhat(zeta_k - xi_m),
+// zero extension: only m with n = k - m + N/2 on the grid.
+//
+// Design (GB300, sm_103a):
+// - One warp lane per spatial cell: a warp evaluates the same (zeta, xi) pairs
+//   for 32 cells, so each weight is loaded once per warp and shared by 32
+//   cells (the paper's weights Ghat are the same for every cell, Sec. 4).
+// - Pair symmetry: fhat_m fhat_n serves both m and its partner n, so every
+//   unordered pair is evaluated once with the weight Ghat(k,m) + Ghat(k,n)
+//   (host-packed, see tables.cpp). Half the products, half the weight bytes.
+// - Work item = (32-cell group, pencil (k1, k2), k3 tile of T outputs). The
+//   item loops over the kept (m1, m2) blocks of the pencil. For each block the
+//   row fhat[m1][m2][:] ("a"), the partner row fhat[n1][n2][:] ("b") and the
+//   block's weights are brought into a per-warp shared-memory ring by TMA bulk
+//   copies (cp.async.bulk, mbarrier transaction counts). The block is then a
+//   fully unrolled (m3, k3) loop: each a-value is reused for all T outputs of
+//   the tile, each b-value by T pairs along the diagonal k3 - m3, weights are
+//   read as warp-uniform 16-byte shared loads.
+// - Accumulation: plain FP32 FMAs inside `merge` blocks, then Knuth's TwoSum
+//   folds the partial into a (hi, lo) pair per output (compensated sum).
+// - Persistent grid (one resident wave), items taken from an atomic queue in
+//   LPT order (costliest first). Every wait is bounded by the global timer; on
+//   expiry the warp records BTE_ETIMEOUT in the status word, waits (bounded)
+//   for its own copies in flight and leaves.
+#include <map>
+#include <tuple>
+
+#include "kernels.h"
+
+namespace bte {
+
+namespace {
+
+constexpr int kMaxStages = 4;
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait on one phase of a stage barrier; false after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+// Compile-time shape of one kernel variant.
+template <int N_, int T_, int K0_>
+struct Kind {
+    static constexpr int N = N_, T = T_, K0 = K0_, H = N_ / 2;
+    static constexpr int lo(int k) { return k - H + 1 > 0 ? k - H + 1 : 0; }
+    static constexpr int hi(int k) { return k + H < N - 1 ? k + H : N - 1; }
+    static constexpr int count() {
+        int c = 0;
+        for (int j = 0; j < T; ++j) c += hi(K0 + j) - lo(K0 + j) + 1;
+        return c;
+    }
+    static constexpr int cpad = (count() + 3) & ~3;
+    static constexpr int row_bytes = N * kLanes * 8;
+    static constexpr int stage_bytes = 2 * row_bytes + cpad * 4;
+};
+
+using K8 = Kind<8, 8, 0>;
+using K12 = Kind<12, 12, 0>;
+using K16 = Kind<16, 16, 0>;
+using K24a = Kind<24, 12, 0>;
+using K24b = Kind<24, 12, 12>;
+using K32a = Kind<32, 16, 0>;
+using K32b = Kind<32, 16, 16>;
+
+// One block: a-row, b-row and weights of stage `st` into the part accumulators.
+template <class K>
+__device__ __forceinline__ void conv_block(const char *st, int lane, float (&part)[2 * K::T]) {
+    const float2 *A = reinterpret_cast<const float2 *>(st);
+    const float2 *B = A + K::N * kLanes;
+    const float4 *W4 = reinterpret_cast<const float4 *>(B + K::N * kLanes);
+    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int wi = 0;
+#pragma unroll
+    for (int m3 = 0; m3 < K::N; ++m3) {
+        const float2 a = A[m3 * kLanes + lane];
+#pragma unroll
+        for (int j = 0; j < K::T; ++j) {
+            const int n3 = K::K0 + j - m3 + K::H;
+            if (n3 >= 0 && n3 < K::N) {
+                if ((wi & 3) == 0) w4 = W4[wi >> 2];
+                const float w = (wi & 3) == 0 ? w4.x : (wi & 3) == 1 ? w4.y : (wi & 3) == 2 ? w4.z : w4.w;
+                ++wi;
+                const float2 b = B[n3 * kLanes + lane];
+                const float tr = w * a.x, ti = w * a.y;
+                part[2 * j] = fmaf(tr, b.x, part[2 * j]);
+                part[2 * j] = fmaf(-ti, b.y, part[2 * j]);
+                part[2 * j + 1] = fmaf(tr, b.y, part[2 * j + 1]);
+                part[2 * j + 1] = fmaf(ti, b.x, part[2 * j + 1]);
+            }
+        }
+    }
+}
+
+struct WarpRing {
+    char *base;        // stages * stage_bytes (this warp's ring)
+    uint32_t bars;     // shared address of the first stage barrier (8 bytes each)
+    uint32_t phase;    // bit s: parity of the next completion of stage s
+    int stage_bytes;
+};
+
+// Issue the three bulk copies of block j of the item into stage s (lane 0 only).
+template <class K>
+__device__ __forceinline__ void issue_block(const WarpRing &r, int s, const ConvItem &it,
+                                            const ConvParams &p, int j) {
+    const uint32_t d = p.D[it.table][it.desc_off + j];
+    int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16);
+    int n1 = (int)it.k1 - m1 + K::H, n2 = (int)it.k2 - m2 + K::H;
+    if (m1 >= K::N || m2 >= K::N || n1 < 0 || n1 >= K::N || n2 < 0 || n2 >= K::N) {
+        atomicOr(p.status, ST_BADDESC);
+        m1 = m2 = n1 = n2 = 0;  // stay in bounds; the result is flagged as invalid
+    }
+    const float2 *Fg = p.F + it.fofs;
+    const float2 *arow = Fg + (size_t)((m1 * K::N + m2) * K::N) * kLanes;
+    const float2 *brow = Fg + (size_t)((n1 * K::N + n2) * K::N) * kLanes;
+    const float *w = p.W[it.table] + it.wofs + (size_t)j * K::cpad;
+    char *dst = r.base + s * r.stage_bytes;
+    const uint32_t bar = r.bars + 8u * s;
+    mbar_expect_tx(bar, (uint32_t)K::stage_bytes);
+    bulk_g2s(smem_u32(dst), arow, K::row_bytes, bar);
+    bulk_g2s(smem_u32(dst + K::row_bytes), brow, K::row_bytes, bar);
+    bulk_g2s(smem_u32(dst + 2 * K::row_bytes), w, K::cpad * 4, bar);
+}
+
+// Process one item; returns false if a wait timed out (the ring is drained).
+template <class K>
+__device__ bool conv_item(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane) {
+    const int nb = (int)it.nblocks;
+    const int S = p.stages;
+    if (lane == 0)
+        for (int s = 0; s < S && s < nb; ++s) issue_block<K>(r, s, it, p, s);
+    __syncwarp();
+
+    float part[2 * K::T], hi[2 * K::T], lo[2 * K::T];
+#pragma unroll
+    for (int i = 0; i < 2 * K::T; ++i) part[i] = hi[i] = lo[i] = 0.f;
+
+    int since = 0;
+    bool ok = true;
+    int j = 0;
+    for (; j < nb; ++j) {
+        const int s = j % S;
+        const uint32_t par = (r.phase >> s) & 1u;
+        bool got = mbar_wait_bounded(r.bars + 8u * s, par);
+        got = __all_sync(0xffffffffu, got);
+        if (!got) {
+            ok = false;
+            break;
+        }
+        r.phase ^= (1u << s);
+        conv_block<K>(r.base + s * r.stage_bytes, lane, part);
+        if (++since == p.merge || j == nb - 1) {
+            since = 0;
+#pragma unroll
+            for (int i = 0; i < 2 * K::T; ++i) {  // TwoSum(hi, part)
+                const float sum = hi[i] + part[i];
+                const float bp = sum - hi[i];
+                const float err = (hi[i] - (sum - bp)) + (part[i] - bp);
+                hi[i] = sum;
+                lo[i] += err;
+                part[i] = 0.f;
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && j + S < nb) issue_block<K>(r, s, it, p, j + S);
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+        // drain: wait (bounded) for every copy this warp still has in flight
+        const int last = nb < j + S ? nb : j + S;
+        for (int jj = j; jj < last; ++jj) {
+            const int s = jj % S;
+            if (mbar_wait_bounded(r.bars + 8u * s, (r.phase >> s) & 1u)) r.phase ^= (1u << s);
+        }
+        __syncwarp();
+        return false;
+    }
+    float2 *Q = p.Qh + it.fofs + ((size_t)(it.k1 * K::N + it.k2) * K::N + K::K0) * kLanes + lane;
+#pragma unroll
+    for (int t = 0; t < K::T; ++t) Q[t * kLanes] = make_float2(hi[2 * t] + lo[2 * t], hi[2 * t + 1] + lo[2 * t + 1]);
+    return true;
+}
+
+template <class K>
+__device__ __forceinline__ bool run_kind(WarpRing &r, const ConvItem &it, const ConvParams &p,
+                                         int lane) {
+    return conv_item<K>(r, it, p, lane);
+}
+
+// MASK: set of kinds compiled into this kernel instance.
+template <unsigned MASK>
+__global__ void __launch_bounds__(256) conv32_kernel(ConvParams p) {
+    extern __shared__ __align__(128) char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    WarpRing r;
+    r.base = smem + (size_t)warp * p.warp_smem;
+    r.stage_bytes = p.warp_smem / p.stages;
+    r.bars = smem_u32(smem + (size_t)nwarps * p.warp_smem) + 8u * kMaxStages * warp;
+    r.phase = 0;
+    if (lane == 0) {
+        for (int s = 0; s < p.stages; ++s) mbar_init(r.bars + 8u * s, 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = (int)atomicAdd(p.counter, 1u);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= p.nitems) break;
+        const ConvItem it = p.items[idx];
+        bool ok = true;
+        switch (it.kind) {
+            case 0: if (MASK & 1u) ok = run_kind<K8>(r, it, p, lane); break;
+            case 1: if (MASK & 2u) ok = run_kind<K12>(r, it, p, lane); break;
+            case 2: if (MASK & 4u) ok = run_kind<K16>(r, it, p, lane); break;
+            case 3: if (MASK & 8u) ok = run_kind<K24a>(r, it, p, lane); break;
+            case 4: if (MASK & 16u) ok = run_kind<K24b>(r, it, p, lane); break;
+            case 5: if (MASK & 32u) ok = run_kind<K32a>(r, it, p, lane); break;
+            case 6: if (MASK & 64u) ok = run_kind<K32b>(r, it, p, lane); break;
+            default: ok = false; break;
+        }
+        if (!ok) break;
+    }
+}
+
+template <class K>
+constexpr int sb() { return K::stage_bytes; }
+
+}  // namespace
+
+int conv_stage_bytes(int kind) {
+    switch (kind) {
+        case 0: return sb<K8>();
+        case 1: return sb<K12>();
+        case 2: return sb<K16>();
+        case 3: return sb<K24a>();
+        case 4: return sb<K24b>();
+        case 5: return sb<K32a>();
+        case 6: return sb<K32b>();
+        default: return 0;
+    }
+}
+
+cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages,
+                             ConvLaunch *out) {
+    static std::map<std::tuple<unsigned, int, int, int>, ConvLaunch> cache;
+    auto key = std::make_tuple(kinds_mask, num_sms, warps_per_cta, stages);
+    auto itc = cache.find(key);
+    if (itc != cache.end()) {
+        *out = itc->second;
+        return cudaSuccess;
+    }
+    ConvLaunch L{};
+    int stage = 0;
+    for (int k = 0; k < kNumKinds; ++k)
+        if (kinds_mask & (1u << k)) stage = stage > conv_stage_bytes(k) ? stage : conv_stage_bytes(k);
+    L.stages = stages < 1 ? 1 : (stages > kMaxStages ? kMaxStages : stages);
+    L.warp_smem = stage * L.stages;
+    const int max_smem = 227 * 1024;
+    int warps = warps_per_cta < 1 ? 1 : (warps_per_cta > 8 ? 8 : warps_per_cta);
+    while (warps > 1 && warps * (L.warp_smem + 8 * kMaxStages) > max_smem) --warps;
+    L.threads = warps * 32;
+    L.smem = (size_t)warps * (L.warp_smem + 8 * kMaxStages);
+    switch (kinds_mask) {
+        case 1u: L.fn = conv32_kernel<1u>; break;
+        case 2u: L.fn = conv32_kernel<2u>; break;
+        case 4u: L.fn = conv32_kernel<4u>; break;
+        case 8u | 16u: L.fn = conv32_kernel<24u>; break;
+        case 32u | 64u: L.fn = conv32_kernel<96u>; break;
+        default: L.fn = conv32_kernel<127u>; break;
+    }
+    cudaError_t e = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, L.threads, L.smem);
+    if (e != cudaSuccess) return e;
+    L.grid = num_sms * (per_sm < 1 ? 1 : per_sm);
+    cache[key] = L;
+    *out = L;
+    return cudaSuccess;
+}
+
+cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p0, cudaStream_t st) {
+    ConvParams p = p0;
+    p.stages = L.stages;
+    p.warp_smem = L.warp_smem;
+    if (p.merge < 1) p.merge = 1;
+    const int warps = L.threads / 32;
+    int grid = L.grid;
+    if ((int64_t)grid * warps > p.nitems) grid = (p.nitems + warps - 1) / warps;
+    if (grid < 1) grid = 1;
+    L.fn<<<grid, L.threads, L.smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace bte

@@ -1,0 +1,78 @@
+// Launch interfaces of the CUDA kernels (internal).
+#pragma once
+
+#include "bte_internal.h"
+
+namespace bte {
+
+// One segment of a batch: slots [s0, s0 + nslots) that share a weight table
+// (hence N). nslots is a multiple of 32 (padding slots have offset -1).
+struct DftSeg {
+    int N;
+    int s0;        // first slot of the segment (global slot index)
+    int nslots;    // slots in the segment (multiple of 32)
+    int64_t eoff;  // complex-element offset of slot s0 in scratch / group buffers
+};
+
+template <typename C>
+void launch_dft_forward(const double *f, const int64_t *slot_off, const DftSeg &s, const C *root,
+                        double scale, C *T1, C *T2, C *G, int *status, cudaStream_t st);
+template <typename C>
+void launch_dft_inverse(const C *G, const int64_t *slot_off, const DftSeg &s, const C *root,
+                        double scale, C *T1, C *T2, double *q, cudaStream_t st);
+
+// FP32 convolution (persistent, work queue of ConvItems).
+constexpr int kMaxTables = 16;
+struct ConvParams {
+    const ConvItem *items;
+    int nitems;
+    unsigned *counter;
+    const float2 *F;
+    float2 *Qh;
+    const float *W[kMaxTables];
+    const uint32_t *D[kMaxTables];
+    int *status;
+    int stages;     // pipeline depth per warp (1..4)
+    int merge;      // blocks per TwoSum merge
+    int warp_smem;  // bytes of ring per warp
+};
+int conv_stage_bytes(int kind);
+struct ConvLaunch {
+    void (*fn)(ConvParams);
+    int grid, threads, stages, warp_smem;
+    size_t smem;
+};
+// kinds_mask: bit i set when items of kind i are present. Sets the kernel's
+// shared-memory attribute: call outside stream capture.
+cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages,
+                             ConvLaunch *out);
+cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t st);
+
+// Plain FP64 convolution of one segment.
+void launch_conv64(const double2 *F, double2 *Qh, const double *W, const uint64_t *Woff, int N,
+                   int64_t eoff, int ngroups, cudaStream_t st);
+
+// Projection (Sec. 3.3), optionally fused with the RK2 update:
+// mode 0: Q <- P Q;  mode 1: Q <- P Q, Y <- X + a Q;  mode 2: Q <- P Q, Y <- Y + a (Qp + Q).
+struct ProjArgs {
+    int N;
+    double dv;
+    double ainv[25];
+};
+void launch_project(double *Q, const int64_t *slot_off, int s0, int nslots, const ProjArgs &pa,
+                    int mode, const double *X, double *Y, const double *Qp, double a,
+                    cudaStream_t st);
+void launch_moments(const double *f, const int64_t *slot_off, int s0, int nslots, int N, double dv,
+                    const int64_t *slot_out, double *out, cudaStream_t st);
+
+// Transport (Sec. 3.4) on nx uniform cells of M values.
+struct TransportArgs {
+    int N, nx;
+    double dv, dx;
+    int bc_left, bc_right;
+    double Tw_left, Tw_right;
+};
+void launch_transport_half(double *f, double *f1, double *wall, const TransportArgs &ta, double tau,
+                           cudaStream_t st);
+
+}  // namespace bte

@@ -1,0 +1,314 @@
+// Host FP64 tabulation of the convolution weights Ghat (Sec. 2.2, Eq. GHat_calc)
+// and their packing into the layouts the GPU kernels stream.
+//
+// Ghat(xi, zeta) = sqrt(2/pi) [ I(|zeta|/2, |xi - zeta/2|) - J(|xi|) ]  (beta = 1,
+// b = 1/(4 pi), d = 3, radial integral cut off at r0 = L, Sec. 3.1) with
+//   I(a, b) = int_0^L r^{lam+2} sinc(ar) sinc(br) dr,  J(c) = int_0^L r^{lam+2} sinc(cr) dr.
+// The paper notes that for integer lambda these integrals have closed forms;
+// for lambda = 0, 1 they are
+//   I(a, b) = [C(a-b) - C(a+b)] / (2ab),   C(k) = int_0^L r^lam cos(kr) dr,
+//   C_0(k) = sin(kL)/k,   C_1(k) = L sin(kL)/k - 2 sin^2(kL/2)/k^2,
+//   J_0(c) = (sin cL - cL cos cL)/c^3,  J_1(c) = (2cL sin cL - (c^2L^2 - 2) cos cL - 2)/c^4,
+// and I(0, b) = J(b). On the grid every argument is (dz/2) sqrt(integer), so the
+// integrals are evaluated once per integer invariant:
+//   p = |k'|^2 (|zeta| = (dz/2) sqrt p),  q = |2m' - k'|^2 (|xi - zeta/2| = (dz/2) sqrt q),
+//   s = |m'|^2 (|xi| = (dz/2) sqrt(4s)),  k' = k - N/2, m' = m - N/2.
+// With I(0, b) and J evaluated by the same function at bitwise-equal
+// arguments, Ghat(xi, 0) = 0 exactly, as in the continuous weights.
+//
+// FP32 pair-symmetrised layout (the fast path). For a zeta point k the terms m
+// and n = k - m + N/2 (zeta - xi_m = xi_n) multiply the same product
+// fhat_m fhat_n, so the sum over m is taken over unordered pairs with the
+// weight Ghat(k, m) + Ghat(k, n). Pairs are grouped by the first two
+// components: for a "pencil" (k1, k2) the kept blocks are the (m1, m2) of the
+// valid box with (m1, m2) <= (n1, n2) lexicographically; a block with
+// (m1, m2) == (n1, n2) pairs with itself and keeps the plain weight Ghat(k, m)
+// over all m3. Inside a block, for a k3 tile [K0, K0 + T), the weights are
+// stored in the order the kernel consumes them: m3 ascending, then k3
+// ascending, skipping (k3, m3) whose partner n3 = k3 - m3 + N/2 is off the
+// grid. Every weight already carries the trapezoid factor dz^3.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bte_internal.h"
+
+namespace bte {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Radial {
+    double L, lam;
+    double C(double k) const {
+        if (k == 0.0) return lam == 0.0 ? L : 0.5 * L * L;
+        double sk = std::sin(k * L) / k;
+        if (lam == 0.0) return sk;
+        double h = std::sin(0.5 * k * L);
+        return L * sk - 2.0 * h * h / (k * k);
+    }
+    double J(double c) const {
+        if (c == 0.0) return std::pow(L, lam + 3.0) / (lam + 3.0);
+        double x = c * L, s = std::sin(x), co = std::cos(x);
+        if (lam == 0.0) return (s - x * co) / (c * c * c);
+        return (2.0 * x * s - (x * x - 2.0) * co - 2.0) / (c * c * c * c);
+    }
+    double I(double a, double b) const {
+        if (a == 0.0) return J(b);
+        if (b == 0.0) return J(a);
+        return (C(a - b) - C(a + b)) / (2.0 * a * b);
+    }
+};
+
+inline int box_lo(int k, int N) { return std::max(0, k - N / 2 + 1); }
+inline int box_hi(int k, int N) { return std::min(N - 1, k + N / 2); }
+inline int box_len(int k, int N) { return box_hi(k, N) - box_lo(k, N) + 1; }
+
+}  // namespace
+
+int first_kind_for_N(int N) {
+    switch (N) {
+        case 8: return 0;
+        case 12: return 1;
+        case 16: return 2;
+        case 24: return 3;
+        case 32: return 5;
+        default: return -1;
+    }
+}
+
+int tiles_for_N(int N) { return (N == 24 || N == 32) ? 2 : 1; }
+
+double Table::ghat(int k1, int k2, int k3, int m1, int m2, int m3) const {
+    const int h = N / 2;
+    int k[3] = {k1 - h, k2 - h, k3 - h}, m[3] = {m1 - h, m2 - h, m3 - h};
+    int p = 0, q = 0, s = 0;
+    for (int d = 0; d < 3; ++d) {
+        p += k[d] * k[d];
+        q += (2 * m[d] - k[d]) * (2 * m[d] - k[d]);
+        s += m[d] * m[d];
+    }
+    return std::sqrt(2.0 / kPi) * (I[(size_t)p * nq + q] - J[s]);
+}
+
+int build_table(Table &t, std::string &err) {
+    const int N = t.N;
+    if (first_kind_for_N(N) < 0) {
+        err = "unsupported N (supported: 8, 12, 16, 24, 32)";
+        return BTE_EINVAL;
+    }
+    if (!(t.L > 0.0) || !std::isfinite(t.L)) {
+        err = "L must be finite and > 0";
+        return BTE_EINVAL;
+    }
+    if (t.lam != 0.0 && t.lam != 1.0) {
+        err = "lambda must be 0 (Maxwell molecules) or 1 (hard spheres)";
+        return BTE_EINVAL;
+    }
+    const int h = N / 2;
+    t.kind0 = first_kind_for_N(N);
+    t.ntiles = tiles_for_N(N);
+    t.dv = 2.0 * t.L / N;
+    t.dz = kPi / t.L;
+    const double hz = 0.5 * t.dz, dz3 = t.dz * t.dz * t.dz;
+
+    // radial integrals on integer invariants
+    t.np = 3 * h * h + 1;
+    t.nq = 3 * (N - 1) * (N - 1) + 1;
+    t.ns = 3 * h * h + 1;
+    t.I.assign((size_t)t.np * t.nq, 0.0);
+    t.J.assign(t.ns, 0.0);
+    Radial R{t.L, t.lam};
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < t.np; ++p) {
+        double a = hz * std::sqrt((double)p);
+        for (int q = 0; q < t.nq; ++q) {
+            if ((p - q) % 2 != 0) continue;  // q = |2m'-k'|^2 has the parity of |k'|^2
+            double b = hz * std::sqrt((double)q);
+            t.I[(size_t)p * t.nq + q] = R.I(a, b);
+        }
+    }
+    for (int s = 0; s < t.ns; ++s) t.J[s] = R.J(hz * std::sqrt((double)(4 * s)));
+
+    // pencil descriptors: kept (m1, m2) blocks
+    std::vector<uint32_t> desc;
+    t.desc_off.assign(N * N, 0);
+    t.nblocks.assign(N * N, 0);
+    for (int k1 = 0; k1 < N; ++k1)
+        for (int k2 = 0; k2 < N; ++k2) {
+            t.desc_off[k1 * N + k2] = (uint32_t)desc.size();
+            uint32_t nb = 0;
+            for (int m1 = box_lo(k1, N); m1 <= box_hi(k1, N); ++m1) {
+                int n1 = k1 - m1 + h;
+                if (m1 > n1) continue;
+                for (int m2 = box_lo(k2, N); m2 <= box_hi(k2, N); ++m2) {
+                    int n2 = k2 - m2 + h;
+                    if (m1 == n1 && m2 > n2) continue;
+                    desc.push_back((uint32_t)m1 | ((uint32_t)m2 << 16));
+                    ++nb;
+                }
+            }
+            t.nblocks[k1 * N + k2] = nb;
+        }
+    t.n_desc = desc.size();
+
+    // weight offsets per (tile, k1, k2)
+    const int T = conv_kind(t.kind0).T;
+    t.wofs.assign((size_t)t.ntiles * N * N, 0);
+    size_t total = 0;
+    for (int tile = 0; tile < t.ntiles; ++tile) {
+        int K0 = tile * T, cnt = 0;
+        for (int j = 0; j < T; ++j) cnt += box_len(K0 + j, N);
+        t.cpad[tile] = (cnt + 3) & ~3;
+        for (int kk = 0; kk < N * N; ++kk) {
+            t.wofs[(size_t)tile * N * N + kk] = total;
+            total += (size_t)t.nblocks[kk] * t.cpad[tile];
+        }
+    }
+    t.n_w32 = total;
+    std::vector<float> w32(total, 0.0f);
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int tile = 0; tile < t.ntiles; ++tile)
+        for (int kk = 0; kk < N * N; ++kk) {
+            const int k1 = kk / N, k2 = kk % N, K0 = tile * T;
+            size_t o = t.wofs[(size_t)tile * N * N + kk];
+            for (uint32_t b = 0; b < t.nblocks[kk]; ++b) {
+                uint32_t d = desc[t.desc_off[kk] + b];
+                int m1 = d & 0xffff, m2 = d >> 16, n1 = k1 - m1 + h, n2 = k2 - m2 + h;
+                bool pair = !(m1 == n1 && m2 == n2);
+                size_t wi = o + (size_t)b * t.cpad[tile];
+                for (int m3 = 0; m3 < N; ++m3)
+                    for (int j = 0; j < T; ++j) {
+                        int k3 = K0 + j, n3 = k3 - m3 + h;
+                        if (n3 < 0 || n3 >= N) continue;
+                        double g = t.ghat(k1, k2, k3, m1, m2, m3);
+                        if (pair) g += t.ghat(k1, k2, k3, n1, n2, n3);
+                        w32[wi++] = (float)(g * dz3);
+                    }
+            }
+        }
+
+    // projection constants: A = sum_j c_j c_j^T, c_j = (1, v1, v2, v3, |v|^2)
+    double A[5][5] = {{0}};
+    for (int j1 = 0; j1 < N; ++j1)
+        for (int j2 = 0; j2 < N; ++j2)
+            for (int j3 = 0; j3 < N; ++j3) {
+                double v1 = t.dv * (j1 - h), v2 = t.dv * (j2 - h), v3 = t.dv * (j3 - h);
+                double c[5] = {1.0, v1, v2, v3, v1 * v1 + v2 * v2 + v3 * v3};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) A[a][b] += c[a] * c[b];
+            }
+    // Gauss-Jordan inverse with partial pivoting
+    double Ai[5][10];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 10; ++b) Ai[a][b] = b < 5 ? A[a][b] : (b - 5 == a ? 1.0 : 0.0);
+    for (int c = 0; c < 5; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < 5; ++r)
+            if (std::fabs(Ai[r][c]) > std::fabs(Ai[piv][c])) piv = r;
+        for (int b = 0; b < 10; ++b) std::swap(Ai[c][b], Ai[piv][b]);
+        double d = Ai[c][c];
+        for (int b = 0; b < 10; ++b) Ai[c][b] /= d;
+        for (int r = 0; r < 5; ++r)
+            if (r != c) {
+                double f = Ai[r][c];
+                for (int b = 0; b < 10; ++b) Ai[r][b] -= f * Ai[c][b];
+            }
+    }
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) t.ainv[a * 5 + b] = Ai[a][b + 5];
+
+    // DFT roots exp(2 pi i t / N)
+    std::vector<float2> r32(N);
+    std::vector<double2> r64(N);
+    for (int s = 0; s < N; ++s) {
+        double c = std::cos(2.0 * kPi * s / N), sn = std::sin(2.0 * kPi * s / N);
+        r32[s] = make_float2((float)c, (float)sn);
+        r64[s] = make_double2(c, sn);
+    }
+
+    // upload
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&t.d_w32, sizeof(float) * std::max<size_t>(total, 4));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_desc, sizeof(uint32_t) * std::max<size_t>(t.n_desc, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_root32, sizeof(float2) * N);
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_root64, sizeof(double2) * N);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc (weight table): ") + cudaGetErrorString(e);
+        free_table(t);
+        return BTE_ENOMEM;
+    }
+    e = cudaMemcpy(t.d_w32, w32.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.d_desc, desc.data(), sizeof(uint32_t) * t.n_desc, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t.d_root32, r32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(t.d_root64, r64.data(), sizeof(double2) * N, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy (weight table): ") + cudaGetErrorString(e);
+        free_table(t);
+        return BTE_ECUDA;
+    }
+    return BTE_OK;
+}
+
+// FP64 table of the plain operator: for each zeta point k (k1-major, k3
+// fastest) the weights Ghat(k, m) dz^3 over its valid box of m (m1-major, m3
+// fastest); off[k] is the prefix sum of the box sizes.
+int build_table_fp64(Table &t, std::string &err) {
+    if (t.d_w64) return BTE_OK;
+    const int N = t.N, M = N * N * N;
+    const double dz3 = t.dz * t.dz * t.dz;
+    std::vector<uint64_t> off(M + 1, 0);
+    for (int k = 0; k < M; ++k) {
+        int k1 = k / (N * N), k2 = (k / N) % N, k3 = k % N;
+        off[k + 1] = off[k] + (uint64_t)box_len(k1, N) * box_len(k2, N) * box_len(k3, N);
+    }
+    t.n_w64 = off[M];
+    std::vector<double> w((size_t)t.n_w64);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int k = 0; k < M; ++k) {
+        int k1 = k / (N * N), k2 = (k / N) % N, k3 = k % N;
+        size_t o = off[k];
+        for (int m1 = box_lo(k1, N); m1 <= box_hi(k1, N); ++m1)
+            for (int m2 = box_lo(k2, N); m2 <= box_hi(k2, N); ++m2)
+                for (int m3 = box_lo(k3, N); m3 <= box_hi(k3, N); ++m3)
+                    w[o++] = t.ghat(k1, k2, k3, m1, m2, m3) * dz3;
+    }
+    cudaError_t e = cudaMalloc(&t.d_w64, sizeof(double) * std::max<uint64_t>(t.n_w64, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_w64_off, sizeof(uint64_t) * (M + 1));
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc (FP64 weight table): ") + cudaGetErrorString(e);
+        cudaFree(t.d_w64);
+        cudaFree(t.d_w64_off);
+        t.d_w64 = nullptr;
+        t.d_w64_off = nullptr;
+        return BTE_ENOMEM;
+    }
+    e = cudaMemcpy(t.d_w64, w.data(), sizeof(double) * t.n_w64, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(t.d_w64_off, off.data(), sizeof(uint64_t) * (M + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy (FP64 weight table): ") + cudaGetErrorString(e);
+        return BTE_ECUDA;
+    }
+    return BTE_OK;
+}
+
+void free_table(Table &t) {
+    cudaFree(t.d_w32);
+    cudaFree(t.d_desc);
+    cudaFree(t.d_w64);
+    cudaFree(t.d_w64_off);
+    cudaFree(t.d_root32);
+    cudaFree(t.d_root64);
+    t.d_w32 = nullptr;
+    t.d_desc = nullptr;
+    t.d_w64 = nullptr;
+    t.d_w64_off = nullptr;
+    t.d_root32 = nullptr;
+    t.d_root64 = nullptr;
+}
+
+}  // namespace bte

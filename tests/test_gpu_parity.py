@@ -1,0 +1,248 @@
+"""GPU parity: libbte (through the C ABI) against the FP64 CPU oracle.
+
+Error metric per cell (the reading adopted for "relative L2" near equilibrium):
+    err = ||Q_gpu - Q_oracle||_2 / ||Q^-_oracle||_2,
+where Q^- is the loss term of the operator (the convolution with the -J part
+of Ghat only, unprojected), computed by the oracle. Bars:
+  - FP32 path: err <= 1e-5 (target accuracy of the fast path);
+  - FP64 plain path: err <= 1e-12 (FP64 sums in a different order);
+  - conservation: |(C Q)_i| <= 1e-12 sum_j |C_ij Q_j| for every cell and moment.
+Sizes span several 32-cell groups and a ragged tail; the full-size workloads
+are checked on sampled cells.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1211_0540_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+L = 6.0
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def bte():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_0540_gb300 import bte as b
+    return b
+
+
+_ctx_cache = {}
+
+
+def ctx_for(bte, grids):
+    key = tuple(grids)
+    if key not in _ctx_cache:
+        c = bte.Context(0)
+        c.init_weights(list(grids))
+        _ctx_cache[key] = c
+    return _ctx_cache[key]
+
+
+def loss_norm(N, lam, f):
+    Qm = oracle.collide(N, L, lam, f, part=1, project=False)
+    return np.linalg.norm(Qm, axis=1)
+
+
+def abs_moment_scale(N, Q):
+    v1, v2, v3 = inputs.velocity_nodes(N, L)
+    dv3 = (2 * L / N) ** 3
+    C = dv3 * np.stack([np.ones(N ** 3), v1.ravel(), v2.ravel(), v3.ravel(),
+                        (v1 ** 2 + v2 ** 2 + v3 ** 2).ravel()])
+    return np.abs(Q.reshape(-1, N ** 3)) @ np.abs(C).T
+
+
+def run_collide(bte, N, lam, f, mode, raw=False):
+    c = ctx_for(bte, ((N, L, lam),))
+    ft = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+    Q = c.collide(ft, mode=mode, raw=raw)
+    c.sync_status()
+    return Q.cpu().numpy().reshape(f.shape)
+
+
+@pytest.mark.parametrize("N,ncells,lam", [(8, 5, 1.0), (8, 70, 0.0), (12, 37, 1.0), (16, 33, 1.0)])
+def test_fp32_collide_matches_oracle(bte, N, ncells, lam):
+    f = inputs.homogeneous_cells(N, L, ncells, seed=100 + N + ncells)
+    Qg = run_collide(bte, N, lam, f, bte.FP32)
+    Qo = oracle.collide(N, L, lam, f)
+    err = np.linalg.norm(Qg - Qo, axis=1) / loss_norm(N, lam, f)
+    assert err.max() <= TOL32, err.max()
+    mom = oracle.moments(N, L, Qg)
+    assert np.all(np.abs(mom) <= 1e-12 * abs_moment_scale(N, Qg))
+
+
+@pytest.mark.parametrize("N,ncells,lam", [(8, 3, 1.0), (12, 33, 0.0)])
+def test_fp64_plain_collide_matches_oracle(bte, N, ncells, lam):
+    f = inputs.homogeneous_cells(N, L, ncells, seed=200 + N)
+    Qg = run_collide(bte, N, lam, f, bte.FP64_PLAIN)
+    Qo = oracle.collide(N, L, lam, f)
+    err = np.linalg.norm(Qg - Qo, axis=1) / loss_norm(N, lam, f)
+    assert err.max() <= TOL64, err.max()
+
+
+def test_raw_operator_matches_oracle_raw(bte):
+    N, lam = 12, 1.0
+    f = inputs.homogeneous_cells(N, L, 3, seed=7)
+    _, raw, _ = oracle.collide(N, L, lam, f, want_raw=True)
+    for mode, tol in ((bte.FP32, TOL32), (bte.FP64_PLAIN, TOL64)):
+        g = run_collide(bte, N, lam, f, mode, raw=True)
+        err = np.linalg.norm(g - raw, axis=1) / loss_norm(N, lam, f)
+        assert err.max() <= tol, (mode, err.max())
+
+
+def test_projection_and_moments_match_oracle(bte):
+    N = 12
+    c = ctx_for(bte, ((N, L, 1.0),))
+    rng = np.random.default_rng(3)
+    Q = rng.standard_normal((35, N ** 3))
+    Qt = torch.from_numpy(Q).cuda()
+    c.project(Qt)
+    c.sync_status()
+    ref = oracle.project(N, L, Q)
+    assert np.abs(Qt.cpu().numpy() - ref).max() <= 1e-12 * np.abs(Q).max()
+    f = inputs.homogeneous_cells(N, L, 35, seed=4)
+    m = c.moments(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert np.abs(m - oracle.moments(N, L, f)).max() <= 1e-13
+
+
+def test_uneven_batch_matches_oracle(bte):
+    grids = ((8, L, 0.0), (12, L, 1.0), (16, L, 1.0))
+    c = ctx_for(bte, grids)
+    rng = np.random.default_rng(5)
+    inst, chunks, cfg = [], [], []
+    off = 0
+    for i in range(45):
+        t = int(rng.integers(0, 3))
+        N = grids[t][0]
+        f = inputs.homogeneous_cells(N, L, 1, seed=1000 + i)[0]
+        off += int(rng.integers(0, 3)) * 8  # gaps between instances
+        inst.append((t, off))
+        chunks.append((off, f))
+        cfg.append(t)
+        off += N ** 3
+    buf = np.zeros(off + 16)
+    for o, f in chunks:
+        buf[o:o + f.size] = f
+    ft = torch.from_numpy(buf).cuda()
+    Qt = torch.full_like(ft, 7.0)
+    c.collide(ft, Qt, inst=inst, mode=bte.FP32)
+    c.sync_status()
+    Qg = Qt.cpu().numpy()
+    for t in range(3):
+        N, _, lam = grids[t]
+        idx = [k for k in range(len(inst)) if cfg[k] == t]
+        f = np.stack([chunks[k][1] for k in idx])
+        Qo = oracle.collide(N, L, lam, f)
+        got = np.stack([Qg[inst[k][1]:inst[k][1] + N ** 3] for k in idx])
+        err = np.linalg.norm(got - Qo, axis=1) / loss_norm(N, lam, f)
+        assert err.max() <= TOL32, (N, err.max())
+    # gaps untouched
+    mask = np.ones(off + 16, bool)
+    for o, f in chunks:
+        mask[o:o + f.size] = False
+    assert np.all(Qg[mask] == 7.0)
+
+
+def test_rk2_step_matches_oracle(bte):
+    N, lam = 12, 1.0
+    f = inputs.homogeneous_cells(N, L, 33, seed=9)
+    ref = oracle.rk2_homogeneous(N, L, lam, f, 0.01, 1.0)
+    c = ctx_for(bte, ((N, L, lam),))
+    s = torch.cuda.Stream()
+    for mode, tol in ((bte.FP64_PLAIN, 1e-13), (bte.FP32, 1e-7)):
+        ft = torch.from_numpy(f.copy()).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            c.step(ft, 0.01, 1.0, mode=mode, stream=s)
+        c.sync_status(s)
+        d = np.abs(ft.cpu().numpy() - ref).max() / np.abs(f).max()
+        assert d <= tol, (mode, d)
+        m0 = oracle.moments(N, L, f)
+        m1 = oracle.moments(N, L, ft.cpu().numpy())
+        scale = np.maximum(np.abs(m0[:, :1]), np.abs(m0[:, 4:5]))
+        assert np.all(np.abs(m1 - m0) <= 1e-12 * scale)
+
+
+def test_strang_step_with_walls_matches_oracle(bte):
+    N, nx, lam = 8, 12, 1.0
+    f = inputs.wall_heating_initial(N, L, nx)
+    f *= (1.0 + 0.1 * np.sin(np.arange(nx) / 3.0))[:, None]
+    dt, eps = 2e-3, 0.1
+    kw = dict(x0=0.0, x1=1.0, bc_left=oracle.BC_DIFFUSE, bc_right=oracle.BC_SPECULAR, Tw_left=2.0,
+              Tw_right=1.0)
+    ref = oracle.strang_step(N, L, lam, f, dt, eps, **kw)
+    c = ctx_for(bte, ((N, L, lam),))
+    s = torch.cuda.Stream()
+    tr = dict(nx=nx, **kw)
+    for mode, tol in ((bte.FP64_PLAIN, 1e-13), (bte.FP32, 1e-7)):
+        ft = torch.from_numpy(f.copy()).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for _ in range(2):  # second call replays the captured graph
+                c.step(ft, dt, eps, transport=tr, mode=mode, stream=s)
+        c.sync_status(s)
+        ref2 = oracle.strang_step(N, L, lam, ref, dt, eps, **kw)
+        d = np.abs(ft.cpu().numpy() - ref2).max() / np.abs(f).max()
+        assert d <= tol, (mode, d)
+        dv3 = (2 * L / N) ** 3
+        assert abs(ft.cpu().numpy().sum() - f.sum()) * dv3 <= 1e-12 * f.sum() * dv3
+
+
+def test_nonfinite_input_is_reported(bte):
+    N = 8
+    c = ctx_for(bte, ((N, L, 1.0),))
+    f = inputs.homogeneous_cells(N, L, 2, seed=1)
+    f[1, 17] = np.nan
+    c.collide(torch.from_numpy(f).cuda(), mode=bte.FP32)
+    with pytest.raises(bte.BteError) as e:
+        c.sync_status()
+    assert e.value.code == -5
+    c.sync_status()  # cleared
+
+
+def test_invalid_arguments_rejected(bte):
+    N = 8
+    c = ctx_for(bte, ((N, L, 1.0),))
+    f = torch.zeros(3 * N ** 3, dtype=torch.float64, device="cuda")
+    with pytest.raises(bte.BteError) as e:
+        c.collide(f, inst=[(5, 0)])
+    assert e.value.code == -1
+    with pytest.raises(bte.BteError):
+        c.collide(f, inst=[(0, 0), (0, 100)])  # overlapping instances
+    with pytest.raises(bte.BteError) as e:
+        c.collide(f, mode=bte.LEARNED)
+    assert e.value.code == -6
+    with pytest.raises(bte.BteError):
+        c.step(f, -1.0)
+    d = bte.Context(0)
+    with pytest.raises(bte.BteError):
+        d.init_weights([(10, L, 1.0)])  # unsupported N
+    with pytest.raises(bte.BteError):
+        d.init_weights([(16, L, 0.5)])  # no closed form for this lambda
+    d.close()
+
+
+@pytest.mark.parametrize("N,ncells,nsample,seed", [(16, 128, 6, 11), (24, 64, 2, 12), (32, 256, 2, 13)])
+def test_full_size_workloads_on_sampled_cells(bte, N, ncells, nsample, seed):
+    """Full batch at the benchmark's sizes; oracle on sampled cells."""
+    f = inputs.precision_sweep_cells(N, L, ncells, seed=seed)
+    c = ctx_for(bte, ((N, L, 1.0),))
+    ft = torch.from_numpy(f).cuda()
+    Q = c.collide(ft, mode=bte.FP32)
+    c.sync_status()
+    Qg = Q.cpu().numpy().reshape(ncells, -1)
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(ncells, size=nsample, replace=False))
+    pick[-1] = ncells - 1  # include the ragged end of the batch
+    Qo = oracle.collide(N, L, 1.0, f[pick])
+    err = np.linalg.norm(Qg[pick] - Qo, axis=1) / loss_norm(N, 1.0, f[pick])
+    assert err.max() <= TOL32, err
+    mom = oracle.moments(N, L, Qg)
+    assert np.all(np.abs(mom) <= 1e-12 * abs_moment_scale(N, Qg))
