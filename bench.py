@@ -1,0 +1,372 @@
+"""Benchmark: cell-collision evaluations per second on the sudden-wall-heating slab.
+
+Workload (one "step" = one Strang step of the whole hot path): 128 uniform
+cells on [0, 1], N = 16 velocity points per dimension on [-6, 6]^3, hard
+spheres (lambda = 1), Knudsen number eps = 0.1, gas initially a Maxwellian at
+rest (rho = 1, T = 1), diffuse wall at x = 0 heated to T_w = 2, specular wall
+at x = 1, dt = 0.5 dx / max|v1| (CFL 0.5). A step is T(dt/2) C(dt) T(dt/2):
+two transport half steps (second-order upwind/minmod) and one Heun step of the
+collision operator over all 128 cells, i.e. 2 x 128 = 256 cell-collision
+evaluations (forward DFT, FP32 weighted convolution, inverse DFT, FP64
+conservation projection), replayed from one CUDA graph.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU) runs independent replicas of the slab
+("scaling": "weak"); the only collectives are the barrier and the max-reduction
+of the timings. --impl reference times the FP64 CPU oracle on the same step.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N, L, LAM = 16, 6.0, 1.0
+NX, EPS, TW = 128, 0.1, 2.0
+DT = 0.5 * (1.0 / NX) / L
+EVALS_PER_STEP = 2 * NX
+METRIC = "cell-collision evals/s at N=16/32 vs plain FP64 GPU op, at stated rel-L2 error"
+UNIT = "cell-collision evals/s"
+WORKLOAD = ("sudden wall heating: 128 cells x N=16^3 velocities (L=6, hard spheres, Kn=0.1, "
+            "Tw=2 diffuse / specular), one Strang step = 2 transport half steps + RK2 over "
+            "128 cells = 256 collision evals")
+FLUSH_BYTES = 512 << 20  # > 129 MB L2
+SMS, FP32_LANES = 152, 128
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def conv_pairs_per_cell(n):
+    """Unordered (zeta, {xi, zeta - xi}) pairs the FP32 kernel evaluates per cell."""
+    h = n // 2
+
+    def lo(k):
+        return max(0, k - h + 1)
+
+    def hi(k):
+        return min(n - 1, k + h)
+
+    row = sum(hi(k) - lo(k) + 1 for k in range(n))
+    blocks = 0
+    for k1 in range(n):
+        for k2 in range(n):
+            for m1 in range(lo(k1), hi(k1) + 1):
+                n1 = k1 - m1 + h
+                if m1 > n1:
+                    continue
+                for m2 in range(lo(k2), hi(k2) + 1):
+                    if m1 == n1 and m2 > k2 - m2 + h:
+                        continue
+                    blocks += 1
+    return blocks * row
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in ("conv32.cu", "kernels.h", "bte_internal.h"):
+        with open(os.path.join(ROOT, "paper_1211_0540_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """DRAM bytes per launch of the convolution kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(PROFILES, "conv32_wallheating_n16_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").strip()
+        ids = [v.strip() for v in vis.split(",") if v.strip()] if vis else []
+        self.index = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+        self.fh = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL, start_new_session=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        self.fh.flush()
+        self.fh.seek(0)
+        rows = [r.split(",") for r in self.fh.read().strip().splitlines() if r.strip()]
+        os.unlink(self.fh.name)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(mhz)) if mhz else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_strang_step(f, oracle):
+    return oracle.strang_step(N, L, LAM, f, DT, EPS, x0=0.0, x1=1.0, bc_left=oracle.BC_DIFFUSE,
+                              bc_right=oracle.BC_SPECULAR, Tw_left=TW, Tw_right=1.0)
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, as it stands, on the same Strang step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1211_0540_gb300 import inputs
+    cores = oracle.get_threads()
+    f = inputs.wall_heating_initial(N, L, NX)
+    oracle.weights(N, L, LAM)  # table build is set-up, not part of a step
+    for _ in range(args.warmup):
+        f = oracle_strang_step(f, oracle)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = oracle_strang_step(f, oracle)
+    dt = time.perf_counter() - t0
+    value = EVALS_PER_STEP * args.steps / dt
+    sample = "the full workload: every step is one whole Strang step of the 128-cell slab"
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "arm": "FP64 CPU oracle (direct sums)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_1211_0540_gb300 import bte, inputs
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    ctx = bte.Context(local)
+    ctx.init_weights([(N, L, LAM)])
+    ctx.profile_enable(True)
+    tr = dict(nx=NX, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=TW,
+              Tw_right=1.0)
+    f0 = inputs.wall_heating_initial(N, L, NX)
+    f = torch.from_numpy(f0).cuda()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    ctx.profile_read("*", stream)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = ctx.launch_count()
+    step_ms, conv_ms, conv_n = [], 0.0, 0
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)  # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
+            e1.record(stream)
+            n, ms = ctx.profile_read("conv32", stream)
+            conv_n += n
+            conv_ms += ms
+            step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - n0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ctx.sync_status(stream)
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = EVALS_PER_STEP * args.steps * world / (total_ms * 1e-3)
+
+    # end to end through the public API: pinned host state in and out every step
+    fh_in = torch.from_numpy(f.cpu().numpy()).pin_memory()
+    fh_out = torch.empty_like(fh_in).pin_memory()
+    e2e_ms = []
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.copy_(fh_in, non_blocking=True)
+            ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
+            fh_out.copy_(f, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+    ctx.profile_read("*", stream)
+    e2e_total = float(sum(e2e_ms))
+    if world > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = EVALS_PER_STEP * args.steps * world / (e2e_total * 1e-3)
+    nbytes = f.numel() * 8
+
+    # plain FP64 GPU operator on the same state (the metric's comparator)
+    f64 = f.clone()
+    with torch.cuda.stream(stream):
+        ctx.step(f64, DT, EPS, transport=tr, mode=bte.FP64_PLAIN, stream=stream)  # build + capture
+        ctx.sync_status(stream)
+        ctx.profile_read("*", stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.step(f64, DT, EPS, transport=tr, mode=bte.FP64_PLAIN, stream=stream)
+        e1.record(stream)
+        ctx.profile_read("*", stream)
+    fp64_value = EVALS_PER_STEP * reps / (e0.elapsed_time(e1) * 1e-3)
+
+    # stated accuracy of the FP32 operator on the benchmark state
+    out = {}
+    if rank == 0:
+        import oracle
+        Qg = ctx.collide(f, mode=bte.FP32, stream=stream)
+        Q64 = ctx.collide(f, mode=bte.FP64_PLAIN, stream=stream)
+        ctx.sync_status(stream)
+        Qg, Q64 = Qg.cpu().numpy().reshape(NX, -1), Q64.cpu().numpy().reshape(NX, -1)
+        fs = f.cpu().numpy().reshape(NX, -1)
+        pick = [0, 1, 2, NX // 2, NX - 1]
+        Qo = oracle.collide(N, L, LAM, fs[pick])
+        Qm = oracle.collide(N, L, LAM, fs[pick], part=1, project=False)
+        rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+        rel64 = np.linalg.norm(Q64[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+        mom = oracle.moments(N, L, Qg)
+        out["accuracy"] = {"fp32_rel_l2_vs_oracle_max": float(rel.max()),
+                           "fp64_plain_rel_l2_vs_oracle_max": float(rel64.max()),
+                           "cells_checked": pick, "norm": "||Q - Q_oracle|| / ||Q_loss_oracle||",
+                           "fp32_max_abs_moment": float(np.abs(mom).max())}
+
+    conv_pairs = conv_pairs_per_cell(N)
+    flops_per_launch = 10.0 * conv_pairs * NX
+    conv_avg_ms = conv_ms / max(conv_n, 1)
+    achieved = flops_per_launch / (conv_avg_ms * 1e-3) / 1e12
+    clk = clocks["sm_mhz"] or 1920.0
+    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    traffic = load_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": NX, "N": N, "L": L, "lambda": LAM, "eps": EPS,
+                   "dt": DT, "l2": "flushed (512 MB write) before every timed step",
+                   "arith": "FP32 convolution (TwoSum-compensated), FP32 DFTs, FP64 projection/state",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz "
+                                   "(measured FFMA microbenchmark: 74.9 TFLOP/s)" % clk,
+                     "flops_per_launch": flops_per_launch,
+                     "flop_unit": "10 flops per evaluated (zeta, {xi, zeta-xi}) pair per cell",
+                     "conv_ms_per_launch": conv_avg_ms, "conv_launches_timed": conv_n},
+        "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(out)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        fs = f0.copy()
+        t0 = time.perf_counter()
+        oracle_strang_step(fs, oracle)
+        tcpu = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": EVALS_PER_STEP / tcpu, "unit": UNIT,
+                                "cores": oracle.get_threads(), "kind": "oracle",
+                                "sample": "one whole Strang step of the 128-cell slab (256 evals)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -60,7 +60,6 @@ typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1 } bte_bc;
 
 /* bte_collide_ex flags */
 #define BTE_FLAG_RAW 1u        /* return Qt (skip the conservation projection)   */
-#define BTE_FLAG_LOSS_ONLY 2u  /* FP64_PLAIN only: loss term of Ghat alone, raw   */
 
 /* Velocity grid and collision kernel of one weight table: B = |u|^lambda / (4 pi)
  * (isotropic, Sec. 2.2). lambda = 0: Maxwell molecules, 1: hard spheres. */
@@ -152,6 +151,32 @@ bte_status bte_sync_status(bte_ctx *ctx, void *stream);
  * array of 5*ninst doubles. FP64. Asynchronous. */
 bte_status bte_moments(bte_ctx *ctx, const double *f, double *out, const bte_instance *inst,
                        int64_t ninst, void *stream);
+
+/* Kernel timing for benchmarks. When enabled, CUDA events are recorded on the
+ * launching stream around every launch of the kernels named below (also inside
+ * the graphs bte_step captures while enabled). bte_profile_read synchronises
+ * `stream`, returns the number of such launches completed since the last read
+ * and their summed device time in milliseconds, and forgets them.
+ * kernel: "conv32" (FP32 convolution), "conv64" (plain FP64 convolution),
+ * "collide" (a whole collide call), or "*" (all of them).
+ * bte_launch_count returns the number of libbte kernels enqueued by this context
+ * so far (a graph replay counts its kernels). */
+bte_status bte_profile_enable(bte_ctx *ctx, int enable);
+bte_status bte_profile_read(bte_ctx *ctx, const char *kernel, int64_t *launches, double *total_ms,
+                            void *stream);
+bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
+
+/* Tuning options of the FP32 convolution (read by the autotuner and tests).
+ * name: "conv_impl"   0 = one warp per work item, 1 = all warps of a CTA share
+ *                      an item (reduced in shared memory), 2 = as 1 with packed
+ *                      f32x2 arithmetic;
+ *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
+ *       "conv_stages" blocks in flight per warp (1..4);
+ *       "conv_merge"  blocks accumulated in plain FP32 between compensated
+ *                      (TwoSum) merges (>= 1).
+ * Changing an option drops the captured step graphs. Errors: BTE_EINVAL. */
+bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
+bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
 /* Library build identification (static string). */
 const char *bte_version(void);

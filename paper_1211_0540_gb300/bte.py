@@ -24,7 +24,8 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 # Every symbol include/bte.h declares (checked by the ABI tests).
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
-           "bte_version"]
+           "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
+           "bte_set_option", "bte_get_option"]
 
 
 class Grid(ctypes.Structure):
@@ -77,6 +78,12 @@ def load(path=None):
         "bte_sync_status": (c_int, [vp, vp]),
         "bte_moments": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
         "bte_version": (ctypes.c_char_p, []),
+        "bte_profile_enable": (c_int, [vp, c_int]),
+        "bte_profile_read": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_i64),
+                                     ctypes.POINTER(c_d), vp]),
+        "bte_launch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
+        "bte_set_option": (c_int, [vp, ctypes.c_char_p, c_int]),
+        "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -189,6 +196,30 @@ class Context:
         self._rc(self._lib.bte_step(self._h, _ptr(f), arr, n, float(dt), float(eps), tr, int(mode),
                                     _stream(stream)), "bte_step")
         return f
+
+    def profile_enable(self, on=True):
+        self._rc(self._lib.bte_profile_enable(self._h, int(bool(on))), "bte_profile_enable")
+
+    def profile_read(self, kernel="conv32", stream=None):
+        """(launches, total_ms) of profiled launches since the last read."""
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        self._rc(self._lib.bte_profile_read(self._h, kernel.encode(), ctypes.byref(n),
+                                            ctypes.byref(ms), _stream(stream)), "bte_profile_read")
+        return n.value, ms.value
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        self._rc(self._lib.bte_launch_count(self._h, ctypes.byref(n)), "bte_launch_count")
+        return n.value
+
+    def set_option(self, name, value):
+        self._rc(self._lib.bte_set_option(self._h, name.encode(), int(value)), "bte_set_option")
+
+    def get_option(self, name):
+        v = ctypes.c_int()
+        self._rc(self._lib.bte_get_option(self._h, name.encode(), ctypes.byref(v)), "bte_get_option")
+        return v.value
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

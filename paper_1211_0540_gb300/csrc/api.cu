@@ -56,6 +56,7 @@ bte_status fail(bte_ctx *c, bte_status s, const std::string &msg) {
 }
 
 bte_status cuda_fail(bte_ctx *c, cudaError_t e, const char *what) {
+    cudaGetLastError();  // do not leave a non-sticky error behind for the caller's runtime checks
     return fail(c, BTE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
@@ -65,9 +66,54 @@ bte_status ensure_scratch(bte_ctx *c, int id, size_t bytes) {
     c->scratch[id] = nullptr;
     c->scratch_bytes[id] = 0;
     cudaError_t e = cudaMalloc(&c->scratch[id], bytes);
-    if (e != cudaSuccess) return fail(c, BTE_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, BTE_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+    }
     c->scratch_bytes[id] = bytes;
     return BTE_OK;
+}
+
+void count_launches(bte_ctx *c, int n) {
+    if (c->capturing) c->cap_launches += n;
+    else c->launches += n;
+}
+
+// Reserve event pairs outside stream capture so that profiled captures never create events.
+void prof_reserve(bte_ctx *c, size_t n) {
+    if (!c->prof) return;
+    while (c->ev_free.size() < n) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return;
+        }
+        c->ev_free.push_back({a, b});
+    }
+}
+
+int prof_begin(bte_ctx *c, int kernel, cudaStream_t st, ProfEntry *pe) {
+    if (!c->prof) return 0;
+    if (c->ev_free.empty()) {
+        if (c->capturing) return 0;
+        prof_reserve(c, 1);
+        if (c->ev_free.empty()) return 0;
+    }
+    pe->kernel = kernel;
+    pe->a = c->ev_free.back().first;
+    pe->b = c->ev_free.back().second;
+    c->ev_free.pop_back();
+    // inside stream capture only an "external" record becomes an event-record node
+    cudaEventRecordWithFlags(pe->a, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    return 1;
+}
+
+void prof_end(bte_ctx *c, int active, const ProfEntry &pe, cudaStream_t st) {
+    if (!active) return;
+    cudaEventRecordWithFlags(pe.b, st, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    if (c->capturing) c->cap_prof.push_back(pe);
+    else c->pending.push_back(pe);
 }
 
 uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
@@ -225,6 +271,8 @@ bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
         for (int id : {SC_FS, SC_Q1, SC_Q2})
             if ((s = ensure_scratch(c, id, sizeof(double) * (size_t)B->extent)) != BTE_OK) return s;
     }
+    for (const Segment &sg : B->segs)
+        if (fused_dft_supported(c->tables[sg.table]->N)) fused_dft_prepare(c->tables[sg.table]->N);
     if (mode == BTE_FP64_PLAIN) {
         for (const Segment &sg : B->segs) {
             int r = build_table_fp64(*c->tables[sg.table], c->err);
@@ -232,36 +280,55 @@ bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
         }
     } else if (mode == BTE_FP32) {
         ConvLaunch L;
-        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, &L);
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
     }
     return BTE_OK;
 }
 
-// Enqueue Qt (raw) or Q = P Qt for the batch: f -> Q. Scratch must be ready.
-bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, bool project,
-                           cudaStream_t st) {
+// What happens after the inverse transform of a collide.
+enum Post { POST_RAW = 0, POST_PROJECT = 1, POST_STAGE1 = 2, POST_STAGE2 = 3 };
+
+// Enqueue the operator for the batch: f -> Q, then `post`:
+// RAW: Qt;  PROJECT: P Qt;  STAGE1: Q = P Qt and y = x + a Q;  STAGE2: Q = P Qt and
+// y += a (qp + Q). Scratch must be ready (prepare).
+bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, int post,
+                           const double *x, double *y, const double *qp, double a, cudaStream_t st) {
     const bool fp64 = mode == BTE_FP64_PLAIN;
+    ProfEntry pe_all{}, pe_conv{};
+    const int on_all = prof_begin(c, PK_COLLIDE, st, &pe_all);
     for (const Segment &sg : B->segs) {
         const Table *t = c->tables[sg.table];
         DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
         const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
-        if (fp64)
+        if (fp64) {
             launch_dft_forward<double2>(f, B->d_slot_off, ds, t->d_root64, sf, (double2 *)c->scratch[SC_T1],
                                         (double2 *)c->scratch[SC_T2], (double2 *)c->scratch[SC_F], c->d_status, st);
-        else
+            count_launches(c, 3);
+        } else if (fused_dft_supported(t->N)) {
+            launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status,
+                                     st);
+            count_launches(c, 1);
+        } else {
             launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
                                        (float2 *)c->scratch[SC_T2], (float2 *)c->scratch[SC_F], c->d_status, st);
+            count_launches(c, 3);
+        }
+        cudaError_t e0 = cudaGetLastError();
+        if (e0 != cudaSuccess) return cuda_fail(c, e0, "forward transform launch");
     }
     if (fp64) {
+        const int on = prof_begin(c, PK_CONV64, st, &pe_conv);
         for (const Segment &sg : B->segs) {
             const Table *t = c->tables[sg.table];
             launch_conv64((const double2 *)c->scratch[SC_F], (double2 *)c->scratch[SC_QH], t->d_w64, t->d_w64_off,
                           t->N, sg.eoff, sg.nslots / kLanes, st);
+            count_launches(c, 1);
         }
+        prof_end(c, on, pe_conv, st);
     } else {
         ConvLaunch L;
-        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, &L);
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
         ConvParams p{};
         p.items = B->d_items;
@@ -277,43 +344,93 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         p.merge = c->conv_merge;
         e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(c, e, "queue reset");
+        const int on = prof_begin(c, PK_CONV32, st, &pe_conv);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "before the convolution launch");
         e = conv32_launch(L, p, st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "convolution launch");
+        prof_end(c, on, pe_conv, st);
+        count_launches(c, 1);
+        if (e != cudaSuccess) {
+            char msg[256];
+            std::snprintf(msg, sizeof msg, "convolution launch (impl %d, grid %d, threads %d, smem %zu, items %d)",
+                          L.impl, L.grid, L.threads, L.smem, p.nitems);
+            return cuda_fail(c, e, msg);
+        }
     }
     for (const Segment &sg : B->segs) {
         const Table *t = c->tables[sg.table];
         DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
         const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
+        if (!fp64 && fused_dft_supported(t->N)) {
+            launch_dft_inverse_fused((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si, Q,
+                                     proj_args(t), post, x, y, qp, a, st);
+            count_launches(c, 1);
+            continue;
+        }
         if (fp64)
             launch_dft_inverse<double2>((const double2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root64, si,
                                         (double2 *)c->scratch[SC_T1], (double2 *)c->scratch[SC_T2], Q, st);
         else
             launch_dft_inverse<float2>((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si,
                                        (float2 *)c->scratch[SC_T1], (float2 *)c->scratch[SC_T2], Q, st);
-        if (project)
-            launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(t), 0, nullptr, nullptr, nullptr, 0.0, st);
+        count_launches(c, 3);
+        if (post != POST_RAW) {
+            launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(t), post - 1, x, y, qp, a, st);
+            count_launches(c, 1);
+        }
     }
+    prof_end(c, on_all, pe_all, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
     return BTE_OK;
 }
 
-// Heun step of the homogeneous problem on f (in place).
+// Heun step of the homogeneous problem on f (in place); the stage updates are
+// fused into the projection that ends each collide.
 bte_status enqueue_rk2(bte_ctx *c, Batch *B, double *f, double dt, double eps, int mode, cudaStream_t st) {
     double *fs = (double *)c->scratch[SC_FS];
     double *q1 = (double *)c->scratch[SC_Q1];
     double *q2 = (double *)c->scratch[SC_Q2];
-    bte_status s = enqueue_collide(c, B, f, q1, mode, false, st);
+    bte_status s = enqueue_collide(c, B, f, q1, mode, POST_STAGE1, f, fs, nullptr, dt / eps, st);
     if (s != BTE_OK) return s;
-    for (const Segment &sg : B->segs)
-        launch_project(q1, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 1, f, fs, nullptr,
-                       dt / eps, st);
-    if ((s = enqueue_collide(c, B, fs, q2, mode, false, st)) != BTE_OK) return s;
-    for (const Segment &sg : B->segs)
-        launch_project(q2, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 2, nullptr, f, q1,
-                       0.5 * dt / eps, st);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return enqueue_collide(c, B, fs, q2, mode, POST_STAGE2, nullptr, f, q1, 0.5 * dt / eps, st);
+}
+
+// Wall Maxwellian M_w(v) = (2 pi T_w)^{-3/2} exp(-|v|^2 / (2 T_w)) on the grid of table t
+// (FP64, host) and den = sum over the half entering the slab of |v.n| M_w
+// (side 0: left wall, n = +e1; side 1: right wall, n = -e1). Cached per (grid, T_w).
+bte_status wall_table(bte_ctx *c, const Table *t, double Tw, int side, const double **dptr, double *den) {
+    const auto key = std::make_tuple(t->N, t->dv, Tw);
+    auto it = c->walls.find(key);
+    const int N = t->N, M = N * N * N, h = N / 2;
+    if (it == c->walls.end()) {
+        std::vector<double> mw(M);
+        const double pref = std::pow(2.0 * kPi * Tw, -1.5);
+        for (int j = 0; j < M; ++j) {
+            const double v1 = t->dv * (j / (N * N) - h), v2 = t->dv * ((j / N) % N - h), v3 = t->dv * (j % N - h);
+            mw[j] = pref * std::exp(-(v1 * v1 + v2 * v2 + v3 * v3) / (2.0 * Tw));
+        }
+        double *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(double) * M);
+        if (e != cudaSuccess) return cuda_fail(c, e, "wall table allocation");
+        e = cudaMemcpy(d, mw.data(), sizeof(double) * M, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(c, e, "wall table upload");
+        }
+        WallTable w;
+        w.d = d;
+        w.host = std::move(mw);
+        it = c->walls.emplace(key, std::move(w)).first;
+    }
+    double sum = 0.0;
+    for (int j = 0; j < M; ++j) {
+        const double v1 = t->dv * (j / (N * N) - h);
+        const double vn = side == 0 ? v1 : -v1;
+        if (vn > 0.0) sum += vn * it->second.host[j];
+    }
+    *dptr = it->second.d;
+    *den = sum;
     return BTE_OK;
 }
 
@@ -354,7 +471,18 @@ void bte_destroy(bte_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto &kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto &pe : kv.second.prof) {
+            cudaEventDestroy(pe.a);
+            cudaEventDestroy(pe.b);
+        }
+    }
+    for (auto &pe : c->pending) c->ev_free.push_back({pe.a, pe.b});
+    for (auto &ab : c->ev_free) {
+        cudaEventDestroy(ab.first);
+        cudaEventDestroy(ab.second);
+    }
     for (auto &kv : c->batches) {
         cudaFree(kv.second->d_slot_off);
         cudaFree(kv.second->d_slot_out);
@@ -369,6 +497,7 @@ void bte_destroy(bte_ctx *c) {
     cudaFree(c->d_status);
     cudaFree(c->d_counter);
     cudaFree(c->d_wall);
+    for (auto &kv : c->walls) cudaFree(kv.second.d);
     delete c;
 }
 
@@ -407,7 +536,8 @@ bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_inst
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
     if ((s = prepare(c, B, mode, false, false)) != BTE_OK) return s;
-    return enqueue_collide(c, B, f, Q, mode, !(flags & BTE_FLAG_RAW), (cudaStream_t)stream);
+    return enqueue_collide(c, B, f, Q, mode, (flags & BTE_FLAG_RAW) ? POST_RAW : POST_PROJECT, nullptr, nullptr,
+                           nullptr, 0.0, (cudaStream_t)stream);
 }
 
 bte_status bte_collide(bte_ctx *c, const double *f, double *Q, const bte_instance *inst, int64_t ninst, int mode,
@@ -472,18 +602,28 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         ta.dx = (tr->x1 - tr->x0) / tr->nx;
         ta.bc_left = tr->bc_left;
         ta.bc_right = tr->bc_right;
-        ta.Tw_left = tr->Tw_left;
-        ta.Tw_right = tr->Tw_right;
+        if (ta.bc_left == BTE_BC_DIFFUSE &&
+            (s = wall_table(c, t0, tr->Tw_left, 0, &ta.mw_left, &ta.den_left)) != BTE_OK)
+            return s;
+        if (ta.bc_right == BTE_BC_DIFFUSE &&
+            (s = wall_table(c, t0, tr->Tw_right, 1, &ta.mw_right, &ta.den_right)) != BTE_OK)
+            return s;
     }
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
     if ((s = prepare(c, B, mode, true, tr != nullptr)) != BTE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     auto body = [&]() -> bte_status {
-        if (tr) launch_transport_half(f, (double *)c->scratch[SC_FS], c->d_wall, ta, 0.5 * dt, st);
+        if (tr) {
+            launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            count_launches(c, 2);
+        }
         bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st);
         if (r != BTE_OK) return r;
-        if (tr) launch_transport_half(f, (double *)c->scratch[SC_FS], c->d_wall, ta, 0.5 * dt, st);
+        if (tr) {
+            launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            count_launches(c, 2);
+        }
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "kernel launch");
     };
@@ -492,24 +632,119 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
                  tr ? 1 : 0, dt, eps, f, stream};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
+        prof_reserve(c, 8);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "stream capture");
+        c->capturing = true;
+        c->cap_launches = 0;
+        c->cap_prof.clear();
         bte_status r = body();
+        c->capturing = false;
         e = cudaStreamEndCapture(st, &g);
-        if (r != BTE_OK) {
+        GraphRec rec;
+        rec.prof = c->cap_prof;
+        rec.launches = c->cap_launches;
+        c->cap_prof.clear();
+        if (r != BTE_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
-            return r;
+            for (auto &pe : rec.prof) c->ev_free.push_back({pe.a, pe.b});
+            return r != BTE_OK ? r : cuda_fail(c, e, "stream capture end");
         }
-        if (e != cudaSuccess) return cuda_fail(c, e, "stream capture end");
-        cudaGraphExec_t ex = nullptr;
-        e = cudaGraphInstantiate(&ex, g, 0);
+        e = cudaGraphInstantiate(&rec.exec, g, 0);
         cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-        it = c->graphs.emplace(key, ex).first;
+        if (e != cudaSuccess) {
+            for (auto &pe : rec.prof) c->ev_free.push_back({pe.a, pe.b});
+            return cuda_fail(c, e, "graph instantiate");
+        }
+        it = c->graphs.emplace(key, rec).first;
     }
-    cudaError_t e = cudaGraphLaunch(it->second, st);
-    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "graph launch");
+    cudaError_t e = cudaGraphLaunch(it->second.exec, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->launches += it->second.launches;
+    for (const ProfEntry &pe : it->second.prof) c->pending.push_back(pe);
+    return BTE_OK;
+}
+
+bte_status bte_profile_enable(bte_ctx *c, int enable) {
+    if (!c) return BTE_EINVAL;
+    c->prof = enable != 0;
+    return BTE_OK;
+}
+
+bte_status bte_profile_read(bte_ctx *c, const char *kernel, int64_t *launches, double *total_ms, void *stream) {
+    if (!c || !kernel || !launches || !total_ms) return fail(c, BTE_EINVAL, "bte_profile_read: bad arguments");
+    int want = -1;
+    if (!std::strcmp(kernel, "conv32")) want = PK_CONV32;
+    else if (!std::strcmp(kernel, "conv64")) want = PK_CONV64;
+    else if (!std::strcmp(kernel, "collide")) want = PK_COLLIDE;
+    else if (std::strcmp(kernel, "*") != 0) return fail(c, BTE_EINVAL, "bte_profile_read: unknown kernel name");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+    int64_t n = 0;
+    double ms = 0.0;
+    // entries owned by graphs stay with the graphs; the others return to the pool
+    std::vector<cudaEvent_t> owned;
+    for (auto &kv : c->graphs)
+        for (auto &pe : kv.second.prof) owned.push_back(pe.a);
+    for (const ProfEntry &pe : c->pending) {
+        if (want < 0 || pe.kernel == want) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, pe.a, pe.b) == cudaSuccess) {
+                ms += t;
+                ++n;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        if (std::find(owned.begin(), owned.end(), pe.a) == owned.end()) c->ev_free.push_back({pe.a, pe.b});
+    }
+    c->pending.clear();
+    *launches = n;
+    *total_ms = ms;
+    return BTE_OK;
+}
+
+bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
+    if (!c || !count) return BTE_EINVAL;
+    *count = c->launches;
+    return BTE_OK;
+}
+
+static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
+    if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 2; return &c->conv_impl; }
+    if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
+    if (!std::strcmp(name, "conv_stages")) { *lo = 1; *hi = 4; return &c->conv_stages; }
+    if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
+    return nullptr;
+}
+
+bte_status bte_set_option(bte_ctx *c, const char *name, int value) {
+    if (!c || !name) return BTE_EINVAL;
+    int lo, hi;
+    int *slot = option_slot(c, name, &lo, &hi);
+    if (!slot) return fail(c, BTE_EINVAL, std::string("unknown option ") + name);
+    if (value < lo || value > hi) return fail(c, BTE_EINVAL, std::string("option out of range: ") + name);
+    if (*slot != value) {
+        cudaDeviceSynchronize();
+        for (auto &kv : c->graphs) {
+            cudaGraphExecDestroy(kv.second.exec);
+            for (auto &pe : kv.second.prof) c->ev_free.push_back({pe.a, pe.b});
+        }
+        c->graphs.clear();
+        c->pending.clear();
+        *slot = value;
+    }
+    return BTE_OK;
+}
+
+bte_status bte_get_option(const bte_ctx *c, const char *name, int *value) {
+    if (!c || !name || !value) return BTE_EINVAL;
+    int lo, hi;
+    int *slot = option_slot(const_cast<bte_ctx *>(c), name, &lo, &hi);
+    if (!slot) return BTE_EINVAL;
+    *value = *slot;
+    return BTE_OK;
 }
 
 bte_status bte_sync_status(bte_ctx *c, void *stream) {

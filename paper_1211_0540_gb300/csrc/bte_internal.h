@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bte.h"
@@ -87,6 +88,21 @@ struct GraphKey {
 
 struct Batch;  // device-side description of one instance layout (defined in api.cu)
 
+enum ProfKernel { PK_CONV32 = 0, PK_CONV64 = 1, PK_COLLIDE = 2 };
+struct ProfEntry {
+    int kernel;
+    cudaEvent_t a, b;
+};
+struct WallTable {
+    double *d = nullptr;       // device M_w per velocity
+    std::vector<double> host;  // same values on the host
+};
+struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ProfEntry> prof;  // events baked into the graph
+    int64_t launches = 0;         // kernels per replay
+};
+
 }  // namespace bte
 
 struct bte_ctx {
@@ -100,11 +116,20 @@ struct bte_ctx {
     void *scratch[8] = {nullptr};
     size_t scratch_bytes[8] = {0};
     std::map<std::string, bte::Batch *> batches;
-    std::map<bte::GraphKey, cudaGraphExec_t> graphs;
-    double *d_wall = nullptr;  // sigma_w of the diffuse walls (2 doubles)
-    int conv_warps = 8;        // warps per CTA of the convolution kernel
+    std::map<bte::GraphKey, bte::GraphRec> graphs;
+    // profiling / launch accounting
+    bool prof = false;
+    bool capturing = false;
+    std::vector<bte::ProfEntry> pending;       // direct launches and replays not yet read
+    std::vector<bte::ProfEntry> cap_prof;      // entries of the graph being captured
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_free;
+    int64_t launches = 0, cap_launches = 0;
+    double *d_wall = nullptr;  // unused scratch word pair
+    std::map<std::tuple<int, double, double>, bte::WallTable> walls;  // (N, dv, T_w) -> M_w
+    int conv_warps = 4;        // warps per CTA of the convolution kernel
     int conv_stages = 2;       // pipeline depth (weight/row blocks in flight per warp)
     int conv_merge = 4;        // blocks per compensated (TwoSum) merge
+    int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
 };
 
 namespace bte {

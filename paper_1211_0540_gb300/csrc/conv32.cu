@@ -265,6 +265,217 @@ __global__ void __launch_bounds__(256) conv32_kernel(ConvParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// v2: CTA-cooperative items and packed (f32x2) arithmetic.
+// All warps of a CTA work on the same item: warp w takes blocks w, w + W, ...
+// of the pencil through its own ring; the W partial (hi, lo) sums are then
+// reduced through shared memory in a fixed warp order (deterministic). This
+// keeps every warp of a resident CTA busy and turns the heavy-tailed pencil
+// costs into many balanced units. With PACKED, a pair costs three packed
+// instructions: p = (a.re, a.re) * (b.re, b.im) + (a.im, a.im) * (-b.im, b.re),
+// acc += (w, w) * p, which occupy the FP32 pipe as six scalar operations but
+// leave issue slots free for the shared loads and bookkeeping.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t pk2(float x, float y) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ float2 up2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+template <class K>
+__device__ __forceinline__ void conv_block_packed(const char *st, int lane, uint64_t (&part)[K::T]) {
+    const float2 *A = reinterpret_cast<const float2 *>(st);
+    const float2 *B = A + K::N * kLanes;
+    const float4 *W4 = reinterpret_cast<const float4 *>(B + K::N * kLanes);
+    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int wi = 0;
+#pragma unroll
+    for (int m3 = 0; m3 < K::N; ++m3) {
+        const float2 a = A[m3 * kLanes + lane];
+        const uint64_t aR = pk2(a.x, a.x), aI = pk2(a.y, a.y);
+#pragma unroll
+        for (int j = 0; j < K::T; ++j) {
+            const int n3 = K::K0 + j - m3 + K::H;
+            if (n3 >= 0 && n3 < K::N) {
+                if ((wi & 3) == 0) w4 = W4[wi >> 2];
+                const float w = (wi & 3) == 0 ? w4.x : (wi & 3) == 1 ? w4.y : (wi & 3) == 2 ? w4.z : w4.w;
+                ++wi;
+                const float2 b = B[n3 * kLanes + lane];
+                uint64_t pr = fmul2(aR, pk2(b.x, b.y));
+                pr = ffma2(aI, pk2(-b.y, b.x), pr);
+                part[j] = ffma2(pk2(w, w), pr, part[j]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void two_sum(float &hi, float &lo, float p) {
+    const float s = hi + p;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (p - bp);
+    hi = s;
+}
+
+// One item by all warps of the CTA. Returns false if this warp timed out.
+template <class K, bool PACKED>
+__device__ bool coop_item(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane, int warp,
+                          int nwarps, char *ring0) {
+    constexpr int T = K::T;
+    const int nb = (int)it.nblocks;
+    const int S = p.stages;
+    const int mine = nb > warp ? (nb - warp + nwarps - 1) / nwarps : 0;
+    if (lane == 0)
+        for (int s = 0; s < S && s < mine; ++s) issue_block<K>(r, s, it, p, warp + s * nwarps);
+    __syncwarp();
+
+    float hi[2 * T], lo[2 * T];
+    float part[2 * T];
+    uint64_t pp[T];
+#pragma unroll
+    for (int i = 0; i < 2 * T; ++i) hi[i] = lo[i] = part[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < T; ++i) pp[i] = 0ull;
+
+    bool ok = true;
+    int since = 0, i = 0;
+    for (; i < mine; ++i) {
+        const int s = i % S;
+        bool got = mbar_wait_bounded(r.bars + 8u * s, (r.phase >> s) & 1u);
+        got = __all_sync(0xffffffffu, got);
+        if (!got) {
+            ok = false;
+            break;
+        }
+        r.phase ^= (1u << s);
+        if (PACKED) conv_block_packed<K>(r.base + s * r.stage_bytes, lane, pp);
+        else conv_block<K>(r.base + s * r.stage_bytes, lane, part);
+        if (++since == p.merge || i == mine - 1) {
+            since = 0;
+            if (PACKED) {
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const float2 v = up2(pp[t]);
+                    two_sum(hi[2 * t], lo[2 * t], v.x);
+                    two_sum(hi[2 * t + 1], lo[2 * t + 1], v.y);
+                    pp[t] = 0ull;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2 * T; ++q) {
+                    two_sum(hi[q], lo[q], part[q]);
+                    part[q] = 0.f;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && i + S < mine) issue_block<K>(r, s, it, p, warp + (i + S) * nwarps);
+    }
+    if (!ok) {
+        const int last = mine < i + S ? mine : i + S;
+        for (int jj = i; jj < last; ++jj) {
+            const int s = jj % S;
+            if (mbar_wait_bounded(r.bars + 8u * s, (r.phase >> s) & 1u)) r.phase ^= (1u << s);
+        }
+        __syncwarp();
+    }
+    // partial sums of this warp into its own (drained) ring: [4T][32] floats
+    float *red = reinterpret_cast<float *>(r.base);
+#pragma unroll
+    for (int q = 0; q < 2 * T; ++q) {
+        red[q * kLanes + lane] = hi[q];
+        red[(2 * T + q) * kLanes + lane] = lo[q];
+    }
+    return ok;
+}
+
+// Cross-warp reduction of the partials (fixed warp order) and the store.
+template <class K>
+__device__ __forceinline__ void coop_reduce(const ConvItem &it, const ConvParams &p, int lane, int warp,
+                                            int nwarps, const char *ring0, int warp_smem) {
+    constexpr int T = K::T;
+    float2 *Q = p.Qh + it.fofs + ((size_t)(it.k1 * K::N + it.k2) * K::N + K::K0) * kLanes + lane;
+    for (int t = warp; t < T; t += nwarps) {
+        float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+        for (int w = 0; w < nwarps; ++w) {
+            const float *red = reinterpret_cast<const float *>(ring0 + (size_t)w * warp_smem);
+            two_sum(sr, lr, red[(2 * t) * kLanes + lane]);
+            lr += red[(2 * T + 2 * t) * kLanes + lane];
+            two_sum(si, li, red[(2 * t + 1) * kLanes + lane]);
+            li += red[(2 * T + 2 * t + 1) * kLanes + lane];
+        }
+        Q[t * kLanes] = make_float2(sr + lr, si + li);
+    }
+}
+
+template <class K, bool PACKED>
+__device__ __forceinline__ bool coop_run(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
+                                         int warp, int nwarps, char *ring0, int *abort_flag) {
+    const bool ok = coop_item<K, PACKED>(r, it, p, lane, warp, nwarps, ring0);
+    if (!ok && lane == 0) {
+        atomicOr(p.status, ST_TIMEOUT);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    if (!*abort_flag) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem);
+    __syncthreads();
+    // the rings are next written by TMA (async proxy) after these generic accesses
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    return !*abort_flag;
+}
+
+template <unsigned MASK, bool PACKED>
+__global__ void __launch_bounds__(128, 3) conv32_coop_kernel(ConvParams p) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ int s_item, s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    WarpRing r;
+    r.base = smem + (size_t)warp * p.warp_smem;
+    r.stage_bytes = p.warp_smem / p.stages;
+    r.bars = smem_u32(smem + (size_t)nwarps * p.warp_smem) + 8u * kMaxStages * warp;
+    r.phase = 0;
+    if (lane == 0) {
+        for (int s = 0; s < p.stages; ++s) mbar_init(r.bars + 8u * s, 1);
+        fence_mbar_init();
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.counter, 1u);
+        __syncthreads();
+        const int idx = s_item;
+        if (idx >= p.nitems || s_abort) break;
+        const ConvItem it = p.items[idx];
+        bool ok = true;
+        switch (it.kind) {
+            case 0: if (MASK & 1u) ok = coop_run<K8, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 1: if (MASK & 2u) ok = coop_run<K12, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 2: if (MASK & 4u) ok = coop_run<K16, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 3: if (MASK & 8u) ok = coop_run<K24a, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 4: if (MASK & 16u) ok = coop_run<K24b, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 5: if (MASK & 32u) ok = coop_run<K32a, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            case 6: if (MASK & 64u) ok = coop_run<K32b, PACKED>(r, it, p, lane, warp, nwarps, smem, &s_abort); break;
+            default: break;
+        }
+        if (!ok) break;
+    }
+}
+
 template <class K>
 constexpr int sb() { return K::stage_bytes; }
 
@@ -283,10 +494,10 @@ int conv_stage_bytes(int kind) {
     }
 }
 
-cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages,
+cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages, int impl,
                              ConvLaunch *out) {
-    static std::map<std::tuple<unsigned, int, int, int>, ConvLaunch> cache;
-    auto key = std::make_tuple(kinds_mask, num_sms, warps_per_cta, stages);
+    static std::map<std::tuple<unsigned, int, int, int, int>, ConvLaunch> cache;
+    auto key = std::make_tuple(kinds_mask, num_sms, warps_per_cta, stages, impl);
     auto itc = cache.find(key);
     if (itc != cache.end()) {
         *out = itc->second;
@@ -299,24 +510,48 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     L.stages = stages < 1 ? 1 : (stages > kMaxStages ? kMaxStages : stages);
     L.warp_smem = stage * L.stages;
     const int max_smem = 227 * 1024;
-    int warps = warps_per_cta < 1 ? 1 : (warps_per_cta > 8 ? 8 : warps_per_cta);
+    const int max_warps = impl == 0 ? 8 : 4;
+    int warps = warps_per_cta < 1 ? 1 : (warps_per_cta > max_warps ? max_warps : warps_per_cta);
     while (warps > 1 && warps * (L.warp_smem + 8 * kMaxStages) > max_smem) --warps;
     L.threads = warps * 32;
     L.smem = (size_t)warps * (L.warp_smem + 8 * kMaxStages);
-    switch (kinds_mask) {
-        case 1u: L.fn = conv32_kernel<1u>; break;
-        case 2u: L.fn = conv32_kernel<2u>; break;
-        case 4u: L.fn = conv32_kernel<4u>; break;
-        case 8u | 16u: L.fn = conv32_kernel<24u>; break;
-        case 32u | 64u: L.fn = conv32_kernel<96u>; break;
-        default: L.fn = conv32_kernel<127u>; break;
+    if (impl == 0) {
+        switch (kinds_mask) {
+            case 1u: L.fn = conv32_kernel<1u>; break;
+            case 2u: L.fn = conv32_kernel<2u>; break;
+            case 4u: L.fn = conv32_kernel<4u>; break;
+            case 8u | 16u: L.fn = conv32_kernel<24u>; break;
+            case 32u | 64u: L.fn = conv32_kernel<96u>; break;
+            default: L.fn = conv32_kernel<127u>; break;
+        }
+    } else {
+        const bool packed = impl == 2;
+#define BTE_PICK(M) L.fn = packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>
+        switch (kinds_mask) {
+            case 1u: BTE_PICK(1u); break;
+            case 2u: BTE_PICK(2u); break;
+            case 4u: BTE_PICK(4u); break;
+            case 8u | 16u: BTE_PICK(24u); break;
+            case 32u | 64u: BTE_PICK(96u); break;
+            default: BTE_PICK(127u); break;
+        }
+#undef BTE_PICK
     }
-    cudaError_t e = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
-    if (e != cudaSuccess) return e;
+    // the attribute belongs to the function and is shared by every cached
+    // configuration of it: only ever raise it
+    static std::map<void *, size_t> fn_smem;
+    size_t &cur = fn_smem[(void *)L.fn];
+    if (L.smem > cur) {
+        cudaError_t e0 = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+        if (e0 != cudaSuccess) return e0;
+        cur = L.smem;
+    }
+    cudaError_t e = cudaSuccess;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L.fn, L.threads, L.smem);
     if (e != cudaSuccess) return e;
     L.grid = num_sms * (per_sm < 1 ? 1 : per_sm);
+    L.impl = impl;
     cache[key] = L;
     *out = L;
     return cudaSuccess;
@@ -327,9 +562,9 @@ cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p0, cudaStream_
     p.stages = L.stages;
     p.warp_smem = L.warp_smem;
     if (p.merge < 1) p.merge = 1;
-    const int warps = L.threads / 32;
+    const int per_cta = L.impl == 0 ? L.threads / 32 : 1;  // items in flight per CTA
     int grid = L.grid;
-    if ((int64_t)grid * warps > p.nitems) grid = (p.nitems + warps - 1) / warps;
+    if ((int64_t)grid * per_cta > p.nitems) grid = (p.nitems + per_cta - 1) / per_cta;
     if (grid < 1) grid = 1;
     L.fn<<<grid, L.threads, L.smem, st>>>(p);
     return cudaGetLastError();

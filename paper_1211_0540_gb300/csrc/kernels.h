@@ -14,6 +14,14 @@ struct DftSeg {
     int64_t eoff;  // complex-element offset of slot s0 in scratch / group buffers
 };
 
+// Projection (Sec. 3.3), optionally fused with the RK2 update:
+// mode 0: Q <- P Q;  mode 1: Q <- P Q, Y <- X + a Q;  mode 2: Q <- P Q, Y <- Y + a (Qp + Q).
+struct ProjArgs {
+    int N;
+    double dv;
+    double ainv[25];
+};
+
 template <typename C>
 void launch_dft_forward(const double *f, const int64_t *slot_off, const DftSeg &s, const C *root,
                         double scale, C *T1, C *T2, C *G, int *status, cudaStream_t st);
@@ -39,12 +47,13 @@ struct ConvParams {
 int conv_stage_bytes(int kind);
 struct ConvLaunch {
     void (*fn)(ConvParams);
-    int grid, threads, stages, warp_smem;
+    int grid, threads, stages, warp_smem, impl;
     size_t smem;
 };
 // kinds_mask: bit i set when items of kind i are present. Sets the kernel's
 // shared-memory attribute: call outside stream capture.
-cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages,
+// impl: 0 = one warp per item, 1 = CTA-cooperative items, 2 = cooperative + packed f32x2.
+cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages, int impl,
                              ConvLaunch *out);
 cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t st);
 
@@ -52,27 +61,31 @@ cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t
 void launch_conv64(const double2 *F, double2 *Qh, const double *W, const uint64_t *Woff, int N,
                    int64_t eoff, int ngroups, cudaStream_t st);
 
-// Projection (Sec. 3.3), optionally fused with the RK2 update:
-// mode 0: Q <- P Q;  mode 1: Q <- P Q, Y <- X + a Q;  mode 2: Q <- P Q, Y <- Y + a (Qp + Q).
-struct ProjArgs {
-    int N;
-    double dv;
-    double ainv[25];
-};
 void launch_project(double *Q, const int64_t *slot_off, int s0, int nslots, const ProjArgs &pa,
                     int mode, const double *X, double *Y, const double *Qp, double a,
                     cudaStream_t st);
 void launch_moments(const double *f, const int64_t *slot_off, int s0, int nslots, int N, double dv,
                     const int64_t *slot_out, double *out, cudaStream_t st);
 
-// Transport (Sec. 3.4) on nx uniform cells of M values.
+// Fused single-kernel transforms for N in {8, 12, 16} (dft_fused.cu).
+// Inverse mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q).
+bool fused_dft_supported(int N);
+void fused_dft_prepare(int N);  // outside stream capture
+void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
+                              double scale, float2 *G, int *status, cudaStream_t st);
+void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root,
+                              double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
+                              const double *qp, double a, cudaStream_t st);
+
+// Transport (Sec. 3.4) on nx uniform cells of M values. mw_*: wall Maxwellians
+// per velocity (device, M doubles), den_*: sum over the incoming half of |v.n| M_w.
 struct TransportArgs {
     int N, nx;
     double dv, dx;
     int bc_left, bc_right;
-    double Tw_left, Tw_right;
+    const double *mw_left, *mw_right;
+    double den_left, den_right;
 };
-void launch_transport_half(double *f, double *f1, double *wall, const TransportArgs &ta, double tau,
-                           cudaStream_t st);
+void launch_transport_half(double *f, double *f1, const TransportArgs &ta, double tau, cudaStream_t st);
 
 }  // namespace bte

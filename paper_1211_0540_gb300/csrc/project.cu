@@ -4,44 +4,19 @@
 // its minimisation problem is the form above, which is what is computed.) The
 // dv^3 factors cancel, so the kernel uses c_j = (1, v1, v2, v3, |v|^2) and the
 // host-inverted 5x5 matrix A^{-1}, A = sum_j c_j c_j^T.
-// One CTA per cell: the five moment sums are reduced in a fixed order (warp
-// shuffles, then shared memory), so results are deterministic. The kernel can
-// fuse the Heun update of the time step that consumes the projected Q.
-#include "kernels.h"
+//
+// FP64 is slow on this GPU, so the moments use the tensor structure of c_j:
+// with r = sum over j1 of Q, u = sum of v1 Q, w = sum of v1^2 Q taken along the
+// j1 line through each (j2, j3),
+//   mu0 = sum r, mu1 = sum u, mu2 = sum v2 r, mu3 = sum v3 r,
+//   mu4 = sum (w + (v2^2 + v3^2) r),
+// three FP64 operations per value; the correction c_j . lambda splits into a
+// per-(j2, j3) base plus a per-j1 term, two operations per value. One CTA per
+// cell; sums are reduced in a fixed order (deterministic). The same routine
+// runs inside the fused inverse transform (dft_fused.cu).
+#include "project.cuh"
 
 namespace bte {
-
-namespace {
-constexpr int kProjThreads = 256;
-
-__device__ __forceinline__ void cvec(int j, int N, double dv, double c[5]) {
-    const int h = N / 2;
-    const double v1 = dv * (j / (N * N) - h), v2 = dv * ((j / N) % N - h), v3 = dv * (j % N - h);
-    c[0] = 1.0;
-    c[1] = v1;
-    c[2] = v2;
-    c[3] = v3;
-    c[4] = v1 * v1 + v2 * v2 + v3 * v3;
-}
-
-// Block-wide deterministic sum of 5 values; result valid in all threads.
-__device__ __forceinline__ void block_sum5(double v[5]) {
-    __shared__ double red[kProjThreads / 32][5];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int i = 0; i < 5; ++i)
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
-    if (lane == 0)
-        for (int i = 0; i < 5; ++i) red[warp][i] = v[i];
-    __syncthreads();
-    for (int i = 0; i < 5; ++i) {
-        double s = 0.0;
-        for (int w = 0; w < kProjThreads / 32; ++w) s += red[w][i];
-        v[i] = s;
-    }
-    __syncthreads();
-}
-}  // namespace
 
 __global__ void __launch_bounds__(kProjThreads)
 project_kernel(double *__restrict__ Q, const int64_t *__restrict__ slot_off, int s0, ProjArgs pa,
@@ -49,52 +24,21 @@ project_kernel(double *__restrict__ Q, const int64_t *__restrict__ slot_off, int
                const double *__restrict__ Qp, double a) {
     const int64_t off = slot_off[s0 + blockIdx.x];
     if (off < 0) return;
-    const int N = pa.N, M = N * N * N;
-    double *q = Q + off;
-    double mu[5] = {0, 0, 0, 0, 0}, c[5];
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        cvec(j, N, pa.dv, c);
-        const double x = q[j];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) mu[i] += c[i] * x;
-    }
-    block_sum5(mu);
-    double lam[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < 5; ++k) s += pa.ainv[i * 5 + k] * mu[k];
-        lam[i] = s;
-    }
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        cvec(j, N, pa.dv, c);
-        double corr = 0.0;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) corr += c[i] * lam[i];
-        const double v = q[j] - corr;
-        q[j] = v;
-        if (mode == 1) Y[off + j] = X[off + j] + a * v;
-        else if (mode == 2) Y[off + j] += a * (Qp[off + j] + v);
-    }
+    __shared__ ProjShared sh;
+    project_cell(Q + off, Q + off, pa, mode, X ? X + off : nullptr, Y ? Y + off : nullptr,
+                 Qp ? Qp + off : nullptr, a, sh);
 }
 
 __global__ void __launch_bounds__(kProjThreads)
-moments_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, int s0, int N,
-               double dv, const int64_t *__restrict__ slot_out, double *__restrict__ out) {
+moments_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, int s0, ProjArgs pa,
+               const int64_t *__restrict__ slot_out, double *__restrict__ out) {
     const int64_t off = slot_off[s0 + blockIdx.x];
     if (off < 0) return;
-    const int M = N * N * N;
-    double mu[5] = {0, 0, 0, 0, 0}, c[5];
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        cvec(j, N, dv, c);
-        const double x = f[off + j];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) mu[i] += c[i] * x;
-    }
-    block_sum5(mu);
+    __shared__ ProjShared sh;
+    double mu[5];
+    cell_moments(f + off, pa, mu, sh);
     if (threadIdx.x == 0) {
-        const double w = dv * dv * dv;
+        const double w = pa.dv * pa.dv * pa.dv;
         const int64_t o = slot_out[s0 + blockIdx.x];
         for (int i = 0; i < 5; ++i) out[5 * o + i] = w * mu[i];
     }
@@ -108,7 +52,10 @@ void launch_project(double *Q, const int64_t *slot_off, int s0, int nslots, cons
 
 void launch_moments(const double *f, const int64_t *slot_off, int s0, int nslots, int N, double dv,
                     const int64_t *slot_out, double *out, cudaStream_t st) {
-    moments_kernel<<<nslots, kProjThreads, 0, st>>>(f, slot_off, s0, N, dv, slot_out, out);
+    ProjArgs pa{};
+    pa.N = N;
+    pa.dv = dv;
+    moments_kernel<<<nslots, kProjThreads, 0, st>>>(f, slot_off, s0, pa, slot_out, out);
 }
 
 }  // namespace bte

@@ -67,10 +67,19 @@ def run_collide(bte, N, lam, f, mode, raw=False):
     return Q.cpu().numpy().reshape(f.shape)
 
 
-@pytest.mark.parametrize("N,ncells,lam", [(8, 5, 1.0), (8, 70, 0.0), (12, 37, 1.0), (16, 33, 1.0)])
-def test_fp32_collide_matches_oracle(bte, N, ncells, lam):
+@pytest.mark.parametrize("impl", [0, 1, 2])
+@pytest.mark.parametrize("N,ncells,lam", [(8, 5, 1.0), (8, 70, 0.0), (12, 37, 1.0), (16, 33, 1.0),
+                                          (24, 3, 1.0)])
+def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
     f = inputs.homogeneous_cells(N, L, ncells, seed=100 + N + ncells)
-    Qg = run_collide(bte, N, lam, f, bte.FP32)
+    c = ctx_for(bte, ((N, L, lam),))
+    c.set_option("conv_impl", impl)
+    c.set_option("conv_merge", 1 + impl)
+    try:
+        Qg = run_collide(bte, N, lam, f, bte.FP32)
+    finally:
+        c.set_option("conv_impl", 2)
+        c.set_option("conv_merge", 4)
     Qo = oracle.collide(N, L, lam, f)
     err = np.linalg.norm(Qg - Qo, axis=1) / loss_norm(N, lam, f)
     assert err.max() <= TOL32, err.max()
@@ -246,3 +255,31 @@ def test_full_size_workloads_on_sampled_cells(bte, N, ncells, nsample, seed):
     assert err.max() <= TOL32, err
     mom = oracle.moments(N, L, Qg)
     assert np.all(np.abs(mom) <= 1e-12 * abs_moment_scale(N, Qg))
+
+
+def test_profiling_and_launch_count_with_graphs(bte):
+    """Events around the convolution are recorded also inside captured graphs,
+    and no stale CUDA error is left behind for the caller's runtime."""
+    N = 8
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.profile_enable(True)
+    f = torch.from_numpy(inputs.homogeneous_cells(N, L, 40, seed=2)).cuda()
+    s = torch.cuda.Stream()
+    n0 = c.launch_count()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            c.step(f, 0.01, 1.0, stream=s)
+    n, ms = c.profile_read("conv32", s)
+    assert n == 6 and ms > 0.0
+    # per step: 2 x (fused forward DFT + convolution + fused inverse DFT with projection)
+    assert c.launch_count() - n0 == 3 * 6
+    c.collide(f, stream=s)
+    n, ms = c.profile_read("collide", s)
+    assert n == 1 and ms > 0.0
+    x = torch.ones(4, device="cuda") * 2  # a torch launch must not pick up an error of ours
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 8.0
+    c.sync_status(s)
+    c.close()
