@@ -178,6 +178,35 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
+/* Size of the static device work area used by bte_collide_noalloc (16 MiB). */
+#define BTE_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* bte_collide_noalloc — the FP32 collision operator (as bte_collide with
+ * mode BTE_FP32, inst == NULL: ncells uniform cells of table 0, projected Q)
+ * for callers that cannot allocate GPU memory while they run: code that works
+ * inside a fixed memory budget handed out up front (an embedding application's
+ * own arena, or a device whose memory is already reserved by another
+ * allocator), or a time-critical loop that must not pay for, or be
+ * synchronised by, cudaMalloc/cudaFree. The paper has no counterpart; this is
+ * a service of the library.
+ * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine, no host heap. Its work area (queue counter, per-cell
+ * offsets, work list, fhat and Qhat) is one file-scope device array of
+ * BTE_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
+ * the process exits. The caller passes f and Q (device, ncells * N^3 doubles);
+ * the weight tables must have been built before (bte_init_weights, set-up).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Every call shares the array and leaves its contents
+ * behind; each call resets what must start at zero. Calls that overlap on the
+ * GPU (two streams, or two threads) race on the array: serialise them. The
+ * call uploads its work list and synchronises `stream` once before launching.
+ * Limits: table 0 must have N = 8, 12 or 16; the cells must fit the array
+ * (2 * ceil(ncells/32) * 32 * N^3 * 8 bytes of work arrays plus the work list):
+ * up to 224 cells at N = 16, 576 at N = 12, 2016 at N = 8. Larger requests fail with BTE_EINVAL and a message
+ * naming the bytes needed. Errors: BTE_EINVAL, BTE_ESTATE, BTE_ECUDA. */
+bte_status bte_collide_noalloc(bte_ctx *ctx, const double *f, double *Q, int64_t ncells, void *stream);
+
 /* Library build identification (static string). */
 const char *bte_version(void);
 

@@ -25,7 +25,7 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
-           "bte_set_option", "bte_get_option"]
+           "bte_set_option", "bte_get_option", "bte_collide_noalloc"]
 
 
 class Grid(ctypes.Structure):
@@ -84,6 +84,7 @@ def load(path=None):
         "bte_launch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
         "bte_set_option": (c_int, [vp, ctypes.c_char_p, c_int]),
         "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
+        "bte_collide_noalloc": (c_int, [vp, vp, vp, c_i64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
