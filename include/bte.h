@@ -178,6 +178,17 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
+/* BF16 GEMM on the tensor cores (tcgen05 + TMA), the building block of the
+ * learned surrogate's training and inference:
+ *   D[M, N] = A[M, K] . B[N, K]^T (+ bias[N]),  A, B: device bf16, row-major with K
+ *   contiguous; FP32 accumulation. Outputs (each optional, device): D (FP32,
+ *   [M][N], before the activation), D_bf16 ([M][N]) and D_bf16_t (transposed,
+ *   [N][ld_t], ld_t >= M), both after GELU when gelu != 0 (tanh form).
+ * Requirements: K % 64 == 0, N % 64 == 0 (M is free). Asynchronous.
+ * Errors: BTE_EINVAL (shapes), BTE_ECUDA. */
+bte_status bte_tc_gemm(bte_ctx *ctx, const void *A, const void *B, float *D, int M, int N, int K,
+                       const float *bias, int gelu, void *D_bf16, void *D_bf16_t, int ld_t, void *stream);
+
 /* Size of the static device work area used by bte_collide_noalloc (16 MiB). */
 #define BTE_NOALLOC_SCRATCH_BYTES (16u << 20)
 

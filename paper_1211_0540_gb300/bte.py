@@ -25,7 +25,7 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
-           "bte_set_option", "bte_get_option", "bte_collide_noalloc"]
+           "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm"]
 
 
 class Grid(ctypes.Structure):
@@ -85,6 +85,7 @@ def load(path=None):
         "bte_set_option": (c_int, [vp, ctypes.c_char_p, c_int]),
         "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
         "bte_collide_noalloc": (c_int, [vp, vp, vp, c_i64, vp]),
+        "bte_tc_gemm": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, vp, c_int, vp, vp, c_int, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -221,6 +222,25 @@ class Context:
         v = ctypes.c_int()
         self._rc(self._lib.bte_get_option(self._h, name.encode(), ctypes.byref(v)), "bte_get_option")
         return v.value
+
+    def tc_gemm(self, A, B, bias=None, gelu=False, out_f32=True, out_bf16=False, out_bf16_t=False,
+                stream=None):
+        """D = A B^T (+ bias) on the tensor cores; A [M, K], B [N, K] bf16 CUDA tensors.
+        Returns (D fp32 or None, D bf16 or None, D^T bf16 or None)."""
+        import torch
+        M, K = A.shape
+        N = B.shape[0]
+        D = torch.empty((M, N), dtype=torch.float32, device=A.device) if out_f32 else None
+        Db = torch.empty((M, N), dtype=torch.bfloat16, device=A.device) if out_bf16 else None
+        Dt = torch.zeros((N, M), dtype=torch.bfloat16, device=A.device) if out_bf16_t else None
+        vp = ctypes.c_void_p
+        self._rc(self._lib.bte_tc_gemm(self._h, vp(A.data_ptr()), vp(B.data_ptr()),
+                                       vp(D.data_ptr()) if D is not None else None, M, N, K,
+                                       vp(bias.data_ptr()) if bias is not None else None, int(gelu),
+                                       vp(Db.data_ptr()) if Db is not None else None,
+                                       vp(Dt.data_ptr()) if Dt is not None else None, M,
+                                       _stream(stream)), "bte_tc_gemm")
+        return D, Db, Dt
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))
