@@ -59,7 +59,8 @@ typedef enum {
 typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1 } bte_bc;
 
 /* bte_collide_ex flags */
-#define BTE_FLAG_RAW 1u        /* return Qt (skip the conservation projection)   */
+#define BTE_FLAG_RAW 1u          /* return Qt (skip the conservation projection)  */
+#define BTE_FLAG_NO_FALLBACK 2u  /* BTE_LEARNED: projected surrogate output only  */
 
 /* Velocity grid and collision kernel of one weight table: B = |u|^lambda / (4 pi)
  * (isotropic, Sec. 2.2). lambda = 0: Maxwell molecules, 1: hard spheres. */
@@ -118,7 +119,16 @@ bte_status bte_init_weights(bte_ctx *ctx, const bte_grid *grids, int ngrids, int
 bte_status bte_collide(bte_ctx *ctx, const double *f, double *Q, const bte_instance *inst,
                        int64_t ninst, int mode, void *stream);
 
-/* bte_collide with flags (BTE_FLAG_RAW returns the unprojected Qt). */
+/* bte_collide with flags (BTE_FLAG_RAW returns the unprojected Qt).
+ * Mode BTE_LEARNED (uniform cells of table 0, surrogate built with
+ * bte_mlp_init): Q = P_N(Q_nn) from the surrogate, then a residual indicator
+ * per cell: the exact operator is evaluated at 64 sampled Fourier modes
+ * (seeded, |k'|_inf <= N/4, zeta != 0) and
+ *   ind = ||F[Q](zeta_s) - Qhat(zeta_s)|| / ||Qhat_loss(zeta_s)||
+ * (Qhat_loss: the same sum with the loss term of Ghat only). Cells with ind
+ * above the option "learned_tol_ppm" * 1e-6 (default 1e-2) are recomputed with
+ * the FP32 operator. Synchronises `stream` once. BTE_FLAG_NO_FALLBACK skips
+ * the indicator. Counts: bte_learned_stats. */
 bte_status bte_collide_ex(bte_ctx *ctx, const double *f, double *Q, const bte_instance *inst,
                           int64_t ninst, int mode, unsigned flags, void *stream);
 
@@ -173,7 +183,8 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
  *       "conv_stages" blocks in flight per warp (1..4);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
- *                      (TwoSum) merges (>= 1).
+ *                      (TwoSum) merges (>= 1);
+ *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units.
  * Changing an option drops the captured step graphs. Errors: BTE_EINVAL. */
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
@@ -188,6 +199,39 @@ bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
  * Errors: BTE_EINVAL (shapes), BTE_ECUDA. */
 bte_status bte_tc_gemm(bte_ctx *ctx, const void *A, const void *B, float *D, int M, int N, int K,
                        const float *bias, int gelu, void *D_bf16, void *D_bf16_t, int ld_t, void *stream);
+
+/* Learned surrogate of the collision operator (no counterpart in the paper: a
+ * residual MLP trained on (f, Q(f)) pairs that the operator itself produces):
+ *   x = s_in f / rho, h1 = GELU(W1 x + b1), h2 = h1 + GELU(W2 h1 + b2),
+ *   y = W3 h2 + b3, Q_nn = rho^2 y / s_out   (rho = sum f dv^3; Q is bilinear),
+ * GELU in tanh form; BF16 weights/activations on the tensor cores, FP32
+ * accumulation, FP32 master weights and AdamW. Parameters are one flat FP32
+ * vector: W1 [H][M], b1 [H], W2 [H][H], b2 [H], W3 [M][H], b3 [M] (M = N^3).
+ * bte_mlp_init: create it for weight table `table` (N^3 % 64 == 0, N <= 16),
+ *   width H (multiple of 128), seeded initialisation. Synchronous.
+ * bte_mlp_train: `epochs` passes over nsamples device pairs (f[i], Q[i]) (FP64,
+ *   M values each, back to back), mini-batches of `batch`, AdamW (lr with cosine
+ *   decay to lr/20, weight decay). *final_loss: mean square error of the last batch.
+ * bte_mlp_grads: one forward/backward on the first n pairs without an update;
+ *   copies the gradient (nparams floats) to host_grads and the loss to *loss.
+ * bte_mlp_infer: Q_nn for n cells (device FP64; no projection).
+ * bte_mlp_get/set_params: host FP32 vector of nparams values.
+ * The surrogate is used by bte_collide with mode BTE_LEARNED (projection and
+ * fallback there). Errors: BTE_EINVAL, BTE_ESTATE (no surrogate), BTE_ENOMEM, BTE_ECUDA. */
+bte_status bte_mlp_init(bte_ctx *ctx, int table, int width, uint64_t seed);
+bte_status bte_mlp_info(const bte_ctx *ctx, int64_t *nparams, int *width, int *ndim, double *s_in, double *s_out);
+bte_status bte_mlp_set_scales(bte_ctx *ctx, double s_in, double s_out);
+bte_status bte_mlp_get_params(bte_ctx *ctx, float *host, int64_t n);
+bte_status bte_mlp_set_params(bte_ctx *ctx, const float *host, int64_t n);
+bte_status bte_mlp_train(bte_ctx *ctx, const double *f, const double *Q, int64_t nsamples, int epochs, int batch,
+                         double lr, double weight_decay, uint64_t seed, double *final_loss, void *stream);
+bte_status bte_mlp_grads(bte_ctx *ctx, const double *f, const double *Q, int64_t n, double *loss, float *host_grads,
+                         void *stream);
+bte_status bte_mlp_infer(bte_ctx *ctx, const double *f, double *Q, int64_t n, void *stream);
+
+/* Cells evaluated and recomputed by the learned mode since the last reset, and
+ * the largest indicator seen. */
+bte_status bte_learned_stats(bte_ctx *ctx, int64_t *cells, int64_t *fallbacks, double *max_indicator, int reset);
 
 /* Size of the static device work area used by bte_collide_noalloc (16 MiB). */
 #define BTE_NOALLOC_SCRATCH_BYTES (16u << 20)

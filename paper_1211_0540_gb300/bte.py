@@ -17,6 +17,7 @@ LEARNED = 2
 BC_DIFFUSE = 0
 BC_SPECULAR = 1
 FLAG_RAW = 1
+FLAG_NO_FALLBACK = 2
 
 STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: "BTE_ETIMEOUT",
           -5: "BTE_ENONFINITE", -6: "BTE_ESTATE"}
@@ -25,7 +26,9 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
-           "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm"]
+           "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
+           "bte_mlp_set_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
+           "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats"]
 
 
 class Grid(ctypes.Structure):
@@ -86,6 +89,18 @@ def load(path=None):
         "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
         "bte_collide_noalloc": (c_int, [vp, vp, vp, c_i64, vp]),
         "bte_tc_gemm": (c_int, [vp, vp, vp, vp, c_int, c_int, c_int, vp, c_int, vp, vp, c_int, vp]),
+        "bte_mlp_init": (c_int, [vp, c_int, c_int, ctypes.c_uint64]),
+        "bte_mlp_info": (c_int, [vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_d), ctypes.POINTER(c_d)]),
+        "bte_mlp_set_scales": (c_int, [vp, c_d, c_d]),
+        "bte_mlp_get_params": (c_int, [vp, vp, c_i64]),
+        "bte_mlp_set_params": (c_int, [vp, vp, c_i64]),
+        "bte_mlp_train": (c_int, [vp, vp, vp, c_i64, c_int, c_int, c_d, c_d, ctypes.c_uint64,
+                                  ctypes.POINTER(c_d), vp]),
+        "bte_mlp_grads": (c_int, [vp, vp, vp, c_i64, ctypes.POINTER(c_d), vp, vp]),
+        "bte_mlp_infer": (c_int, [vp, vp, vp, c_i64, vp]),
+        "bte_learned_stats": (c_int, [vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_d),
+                                      c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -158,16 +173,23 @@ class Context:
         arr = (Instance * len(inst))(*[Instance(int(t), 0, int(o)) for (t, o) in inst])
         return arr, len(inst)
 
-    def collide(self, f, Q=None, inst=None, mode=FP32, raw=False, stream=None):
+    def collide(self, f, Q=None, inst=None, mode=FP32, raw=False, fallback=True, stream=None):
         _check_f64(f, "f")
         if Q is None:
             import torch
             Q = torch.empty_like(f)
         _check_f64(Q, "Q")
         arr, n = self._inst(inst, f)
-        self._rc(self._lib.bte_collide_ex(self._h, _ptr(f), _ptr(Q), arr, n, int(mode),
-                                          FLAG_RAW if raw else 0, _stream(stream)), "bte_collide")
+        flags = (FLAG_RAW if raw else 0) | (0 if fallback else FLAG_NO_FALLBACK)
+        self._rc(self._lib.bte_collide_ex(self._h, _ptr(f), _ptr(Q), arr, n, int(mode), flags,
+                                          _stream(stream)), "bte_collide")
         return Q
+
+    def learned_stats(self, reset=False):
+        a, b, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        self._rc(self._lib.bte_learned_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(d),
+                                             int(bool(reset))), "bte_learned_stats")
+        return dict(cells=a.value, fallbacks=b.value, max_indicator=d.value)
 
     def project(self, Q, inst=None, stream=None):
         _check_f64(Q, "Q")
@@ -241,6 +263,66 @@ class Context:
                                        vp(Dt.data_ptr()) if Dt is not None else None, M,
                                        _stream(stream)), "bte_tc_gemm")
         return D, Db, Dt
+
+    # ---- learned surrogate ----
+    def mlp_init(self, table=0, width=1024, seed=0):
+        self._rc(self._lib.bte_mlp_init(self._h, int(table), int(width), int(seed)), "bte_mlp_init")
+
+    def mlp_info(self):
+        n, w, d = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        si, so = ctypes.c_double(), ctypes.c_double()
+        self._rc(self._lib.bte_mlp_info(self._h, ctypes.byref(n), ctypes.byref(w), ctypes.byref(d),
+                                        ctypes.byref(si), ctypes.byref(so)), "bte_mlp_info")
+        return dict(nparams=n.value, width=w.value, ndim=d.value, s_in=si.value, s_out=so.value)
+
+    def mlp_set_scales(self, s_in, s_out):
+        self._rc(self._lib.bte_mlp_set_scales(self._h, float(s_in), float(s_out)), "bte_mlp_set_scales")
+
+    def mlp_get_params(self):
+        import numpy as np
+        n = self.mlp_info()["nparams"]
+        out = np.empty(n, dtype=np.float32)
+        self._rc(self._lib.bte_mlp_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p), n),
+                 "bte_mlp_get_params")
+        return out
+
+    def mlp_set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._rc(self._lib.bte_mlp_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p), p.size),
+                 "bte_mlp_set_params")
+
+    def mlp_train(self, f, Q, epochs=1, batch=1024, lr=1e-3, weight_decay=0.0, seed=0, stream=None):
+        _check_f64(f, "f")
+        _check_f64(Q, "Q")
+        n = f.numel() // self.mlp_info()["ndim"]
+        loss = ctypes.c_double()
+        self._rc(self._lib.bte_mlp_train(self._h, _ptr(f), _ptr(Q), n, int(epochs), int(batch), float(lr),
+                                         float(weight_decay), int(seed), ctypes.byref(loss),
+                                         _stream(stream)), "bte_mlp_train")
+        return loss.value
+
+    def mlp_grads(self, f, Q, stream=None):
+        import numpy as np
+        _check_f64(f, "f")
+        _check_f64(Q, "Q")
+        info = self.mlp_info()
+        n = f.numel() // info["ndim"]
+        g = np.empty(info["nparams"], dtype=np.float32)
+        loss = ctypes.c_double()
+        self._rc(self._lib.bte_mlp_grads(self._h, _ptr(f), _ptr(Q), n, ctypes.byref(loss),
+                                         g.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+                 "bte_mlp_grads")
+        return loss.value, g
+
+    def mlp_infer(self, f, Q=None, stream=None):
+        import torch
+        _check_f64(f, "f")
+        if Q is None:
+            Q = torch.empty_like(f)
+        n = f.numel() // self.mlp_info()["ndim"]
+        self._rc(self._lib.bte_mlp_infer(self._h, _ptr(f), _ptr(Q), n, _stream(stream)), "bte_mlp_infer")
+        return Q
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

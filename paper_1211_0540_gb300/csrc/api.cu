@@ -10,6 +10,8 @@
 #include <vector>
 
 #include "kernels.h"
+#include "learned.h"
+#include "mlp.h"
 
 namespace bte {
 
@@ -436,8 +438,82 @@ bte_status wall_table(bte_ctx *c, const Table *t, double Tw, int side, const dou
 
 bte_status check_mode(bte_ctx *c, int mode) {
     if (mode == BTE_FP64_PLAIN || mode == BTE_FP32) return BTE_OK;
-    if (mode == BTE_LEARNED) return fail(c, BTE_ESTATE, "learned mode: no trained surrogate is loaded");
+    if (mode == BTE_LEARNED) {
+        if (!c->mlp) return fail(c, BTE_ESTATE, "learned mode: no surrogate (bte_mlp_init)");
+        return BTE_OK;
+    }
     return fail(c, BTE_EINVAL, "unknown mode");
+}
+
+// Learned path on a uniform batch of table `mlp->table`: surrogate, projection,
+// sampled-mode indicator, FP32 recompute of the flagged cells. Synchronises
+// the stream once (the flagged set decides the fallback launch).
+bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int64_t ncells, unsigned flags,
+                           cudaStream_t st) {
+    Mlp *m = c->mlp;
+    if (!B->uniform || B->segs.size() != 1 || m->table != 0)
+        return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
+    const Segment &sg = B->segs[0];
+    const Table *t = c->tables[0];
+    if (!fused_dft_supported(t->N)) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
+    if (!c->ind) {
+        c->ind = new IndicatorTable();
+        if (build_indicator_table(*t, c->learned_samples, 12345, *c->ind) != 0)
+            return fail(c, BTE_ENOMEM, "learned mode: indicator table");
+    }
+    bte_status s;
+    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * (size_t)B->nslots * (2 * c->ind->S + 1))) != BTE_OK)
+        return s;
+    // 1. surrogate in chunks of up to 8192 cells
+    const int64_t chunk = 8192;
+    for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
+        const int n = (int)std::min<int64_t>(chunk, ncells - c0);
+        if (!m->ensure_batch(n)) return fail(c, BTE_ENOMEM, "learned mode: activations");
+        std::vector<int64_t> rows(n);
+        for (int i = 0; i < n; ++i) rows[i] = (c0 + i) * cell_M(t);
+        cudaError_t e = cudaMemcpyAsync(m->rowoff, rows.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: upload");
+        if (m->run(f, nullptr, n, false, c->d_status, st)) return fail(c, BTE_ECUDA, "learned mode: surrogate");
+        launch_mlp_post(m->Y, m->rho, m->rowoff, n, m->M, m->s_out, Q, st);
+        count_launches(c, 5);
+    }
+    // 2. conservation projection
+    launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(t), 0, nullptr, nullptr, nullptr, 0.0, st);
+    count_launches(c, 1);
+    if (flags & BTE_FLAG_NO_FALLBACK) {
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned mode: launch");
+    }
+    // 3. indicator at the sampled modes
+    DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
+    const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+    launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st);
+    launch_dft_forward_fused(Q, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_QH], c->d_status, st);
+    float *e2 = (float *)c->scratch[SC_MISC];
+    float *d2 = e2 + (size_t)B->nslots * c->ind->S;
+    float *ind = d2 + (size_t)B->nslots * c->ind->S;
+    launch_indicator(*c->ind, (const float2 *)c->scratch[SC_F], (const float2 *)c->scratch[SC_QH], t->N, sg.eoff,
+                     sg.nslots, sg.nvalid, e2, d2, ind, st);
+    count_launches(c, 4);
+    std::vector<float> h(B->nslots);
+    cudaError_t e = cudaMemcpyAsync(h.data(), ind, sizeof(float) * B->nslots, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: indicator");
+    // 4. exact fallback for the flagged cells (the host slot order is the cell order)
+    const double tol = 1e-6 * c->learned_tol_ppm;
+    std::vector<bte_instance> redo;
+    for (int64_t i = 0; i < ncells; ++i) {
+        c->learned_max_ind = std::max(c->learned_max_ind, (double)h[i]);
+        if (!(h[i] <= tol)) redo.push_back(bte_instance{0, 0, i * cell_M(t)});
+    }
+    c->learned_cells += ncells;
+    c->learned_fallbacks += (int64_t)redo.size();
+    if (redo.empty()) return BTE_OK;
+    Batch *R = nullptr;
+    if ((s = get_batch(c, redo.data(), (int64_t)redo.size(), &R)) != BTE_OK) return s;
+    if ((s = prepare(c, R, BTE_FP32, false, false)) != BTE_OK) return s;
+    return enqueue_collide(c, R, f, Q, BTE_FP32, POST_PROJECT, nullptr, nullptr, nullptr, 0.0, st);
 }
 
 }  // namespace
@@ -493,6 +569,11 @@ void bte_destroy(bte_ctx *c) {
         free_table(*t);
         delete t;
     }
+    delete c->mlp;
+    if (c->ind) {
+        free_indicator_table(*c->ind);
+        delete c->ind;
+    }
     for (int i = 0; i < 8; ++i) cudaFree(c->scratch[i]);
     cudaFree(c->d_status);
     cudaFree(c->d_counter);
@@ -535,7 +616,8 @@ bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_inst
     cudaSetDevice(c->device);
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
-    if ((s = prepare(c, B, mode, false, false)) != BTE_OK) return s;
+    if ((s = prepare(c, B, mode == BTE_LEARNED ? BTE_FP32 : mode, false, false)) != BTE_OK) return s;
+    if (mode == BTE_LEARNED) return learned_collide(c, B, f, Q, ninst, flags, (cudaStream_t)stream);
     return enqueue_collide(c, B, f, Q, mode, (flags & BTE_FLAG_RAW) ? POST_RAW : POST_PROJECT, nullptr, nullptr,
                            nullptr, 0.0, (cudaStream_t)stream);
 }
@@ -628,6 +710,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "kernel launch");
     };
     if (st == nullptr) return body();  // the legacy stream cannot be captured
+    if (mode == BTE_LEARNED) return fail(c, BTE_EINVAL, "bte_step: use bte_collide for the learned mode");
     GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
                  tr ? 1 : 0, dt, eps, f, stream};
     auto it = c->graphs.find(key);
@@ -716,6 +799,7 @@ static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
     if (!std::strcmp(name, "conv_stages")) { *lo = 1; *hi = 4; return &c->conv_stages; }
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
+    if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
     return nullptr;
 }
 
@@ -744,6 +828,18 @@ bte_status bte_get_option(const bte_ctx *c, const char *name, int *value) {
     int *slot = option_slot(const_cast<bte_ctx *>(c), name, &lo, &hi);
     if (!slot) return BTE_EINVAL;
     *value = *slot;
+    return BTE_OK;
+}
+
+bte_status bte_learned_stats(bte_ctx *c, int64_t *cells, int64_t *fallbacks, double *max_indicator, int reset) {
+    if (!c) return BTE_EINVAL;
+    if (cells) *cells = c->learned_cells;
+    if (fallbacks) *fallbacks = c->learned_fallbacks;
+    if (max_indicator) *max_indicator = c->learned_max_ind;
+    if (reset) {
+        c->learned_cells = c->learned_fallbacks = 0;
+        c->learned_max_ind = 0.0;
+    }
     return BTE_OK;
 }
 

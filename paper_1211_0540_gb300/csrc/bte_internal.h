@@ -87,6 +87,8 @@ struct GraphKey {
 };
 
 struct Batch;  // device-side description of one instance layout (defined in api.cu)
+struct Mlp;    // learned surrogate (mlp.h)
+struct IndicatorTable;
 
 enum ProfKernel { PK_CONV32 = 0, PK_CONV64 = 1, PK_COLLIDE = 2 };
 struct ProfEntry {
@@ -130,6 +132,12 @@ struct bte_ctx {
     int conv_stages = 2;       // pipeline depth (weight/row blocks in flight per warp)
     int conv_merge = 4;        // blocks per compensated (TwoSum) merge
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
+    bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)
+    bte::IndicatorTable *ind = nullptr;  // sampled modes of the fallback indicator
+    int learned_tol_ppm = 10000;         // fallback when the indicator exceeds 1e-6 * this
+    int learned_samples = 64;
+    int64_t learned_cells = 0, learned_fallbacks = 0;
+    double learned_max_ind = 0.0;
 };
 
 namespace bte {

@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "velocity_nodes", "maxwellian", "bi_maxwellian", "bkw", "random_bi_maxwellian_params",
     "homogeneous_cells", "wall_heating_initial", "precision_sweep_cells", "uneven_batch",
-    "training_states",
+    "training_states", "surrogate_training_states",
 ]
 
 
@@ -100,17 +100,77 @@ def uneven_batch(ninst, seed, L=6.0, Ns=(12, 16, 24, 32), pN=(0.4, 0.3, 0.2, 0.1
     return out
 
 
-def training_states(N, L, nstates, seed):
-    """Seeded bi- and tri-Maxwellians (means ~ U(-1.5, 1.5)^3, T ~ U(0.5, 2),
-    weights from a Dirichlet(1) draw), normalised to density 1."""
+def training_states(N, L, nstates, seed, chunk=2048):
+    """Seeded bi- and tri-Maxwellians (half each; means ~ U(-1.5, 1.5)^3,
+    temperatures ~ U(0.5, 2), weights from a Dirichlet(1) draw), density 1.
+    Vectorised over chunks of states."""
     rng = np.random.default_rng(seed)
+    nb = np.where(rng.uniform(size=nstates) < 0.5, 2, 3)
+    w = rng.dirichlet(np.ones(3), size=nstates)
+    w[nb == 2, 2] = 0.0
+    w /= w.sum(axis=1, keepdims=True)
+    u = rng.uniform(-1.5, 1.5, size=(nstates, 3, 3))
+    T = rng.uniform(0.5, 2.0, size=(nstates, 3))
+    g1 = 2.0 * L / N * (np.arange(N) - N // 2)
     out = np.empty((nstates, N ** 3))
-    for s in range(nstates):
-        nb = 2 if rng.uniform() < 0.5 else 3
-        w = rng.dirichlet(np.ones(nb))
-        f = np.zeros(N ** 3)
-        for b in range(nb):
-            u = tuple(rng.uniform(-1.5, 1.5, size=3))
-            f += maxwellian(N, L, w[b], u, rng.uniform(0.5, 2.0))
-        out[s] = f
+    for c0 in range(0, nstates, chunk):
+        c1 = min(nstates, c0 + chunk)
+        Tb = T[c0:c1, :, None, None]  # (n, 3 bumps, 1, 1)
+        # the Maxwellian factorises over the three velocity components
+        e = np.exp(-(g1[None, None, None, :] - u[c0:c1, :, :, None]) ** 2 / (2.0 * Tb))  # (n, 3, 3, N)
+        amp = w[c0:c1] * (2.0 * math.pi * T[c0:c1]) ** -1.5  # (n, 3)
+        g = np.einsum("nb,nbi,nbj,nbk->nijk", amp, e[:, :, 0], e[:, :, 1], e[:, :, 2], optimize=True)
+        out[c0:c1] = g.reshape(c1 - c0, -1)
+    return out
+
+
+def surrogate_training_states(N, L, nstates, seed, chunk=2048):
+    """Training distribution of the learned surrogate, three seeded families
+    (density 1 each):
+      - 40 %: bi-/tri-Maxwellians as in training_states;
+      - 30 %: a Maxwellian (mean ~ U(-1, 1)^3, T ~ U(0.5, 2)) carrying 2-20 %
+        of its mass in a second Maxwellian (mean offset ~ U(-1.5, 1.5)^3,
+        T ~ U(0.5, 2)) -- states near equilibrium;
+      - 30 %: half-range mixtures, a Maxwellian at T1 ~ U(0.5, 2) for v1 < 0 and
+        one at T2 ~ U(0.5, 3) for v1 >= 0 (zero mean, masses ~ U(0.3, 0.7)
+        of the total): the discontinuous distributions a diffuse wall emits."""
+    rng = np.random.default_rng(seed)
+    fam = rng.choice(3, size=nstates, p=[0.4, 0.3, 0.3])
+    out = np.empty((nstates, N ** 3))
+    i0 = np.flatnonzero(fam == 0)
+    if i0.size:
+        out[i0] = training_states(N, L, i0.size, int(rng.integers(1 << 31)), chunk)
+    g1 = 2.0 * L / N * (np.arange(N) - N // 2)
+
+    def maxw(u, T):  # (n, 3), (n,) -> (n, M), unit mass
+        e = np.exp(-(g1[None, None, :] - u[:, :, None]) ** 2 / (2.0 * T[:, None, None]))
+        a = (2.0 * math.pi * T) ** -1.5
+        return np.einsum("n,ni,nj,nk->nijk", a, e[:, 0], e[:, 1], e[:, 2]).reshape(len(T), -1)
+
+    i1 = np.flatnonzero(fam == 1)
+    for c0 in range(0, i1.size, chunk):
+        idx = i1[c0:c0 + chunk]
+        n = idx.size
+        u0 = rng.uniform(-1.0, 1.0, size=(n, 3))
+        T0 = rng.uniform(0.5, 2.0, size=n)
+        eps = rng.uniform(0.02, 0.2, size=n)
+        u1 = u0 + rng.uniform(-1.5, 1.5, size=(n, 3))
+        T1 = rng.uniform(0.5, 2.0, size=n)
+        out[idx] = (1.0 - eps)[:, None] * maxw(u0, T0) + eps[:, None] * maxw(u1, T1)
+    i2 = np.flatnonzero(fam == 2)
+    v1 = np.repeat(g1, N * N)
+    neg, pos = (v1 < 0.0)[None, :], (v1 >= 0.0)[None, :]
+    for c0 in range(0, i2.size, chunk):
+        idx = i2[c0:c0 + chunk]
+        n = idx.size
+        z = np.zeros((n, 3))
+        T1 = rng.uniform(0.5, 2.0, size=n)
+        T2 = rng.uniform(0.5, 3.0, size=n)
+        m1 = rng.uniform(0.3, 0.7, size=n)
+        A = maxw(z, T1) * neg
+        B = maxw(z, T2) * pos
+        dv3 = (2.0 * L / N) ** 3
+        a = m1 / (A.sum(axis=1) * dv3)
+        b = (1.0 - m1) / (B.sum(axis=1) * dv3)
+        out[idx] = a[:, None] * A + b[:, None] * B
     return out
