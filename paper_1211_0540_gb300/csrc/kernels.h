@@ -79,12 +79,17 @@ void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const Df
 
 // Transport (Sec. 3.4) on nx uniform cells of M values. mw_*: wall Maxwellians
 // per velocity (device, M doubles), den_*: sum over the incoming half of |v.n| M_w.
+constexpr int kTransportMaxN = 32;
 struct TransportArgs {
     int N, nx;
     double dv, dx;
     int bc_left, bc_right;
     const double *mw_left, *mw_right;
     double den_left, den_right;
+    // filled per sub-step by launch_transport_half:
+    double rden_left, rden_right;   // 1 / den (0 when den is 0)
+    double kv[kTransportMaxN];      // (tau / dx) v1_i,  v1_i = dv (i - N/2)
+    double wv[kTransportMaxN];      // |v1_i|
 };
 void launch_transport_half(double *f, double *f1, const TransportArgs &ta, double tau, cudaStream_t st);
 

@@ -5,9 +5,10 @@
 // advanced by Heun's method (the paper's second-order Runge-Kutta):
 //   f1 = f + tau R(f);  f <- (f + f1 + tau R(f1)) / 2,  R = -(F_{j+1/2} - F_{j-1/2}) / dx.
 // Since minmod is positively homogeneous, dx/2 s_j = minmod(f_j - f_{j-1}, f_{j+1} - f_j) / 2:
-// the face values need no division. FP64 arithmetic is expensive on this GPU,
-// so minmod works on the IEEE bit patterns (integer compares) and the wall
-// Maxwellians are tabulated once on the host.
+// the face values need no division. FP64 arithmetic is expensive on this GPU
+// (about 1/75 of the FP32 rate), so minmod works on the IEEE bit patterns
+// (integer compares), the wall Maxwellians, (tau/dx) v1 and |v1| are tabulated
+// on the host and the update takes six FP64 operations per value.
 // Walls (two ghost cells each side, formed on the fly):
 // - diffuse (Sec. 2.1, Eq. BC): components entering the slab take
 //   sigma_w M_w(v), M_w = (2 pi T_w)^{-3/2} exp(-|v|^2 / (2 T_w)); sigma_w is the
@@ -33,6 +34,8 @@ __device__ __forceinline__ double minmod(double a, double b) {
 }
 
 // sigma_w for the wall of `side` (0 left, 1 right), reduced by the whole CTA.
+// Outgoing components (v.n < 0 for the inward normal n) are i < N/2 at the
+// left wall and i > N/2 at the right wall; |v.n| = |v1_i| is tabulated.
 __device__ double wall_sigma(const double *__restrict__ f, const TransportArgs &a, int side) {
     __shared__ double red[kTThreads / 32];
     const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
@@ -40,8 +43,7 @@ __device__ double wall_sigma(const double *__restrict__ f, const TransportArgs &
     double out = 0.0;
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const int i = j / NN;
-        const double vn = side == 0 ? a.dv * (i - h) : -a.dv * (i - h);
-        if (vn < 0.0) out = fma(-vn, fc[j], out);
+        if (side == 0 ? i < h : i > h) out = fma(a.wv[i], fc[j], out);
     }
     for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = out;
@@ -49,8 +51,7 @@ __device__ double wall_sigma(const double *__restrict__ f, const TransportArgs &
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
     __syncthreads();
-    const double den = side == 0 ? a.den_left : a.den_right;
-    return den > 0.0 ? s / den : 0.0;
+    return s * (side == 0 ? a.rden_left : a.rden_right);
 }
 
 // Value of the extended array at cell x in [-2, nx + 1], velocity j.
@@ -73,10 +74,15 @@ __device__ __forceinline__ double ext(const double *__restrict__ f, int x, int j
 
 // stage 1: f1 = f + tau R(f)      (src = f)
 // stage 2: f  = (f + f1 + tau R(f1)) / 2   (src = f1)
+// With the upwind side fixed by the sign of v1 only four stencil points are
+// read, e_0..e_3 = cells c-2..c+1 (v1 >= 0) or c-1..c+2 (v1 < 0), and with
+// D_q = e_q - e_{q-1} the two face values of cell c differ by
+//   f_{c+1/2} - f_{c-1/2} = D_2 +- (minmod(D_2, D_3) - minmod(D_1, D_2)) / 2,
+// so tau R = -(tau / dx) v1 (f_{c+1/2} - f_{c-1/2}) costs six FP64 operations.
 template <int STAGE>
 __global__ void __launch_bounds__(kTThreads) transport_stage_kernel(double *__restrict__ f,
                                                                      double *__restrict__ f1,
-                                                                     TransportArgs a, double tau) {
+                                                                     const __grid_constant__ TransportArgs a) {
     const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
     const int c = blockIdx.y;
     const double *src = STAGE == 1 ? f : f1;
@@ -84,35 +90,37 @@ __global__ void __launch_bounds__(kTThreads) transport_stage_kernel(double *__re
     double sig_l = 0.0, sig_r = 0.0;
     if (c < 2 && a.bc_left == BTE_BC_DIFFUSE) sig_l = wall_sigma(src, a, 0);
     if (c >= a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE) sig_r = wall_sigma(src, a, 1);
-    const double k = tau / a.dx;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
         const int i = j / NN;
-        const double v1 = a.dv * (i - h);
-        double e[5];
+        const bool pos = i >= h;
+        const int x0 = pos ? c - 2 : c - 1;
+        double e[4];
 #pragma unroll
-        for (int d = 0; d < 5; ++d) e[d] = ext(src, c - 2 + d, j, i, a, sig_l, sig_r);
-        const double d01 = e[1] - e[0], d12 = e[2] - e[1], d23 = e[3] - e[2], d34 = e[4] - e[3];
-        double vl, vr;  // face values at c - 1/2 and c + 1/2
-        if (v1 >= 0.0) {
-            vl = fma(0.5, minmod(d01, d12), e[1]);
-            vr = fma(0.5, minmod(d12, d23), e[2]);
-        } else {
-            vl = fma(-0.5, minmod(d12, d23), e[2]);
-            vr = fma(-0.5, minmod(d23, d34), e[3]);
-        }
-        const double dF = v1 * (vr - vl);  // F_{c+1/2} - F_{c-1/2}
+        for (int d = 0; d < 4; ++d) e[d] = ext(src, x0 + d, j, i, a, sig_l, sig_r);
+        const double D1 = e[1] - e[0], D2 = e[2] - e[1], D3 = e[3] - e[2];
+        const double g = fma(pos ? 0.5 : -0.5, minmod(D2, D3) - minmod(D1, D2), D2);
+        const double own = pos ? e[2] : e[1];  // src at cell c
         const int64_t idx = (int64_t)c * M + j;
-        if (STAGE == 1) f1[idx] = fma(-k, dF, f[idx]);
-        else f[idx] = 0.5 * fma(-k, dF, f[idx] + f1[idx]);
+        if (STAGE == 1) f1[idx] = fma(-a.kv[i], g, own);
+        else f[idx] = 0.5 * fma(-a.kv[i], g, f[idx] + own);
     }
 }
 }  // namespace
 
 void launch_transport_half(double *f, double *f1, const TransportArgs &ta, double tau, cudaStream_t st) {
-    const int M = ta.N * ta.N * ta.N;
+    const int M = ta.N * ta.N * ta.N, h = ta.N / 2;
+    TransportArgs a = ta;
+    const double k = tau / ta.dx;
+    for (int i = 0; i < kTransportMaxN; ++i) {
+        const double v1 = i < ta.N ? ta.dv * (i - h) : 0.0;
+        a.kv[i] = k * v1;
+        a.wv[i] = v1 < 0.0 ? -v1 : v1;
+    }
+    a.rden_left = ta.den_left > 0.0 ? 1.0 / ta.den_left : 0.0;
+    a.rden_right = ta.den_right > 0.0 ? 1.0 / ta.den_right : 0.0;
     dim3 grid((M + kTThreads - 1) / kTThreads, ta.nx);
-    transport_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, ta, tau);
-    transport_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f, f1, ta, tau);
+    transport_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, a);
+    transport_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f, f1, a);
 }
 
 }  // namespace bte

@@ -238,7 +238,8 @@ def test_invalid_arguments_rejected(bte):
     d.close()
 
 
-@pytest.mark.parametrize("N,ncells,nsample,seed", [(16, 128, 6, 11), (24, 64, 2, 12), (32, 256, 2, 13)])
+@pytest.mark.parametrize("N,ncells,nsample,seed", [(16, 128, 6, 11), (24, 64, 2, 12), (32, 256, 2, 13),
+                                                   (12, 200, 3, 14), (8, 1000, 4, 15)])
 def test_full_size_workloads_on_sampled_cells(bte, N, ncells, nsample, seed):
     """Full batch at the benchmark's sizes; oracle on sampled cells."""
     f = inputs.precision_sweep_cells(N, L, ncells, seed=seed)
