@@ -41,6 +41,7 @@ WORKLOAD = ("sudden wall heating: 128 cells x N=16^3 velocities (L=6, hard spher
             "Tw=2 diffuse / specular), one Strang step = 2 transport half steps + RK2 over "
             "128 cells = 256 collision evals")
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
+WORKLOADS = ("wall-heating", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16")
 SMS, FP32_LANES = 152, 128
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -79,6 +80,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
+                    help="wall-heating (the headline line) or one of the secondary workloads")
+    ap.add_argument("--train-states", type=int, default=200000, help="learned-n16: training pairs")
+    ap.add_argument("--epochs", type=int, default=30, help="learned-n16: training epochs")
     return ap.parse_args()
 
 
@@ -200,6 +205,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "wall-heating":
+        return run_secondary(args)
     import torch
     import torch.distributed as dist
 
@@ -370,6 +377,338 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Secondary workloads (one JSON line each; the headline is wall-heating).
+
+def _timed_steps(torch, fn, steps, stream, flush):
+    """Device time of each call of fn, L2 flushed before each (outside the events)."""
+    ev = []
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(i & 0xff)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def _moment_rel(oracle, n, q):
+    """max_i |(C Q)_i| / max(m_0(|Q|), m_4(|Q|)) over the cells of q (2-D)."""
+    m = oracle.moments(n, L, q)
+    a = oracle.moments(n, L, np.abs(q))
+    scale = np.maximum(np.abs(a[:, 0]), np.abs(a[:, 4]))
+    return float((np.abs(m).max(axis=1) / scale).max())
+
+
+def _alu_peak(clocks):
+    clk = clocks["sm_mhz"] or 1920.0
+    return SMS * FP32_LANES * 2 * clk * 1e6 / 1e12, clk
+
+
+def _line(args, metric, value, unit, ms_per_step, workload, extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "l2": "flushed (512 MB write) before every timed step"}}
+    line.update(extra)
+    return line
+
+
+def run_homog1(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """One space-homogeneous cell, N = 16, hard spheres, 20 Heun steps of dt = 0.01
+    (40 evaluations), FP64 plain and FP32 paths, against the oracle's trajectory."""
+    n, lam, eps, dt, nsteps = 16, 1.0, 1.0, 0.01, 20
+    ctx.init_weights([(n, L, lam)])
+    f0 = inputs.homogeneous_cells(n, L, 1, seed=1)
+    ref = [f0]
+    for _ in range(nsteps):
+        ref.append(oracle.rk2_homogeneous(n, L, lam, ref[-1], dt, eps))
+    res = {}
+    sampler.start()
+    n0 = ctx.launch_count()
+    for name, mode in (("fp64_plain", bte.FP64_PLAIN), ("fp32", bte.FP32)):
+        f = torch.from_numpy(f0.copy()).cuda().reshape(-1)
+        with torch.cuda.stream(stream):
+            for _ in range(max(args.warmup, 3)):
+                ctx.step(f, dt, eps, mode=mode, stream=stream)
+        ctx.sync_status(stream)
+        f.copy_(torch.from_numpy(f0.reshape(-1)))
+        torch.cuda.synchronize()
+        states, ev = [], []
+        with torch.cuda.stream(stream):
+            for i in range(nsteps):
+                flush.fill_(i & 0xff)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ctx.step(f, dt, eps, mode=mode, stream=stream)
+                e1.record(stream)
+                states.append(f.clone())  # after the step's events
+                ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        ctx.sync_status(stream)
+        traj = np.stack([x.cpu().numpy() for x in states])
+        err = max(np.linalg.norm(traj[i] - ref[i + 1][0]) / np.linalg.norm(ref[i + 1][0]) for i in range(nsteps))
+        m0 = oracle.moments(n, L, f0)[0]
+        m1 = oracle.moments(n, L, traj[-1:])[0]
+        drift = float(np.abs(m1 - m0).max() / max(abs(m0[0]), abs(m0[4])))
+        tot = float(sum(ms))
+        res[name] = {"evals_per_s": 2 * nsteps / (tot * 1e-3), "us_per_eval": 1e3 * tot / (2 * nsteps),
+                     "rel_l2_vs_oracle_trajectory_max": float(err), "moment_drift_rel": drift,
+                     "ms_trajectory": tot}
+    launches = ctx.launch_count() - n0
+    clocks = sampler.stop()
+    wl = ("space-homogeneous 1 cell, N=16, L=6, hard spheres, eps=1, bi-Maxwellian (seed 1), "
+          "20 Heun steps dt=0.01 = 40 evals, projection each stage")
+    return _line(args, "cell-collision evals/s (1 cell, FP64 plain operator)", res["fp64_plain"]["evals_per_s"],
+                 UNIT, res["fp64_plain"]["ms_trajectory"] / nsteps, wl,
+                 {"steps": nsteps, "dtype": "f64", "fp64_plain": res["fp64_plain"], "fp32": res["fp32"],
+                  "gpu_launches": launches, "clocks": clocks})
+
+
+def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """256 bi-Maxwellian cells at N = 32 (means ~ U(-1.5, 1.5)^3), FP32 operator;
+    oracle on 16 seeded cells; plain FP64 operator timed once."""
+    n, lam, nc = 32, 1.0, 256
+    ctx.init_weights([(n, L, lam)])
+    fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
+    f = torch.from_numpy(fn).cuda().reshape(-1)
+    Q = torch.empty_like(f)
+    ctx.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            ctx.collide(f, Q, mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    ctx.profile_read("*", stream)
+    conv = [0.0, 0]
+
+    def one():
+        ctx.collide(f, Q, mode=bte.FP32, stream=stream)
+
+    sampler.start()
+    n0 = ctx.launch_count()
+    ms = _timed_steps(torch, one, args.steps, stream, flush)
+    launches = ctx.launch_count() - n0
+    clocks = sampler.stop()
+    k, t = ctx.profile_read("conv32", stream)
+    conv = [t, k]
+    ctx.sync_status(stream)
+    Qg = Q.cpu().numpy().reshape(nc, -1)
+    tot = float(sum(ms))
+    value = nc * args.steps / (tot * 1e-3)
+    # plain FP64 operator (table build and first call outside the timing)
+    Q64 = torch.empty_like(f)
+    with torch.cuda.stream(stream):
+        ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream)
+    ctx.sync_status(stream)
+    ms64 = _timed_steps(torch, lambda: ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream), 1, stream, flush)
+    fp64_value = nc / (ms64[0] * 1e-3)
+    pick = np.sort(np.random.default_rng(3).choice(nc, 16, replace=False))
+    Qo = oracle.collide(n, L, lam, fn[pick])
+    Qm = oracle.collide(n, L, lam, fn[pick], part=1, project=False)
+    rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+    relp = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
+    peak, clk = _alu_peak(clocks)
+    pairs = conv_pairs_per_cell(n)
+    conv_ms = conv[0] / max(conv[1], 1)
+    achieved = 10.0 * pairs * nc / (conv_ms * 1e-3) / 1e12
+    wl = ("precision sweep: 256 bi-Maxwellian cells (means ~ U(-1.5,1.5)^3, T ~ U(0.5,2), seed 3), "
+          "N=32, L=6, hard spheres; one projected collision evaluation of all cells per step")
+    return _line(args, "cell-collision evals/s at N=32 (FP32 operator)", value, UNIT, tot / args.steps, wl, {
+        "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)", "achieved": achieved,
+                     "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk,
+                     "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
+                     "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
+        "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
+        "accuracy": {"rel_l2_loss_norm_max": float(rel.max()), "rel_l2_loss_norm_median": float(np.median(rel)),
+                     "rel_l2_plain_max": float(relp.max()), "cells_checked": pick.tolist(),
+                     "moment_rel_max": _moment_rel(oracle, n, Qg)},
+        "gpu_launches": launches, "clocks": clocks})
+
+
+def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """4096 homogeneous instances, N in {12,16,24,32} (p = .4/.3/.2/.1), lambda in
+    {0,1}; one Heun step of the whole batch per step (one CUDA graph)."""
+    Ns, lams = (12, 16, 24, 32), (0.0, 1.0)
+    grids = [(n, L, lam) for n in Ns for lam in lams]
+    ids = dict(zip([(g[0], g[2]) for g in grids], ctx.init_weights(grids)))
+    items = inputs.uneven_batch(4096, seed=4)
+    offs, off = [], 0
+    for (n, lam, fi) in items:
+        offs.append(off)
+        off += n ** 3
+    buf = np.empty(off)
+    for (n, lam, fi), o in zip(items, offs):
+        buf[o:o + fi.size] = fi
+    inst = [(ids[(n, lam)], o) for (n, lam, _), o in zip(items, offs)]
+    dt, eps = 0.01, 1.0
+    f = torch.from_numpy(buf).cuda()
+    ctx.profile_enable(True)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            ctx.step(f, dt, eps, inst=inst, mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    ctx.profile_read("*", stream)
+    sampler.start()
+    n0 = ctx.launch_count()
+    ms = _timed_steps(torch, lambda: ctx.step(f, dt, eps, inst=inst, mode=bte.FP32, stream=stream),
+                      args.steps, stream, flush)
+    launches = ctx.launch_count() - n0
+    clocks = sampler.stop()
+    k, t = ctx.profile_read("conv32", stream)
+    ctx.sync_status(stream)
+    tot = float(sum(ms))
+    evals = 2 * len(items)
+    value = evals * args.steps / (tot * 1e-3)
+    flops_step = sum(2 * 10.0 * conv_pairs_per_cell(n) for (n, _, _) in items)
+    conv_ms = t / max(k, 1)
+    peak, clk = _alu_peak(clocks)
+    achieved = flops_step / 2 / (conv_ms * 1e-3) / 1e12
+    # accuracy of one collision evaluation of the batch on sampled instances
+    fb = torch.from_numpy(buf).cuda()
+    Q = ctx.collide(fb, inst=inst, mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    Qn = Q.cpu().numpy()
+    rng = np.random.default_rng(4)
+    errs = {}
+    for n in Ns:
+        cand = [i for i, it in enumerate(items) if it[0] == n]
+        for i in rng.choice(cand, 2 if n < 32 else 1, replace=False):
+            n_, lam, fi = items[i]
+            qo = oracle.collide(n_, L, lam, fi[None])[0]
+            qm = oracle.collide(n_, L, lam, fi[None], part=1, project=False)[0]
+            e = float(np.linalg.norm(Qn[offs[i]:offs[i] + n_ ** 3] - qo) / np.linalg.norm(qm))
+            errs[n] = max(errs.get(n, 0.0), e)
+    mix = {str(n): sum(1 for it in items if it[0] == n) for n in Ns}
+    wl = ("uneven batch: 4096 space-homogeneous instances, N in {12,16,24,32} w.p. .4/.3/.2/.1, lambda in "
+          "{0,1} w.p. .5/.5 (8 tables), BKW or bi-Maxwellian data (seed 4); one Heun step of the whole batch "
+          "(2 evals per instance) replayed from one CUDA graph")
+    return _line(args, "cell-collision evals/s, uneven batch (FP32 operator)", value, UNIT, tot / args.steps, wl, {
+        "instances_by_N": mix, "evals_per_step": evals,
+        "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution, all sizes in one launch)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "conv_ms_per_launch": conv_ms,
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk},
+        "flop_rate_whole_step_tflops": flops_step / (tot / args.steps * 1e-3) / 1e12,
+        "accuracy": {"rel_l2_loss_norm_max_by_N": {str(k_): v for k_, v in errs.items()}},
+        "gpu_launches": launches, "clocks": clocks})
+
+
+def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """Surrogate trained on seeded pairs (f, Q_FP32(f)) at N = 16, evaluated with the
+    fallback indicator on 1024 cells of the wall-heating slab after 200 steps."""
+    from paper_1211_0540_gb300 import surrogate
+    n, lam, nx = 16, 1.0, 1024
+    M = n ** 3
+    ctx.init_weights([(n, L, lam)])
+    ctx.mlp_init(0, 1024, seed=1)
+    t0 = time.perf_counter()
+    f_tr, Q_tr = surrogate.make_training_set(ctx, n, L, args.train_states, seed=5)
+    t_data = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = surrogate.train(ctx, f_tr, Q_tr, n, L, epochs=args.epochs, batch=1024, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del f_tr, Q_tr
+    info = ctx.mlp_info()
+    # evaluation states: the wall-heating slab at nx = 1024 after 200 Strang steps
+    fw = torch.from_numpy(inputs.wall_heating_initial(n, L, nx)).cuda().reshape(-1)
+    tr = dict(nx=nx, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=TW,
+              Tw_right=1.0)
+    with torch.cuda.stream(stream):
+        for _ in range(200):
+            ctx.step(fw, 0.5 * (1.0 / nx) / L, EPS, transport=tr, mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    Q32 = torch.empty_like(fw)
+    Ql = torch.empty_like(fw)
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            ctx.collide(fw, Q32, mode=bte.FP32, stream=stream)
+            ctx.collide(fw, Ql, mode=bte.LEARNED, stream=stream)
+    ctx.sync_status(stream)
+    ctx.learned_stats(reset=True)
+    sampler.start()
+    n0 = ctx.launch_count()
+    ms_l = _timed_steps(torch, lambda: ctx.collide(fw, Ql, mode=bte.LEARNED, stream=stream), args.steps,
+                        stream, flush)
+    launches = ctx.launch_count() - n0
+    clocks = sampler.stop()
+    st = ctx.learned_stats(reset=True)
+    ms_f = _timed_steps(torch, lambda: ctx.collide(fw, Q32, mode=bte.FP32, stream=stream), args.steps,
+                        stream, flush)
+    Q64 = torch.empty_like(fw)
+    with torch.cuda.stream(stream):
+        ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream)
+    ms_64 = _timed_steps(torch, lambda: ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream), 1,
+                         stream, flush)
+    Qnn = ctx.collide(fw, mode=bte.LEARNED, fallback=False, stream=stream)
+    ctx.sync_status(stream)
+    a32, al, ann = (x.cpu().numpy().reshape(nx, M) for x in (Q32, Ql, Qnn))
+    fwn = fw.cpu().numpy().reshape(nx, M)
+    # errors normalised by the loss term (Q itself is near 0 in the equilibrated interior)
+    pick = np.unique(np.concatenate([np.arange(8), np.linspace(0, nx - 1, 56).astype(int)]))
+    qm = np.linalg.norm(oracle.collide(n, L, lam, fwn[pick], part=1, project=False), axis=1)
+    qo = oracle.collide(n, L, lam, fwn[pick])
+    e_l = np.linalg.norm(al[pick] - qo, axis=1) / qm
+    e_nn = np.linalg.norm(ann[pick] - qo, axis=1) / qm
+    e_32 = np.linalg.norm(a32[pick] - qo, axis=1) / qm
+    v_l = nx * args.steps / (sum(ms_l) * 1e-3)
+    v_f = nx * args.steps / (sum(ms_f) * 1e-3)
+    v_64 = nx / (ms_64[0] * 1e-3)
+    wl = ("learned surrogate (residual MLP, width 1024, BF16 tensor cores) + P_N + fallback indicator "
+          "(64 zeta points, tolerance 1e-2) on 1024 cells of the wall-heating slab (N=16, L=6, lambda=1, "
+          "Kn=0.1) after 200 FP32 Strang steps; trained on %d seeded pairs, %d epochs" % (args.train_states,
+                                                                                        args.epochs))
+    return _line(args, "cell-collision evals/s, learned mode with fallback (N=16)", v_l, UNIT,
+                 sum(ms_l) / args.steps, wl, {
+        "dtype": "bf16",
+        "fp32": {"value": v_f, "unit": UNIT}, "fp64_plain": {"value": v_64, "unit": UNIT},
+        "fallback": {"cells": st["cells"], "fallbacks": st["fallbacks"],
+                     "rate": st["fallbacks"] / max(st["cells"], 1), "max_indicator": st["max_indicator"]},
+        "accuracy": {"norm": "||Q - Q_oracle|| / ||Q_loss_oracle|| on %d sampled cells" % len(pick),
+                     "learned_with_fallback_max": float(e_l.max()),
+                     "learned_with_fallback_median": float(np.median(e_l)),
+                     "surrogate_only_max": float(e_nn.max()), "surrogate_only_median": float(np.median(e_nn)),
+                     "fp32_max": float(e_32.max()), "cells_checked": pick.tolist()},
+        "training": {"states": args.train_states, "epochs": args.epochs, "final_loss": float(loss),
+                     "data_s": t_data, "train_s": t_train,
+                     "samples_per_s": args.train_states * args.epochs / t_train, "params": info},
+        "gpu_launches": launches, "clocks": clocks})
+
+
+def run_secondary(args):
+    import torch
+
+    import oracle
+    from paper_1211_0540_gb300 import bte, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        raise SystemExit("secondary workloads run on one GPU")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    ctx = bte.Context(local)
+    if args.conv_impl is not None:
+        ctx.set_option("conv_impl", args.conv_impl)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sampler = ClockSampler(local)
+    fn = {"homog-1cell": run_homog1, "sweep-n32": run_sweep32, "uneven-4096": run_uneven,
+          "learned-n16": run_learned}[args.workload]
+    line = fn(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler)
+    print(json.dumps(line), flush=True)
     ctx.close()
     return 0
 

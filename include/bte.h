@@ -181,7 +181,9 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *                      an item (reduced in shared memory), 2 = as 1 with packed
  *                      f32x2 arithmetic;
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
- *       "conv_stages" blocks in flight per warp (1..4);
+ *       "conv_stages" blocks in flight per warp (1..4; 0 = automatic, the
+ *                      default: the deepest ring up to 2 that keeps the
+ *                      resident CTAs per SM of a one-block ring);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
  *                      (TwoSum) merges (>= 1);
  *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units.

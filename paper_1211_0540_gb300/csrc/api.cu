@@ -714,6 +714,17 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
     GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
                  tr ? 1 : 0, dt, eps, f, stream};
     auto it = c->graphs.find(key);
+    if (it != c->graphs.end() && inst &&
+        (it->second.inst.size() != (size_t)ninst ||
+         std::memcmp(it->second.inst.data(), inst, sizeof(bte_instance) * ninst) != 0)) {
+        // another instance list with the same count and hash: capture anew. A
+        // replay of the old graph may still be in flight, which the driver lets
+        // finish before it frees the executable; its events stay allocated
+        // because pending profile entries may still name them.
+        cudaGraphExecDestroy(it->second.exec);
+        c->graphs.erase(it);
+        it = c->graphs.end();
+    }
     if (it == c->graphs.end()) {
         prof_reserve(c, 8);
         cudaGraph_t g = nullptr;
@@ -728,6 +739,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         GraphRec rec;
         rec.prof = c->cap_prof;
         rec.launches = c->cap_launches;
+        if (inst) rec.inst.assign(inst, inst + ninst);
         c->cap_prof.clear();
         if (r != BTE_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -797,7 +809,7 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 2; return &c->conv_impl; }
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
-    if (!std::strcmp(name, "conv_stages")) { *lo = 1; *hi = 4; return &c->conv_stages; }
+    if (!std::strcmp(name, "conv_stages")) { *lo = 0; *hi = 4; return &c->conv_stages; }
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
     if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
     return nullptr;

@@ -103,6 +103,7 @@ struct GraphRec {
     cudaGraphExec_t exec = nullptr;
     std::vector<ProfEntry> prof;  // events baked into the graph
     int64_t launches = 0;         // kernels per replay
+    std::vector<bte_instance> inst;  // the instance list the graph was captured for (the key holds a hash)
 };
 
 }  // namespace bte
@@ -129,7 +130,7 @@ struct bte_ctx {
     double *d_wall = nullptr;  // unused scratch word pair
     std::map<std::tuple<int, double, double>, bte::WallTable> walls;  // (N, dv, T_w) -> M_w
     int conv_warps = 4;        // warps per CTA of the convolution kernel
-    int conv_stages = 2;       // pipeline depth (weight/row blocks in flight per warp)
+    int conv_stages = 0;       // pipeline depth (blocks in flight per warp); 0 = automatic
     int conv_merge = 4;        // blocks per compensated (TwoSum) merge
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
     bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)

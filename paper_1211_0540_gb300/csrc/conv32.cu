@@ -503,11 +503,25 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
         *out = itc->second;
         return cudaSuccess;
     }
+    if (stages < 1) {
+        // automatic depth: the deepest ring (up to 2 blocks in flight per warp)
+        // that keeps the CTAs per SM of a single-stage ring. At N = 32 a second
+        // stage of 8 KB rows would cost a resident CTA, which the block-level
+        // latency hiding does not buy back.
+        ConvLaunch a{}, b{};
+        cudaError_t e1 = conv32_configure(kinds_mask, num_sms, warps_per_cta, 1, impl, &a);
+        if (e1 != cudaSuccess) return e1;
+        e1 = conv32_configure(kinds_mask, num_sms, warps_per_cta, 2, impl, &b);
+        if (e1 != cudaSuccess) return e1;
+        *out = b.grid >= a.grid ? b : a;
+        cache[key] = *out;
+        return cudaSuccess;
+    }
     ConvLaunch L{};
     int stage = 0;
     for (int k = 0; k < kNumKinds; ++k)
         if (kinds_mask & (1u << k)) stage = stage > conv_stage_bytes(k) ? stage : conv_stage_bytes(k);
-    L.stages = stages < 1 ? 1 : (stages > kMaxStages ? kMaxStages : stages);
+    L.stages = stages > kMaxStages ? kMaxStages : stages;
     L.warp_smem = stage * L.stages;
     const int max_smem = 227 * 1024;
     const int max_warps = impl == 0 ? 8 : 4;
