@@ -80,6 +80,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
+    ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
                     help="wall-heating (the headline line) or one of the secondary workloads")
     ap.add_argument("--train-states", type=int, default=200000, help="learned-n16: training pairs")
@@ -223,6 +224,9 @@ def main():
     ctx.init_weights([(N, L, LAM)])
     if args.conv_impl is not None:
         ctx.set_option("conv_impl", args.conv_impl)
+    if args.dft_split is not None:
+        ctx.set_option("dft_split", args.dft_split)
+    ctx.set_option("profile_mask", 1)  # timed steps: events around the convolution only
     ctx.profile_enable(True)
     tr = dict(nx=NX, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=TW,
               Tw_right=1.0)
@@ -270,6 +274,24 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = EVALS_PER_STEP * args.steps * world / (total_ms * 1e-3)
+
+    # per-stage device times, in a separate pass (events around every stage
+    # lengthen the step, so the timed steps above carry them around conv32 only)
+    ctx.set_option("profile_mask", 63)
+    part_ms = {"conv32": 0.0, "forward": 0.0, "inverse": 0.0, "transport": 0.0}
+    with torch.cuda.stream(stream):
+        ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)  # capture
+        ctx.profile_read("*", stream)
+        for i in range(args.steps):
+            flush.fill_(i & 0xff)
+            ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
+            for name in part_ms:
+                part_ms[name] += ctx.profile_read(name, stream)[1]
+        ctx.profile_read("*", stream)
+    ctx.set_option("profile_mask", 1)  # drops the graphs: capture again before the end-to-end timing
+    with torch.cuda.stream(stream):
+        ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
+    ctx.profile_read("*", stream)
 
     # end to end through the public API: pinned host state in and out every step
     fh_in = torch.from_numpy(f.cpu().numpy()).pin_memory()
@@ -356,6 +378,9 @@ def main():
                      "flops_per_launch": flops_per_launch,
                      "flop_unit": "10 flops per evaluated (zeta, {xi, zeta-xi}) pair per cell",
                      "conv_ms_per_launch": conv_avg_ms, "conv_launches_timed": conv_n},
+        "stage_ms_per_step": dict({k: v / args.steps for k, v in part_ms.items()},
+                                  note="separate pass with events around every stage (each figure includes "
+                                       "the graph's launch gap before the stage)"),
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
@@ -529,6 +554,9 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk,
                      "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
                      "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
+        "stage_ms_per_step": dict({k: v / args.steps for k, v in part_ms.items()},
+                                  note="separate pass with events around every stage (each figure includes "
+                                       "the graph's launch gap before the stage)"),
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
         "accuracy": {"rel_l2_loss_norm_max": float(rel.max()), "rel_l2_loss_norm_median": float(np.median(rel)),
                      "rel_l2_plain_max": float(relp.max()), "cells_checked": pick.tolist(),

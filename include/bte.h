@@ -165,10 +165,14 @@ bte_status bte_moments(bte_ctx *ctx, const double *f, double *out, const bte_ins
 /* Kernel timing for benchmarks. When enabled, CUDA events are recorded on the
  * launching stream around every launch of the kernels named below (also inside
  * the graphs bte_step captures while enabled). bte_profile_read synchronises
- * `stream`, returns the number of such launches completed since the last read
- * and their summed device time in milliseconds, and forgets them.
+ * `stream`, returns the number of launches of `kernel` completed since they
+ * were last read and their summed device time in milliseconds, and forgets
+ * them (entries of other kernels stay pending).
  * kernel: "conv32" (FP32 convolution), "conv64" (plain FP64 convolution),
- * "collide" (a whole collide call), or "*" (all of them).
+ * "forward" (all forward transforms of a collide), "inverse" (all inverse
+ * transforms of a collide with the projection and time update fused into
+ * them), "transport" (one transport sub-step, two launches), "collide" (a
+ * whole collide call), or "*" (all of them, summed).
  * bte_launch_count returns the number of libbte kernels enqueued by this context
  * so far (a graph replay counts its kernels). */
 bte_status bte_profile_enable(bte_ctx *ctx, int enable);
@@ -186,7 +190,12 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *                      resident CTAs per SM of a one-block ring);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
  *                      (TwoSum) merges (>= 1);
- *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units.
+ *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units;
+ *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
+ *                      transforms of N <= 16: 1, 2 or 4 (default 4);
+ *       "profile_mask" which kernels bte_profile_enable times, bit k for
+ *                      conv32 (0), conv64 (1), collide (2), forward (3),
+ *                      inverse (4), transport (5); default 63 (all).
  * Changing an option drops the captured step graphs. Errors: BTE_EINVAL. */
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);

@@ -96,7 +96,7 @@ void prof_reserve(bte_ctx *c, size_t n) {
 }
 
 int prof_begin(bte_ctx *c, int kernel, cudaStream_t st, ProfEntry *pe) {
-    if (!c->prof) return 0;
+    if (!c->prof || !(c->prof_mask & (1 << kernel))) return 0;
     if (c->ev_free.empty()) {
         if (c->capturing) return 0;
         prof_reserve(c, 1);
@@ -297,8 +297,9 @@ enum Post { POST_RAW = 0, POST_PROJECT = 1, POST_STAGE1 = 2, POST_STAGE2 = 3 };
 bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, int post,
                            const double *x, double *y, const double *qp, double a, cudaStream_t st) {
     const bool fp64 = mode == BTE_FP64_PLAIN;
-    ProfEntry pe_all{}, pe_conv{};
+    ProfEntry pe_all{}, pe_conv{}, pe_fwd{}, pe_inv{};
     const int on_all = prof_begin(c, PK_COLLIDE, st, &pe_all);
+    const int on_fwd = prof_begin(c, PK_FORWARD, st, &pe_fwd);
     for (const Segment &sg : B->segs) {
         const Table *t = c->tables[sg.table];
         DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
@@ -309,7 +310,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             count_launches(c, 3);
         } else if (fused_dft_supported(t->N)) {
             launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status,
-                                     st);
+                                     st, c->dft_split);
             count_launches(c, 1);
         } else {
             launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
@@ -319,6 +320,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         cudaError_t e0 = cudaGetLastError();
         if (e0 != cudaSuccess) return cuda_fail(c, e0, "forward transform launch");
     }
+    prof_end(c, on_fwd, pe_fwd, st);
     if (fp64) {
         const int on = prof_begin(c, PK_CONV64, st, &pe_conv);
         for (const Segment &sg : B->segs) {
@@ -359,13 +361,14 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             return cuda_fail(c, e, msg);
         }
     }
+    const int on_inv = prof_begin(c, PK_INVERSE, st, &pe_inv);
     for (const Segment &sg : B->segs) {
         const Table *t = c->tables[sg.table];
         DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
         const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
         if (!fp64 && fused_dft_supported(t->N)) {
             launch_dft_inverse_fused((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si, Q,
-                                     proj_args(t), post, x, y, qp, a, st);
+                                     proj_args(t), post, x, y, qp, a, st, c->dft_split);
             count_launches(c, 1);
             continue;
         }
@@ -381,6 +384,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             count_launches(c, 1);
         }
     }
+    prof_end(c, on_inv, pe_inv, st);
     prof_end(c, on_all, pe_all, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
@@ -488,8 +492,10 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
     // 3. indicator at the sampled modes
     DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
     const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
-    launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st);
-    launch_dft_forward_fused(Q, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_QH], c->d_status, st);
+    launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
+                             c->dft_split);
+    launch_dft_forward_fused(Q, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_QH], c->d_status, st,
+                             c->dft_split);
     float *e2 = (float *)c->scratch[SC_MISC];
     float *d2 = e2 + (size_t)B->nslots * c->ind->S;
     float *ind = d2 + (size_t)B->nslots * c->ind->S;
@@ -697,13 +703,19 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
     cudaStream_t st = (cudaStream_t)stream;
     auto body = [&]() -> bte_status {
         if (tr) {
+            ProfEntry pe{};
+            const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
             launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            prof_end(c, on, pe, st);
             count_launches(c, 2);
         }
         bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st);
         if (r != BTE_OK) return r;
         if (tr) {
+            ProfEntry pe{};
+            const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
             launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            prof_end(c, on, pe, st);
             count_launches(c, 2);
         }
         cudaError_t e = cudaGetLastError();
@@ -726,7 +738,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         it = c->graphs.end();
     }
     if (it == c->graphs.end()) {
-        prof_reserve(c, 8);
+        prof_reserve(c, 16);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(c, e, "stream capture");
@@ -773,6 +785,9 @@ bte_status bte_profile_read(bte_ctx *c, const char *kernel, int64_t *launches, d
     if (!std::strcmp(kernel, "conv32")) want = PK_CONV32;
     else if (!std::strcmp(kernel, "conv64")) want = PK_CONV64;
     else if (!std::strcmp(kernel, "collide")) want = PK_COLLIDE;
+    else if (!std::strcmp(kernel, "forward")) want = PK_FORWARD;
+    else if (!std::strcmp(kernel, "inverse")) want = PK_INVERSE;
+    else if (!std::strcmp(kernel, "transport")) want = PK_TRANSPORT;
     else if (std::strcmp(kernel, "*") != 0) return fail(c, BTE_EINVAL, "bte_profile_read: unknown kernel name");
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
@@ -782,19 +797,22 @@ bte_status bte_profile_read(bte_ctx *c, const char *kernel, int64_t *launches, d
     std::vector<cudaEvent_t> owned;
     for (auto &kv : c->graphs)
         for (auto &pe : kv.second.prof) owned.push_back(pe.a);
+    std::vector<ProfEntry> keep;
     for (const ProfEntry &pe : c->pending) {
-        if (want < 0 || pe.kernel == want) {
-            float t = 0.f;
-            if (cudaEventElapsedTime(&t, pe.a, pe.b) == cudaSuccess) {
-                ms += t;
-                ++n;
-            } else {
-                cudaGetLastError();
-            }
+        if (want >= 0 && pe.kernel != want) {  // another kernel's entry stays pending
+            keep.push_back(pe);
+            continue;
+        }
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pe.a, pe.b) == cudaSuccess) {
+            ms += t;
+            ++n;
+        } else {
+            cudaGetLastError();
         }
         if (std::find(owned.begin(), owned.end(), pe.a) == owned.end()) c->ev_free.push_back({pe.a, pe.b});
     }
-    c->pending.clear();
+    c->pending.swap(keep);
     *launches = n;
     *total_ms = ms;
     return BTE_OK;
@@ -808,6 +826,8 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 2; return &c->conv_impl; }
+    if (!std::strcmp(name, "dft_split")) { *lo = 1; *hi = 4; return &c->dft_split; }
+    if (!std::strcmp(name, "profile_mask")) { *lo = 0; *hi = 63; return &c->prof_mask; }
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
     if (!std::strcmp(name, "conv_stages")) { *lo = 0; *hi = 4; return &c->conv_stages; }
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }

@@ -90,7 +90,7 @@ struct Batch;  // device-side description of one instance layout (defined in api
 struct Mlp;    // learned surrogate (mlp.h)
 struct IndicatorTable;
 
-enum ProfKernel { PK_CONV32 = 0, PK_CONV64 = 1, PK_COLLIDE = 2 };
+enum ProfKernel { PK_CONV32 = 0, PK_CONV64 = 1, PK_COLLIDE = 2, PK_FORWARD = 3, PK_INVERSE = 4, PK_TRANSPORT = 5 };
 struct ProfEntry {
     int kernel;
     cudaEvent_t a, b;
@@ -122,6 +122,7 @@ struct bte_ctx {
     std::map<bte::GraphKey, bte::GraphRec> graphs;
     // profiling / launch accounting
     bool prof = false;
+    int prof_mask = 63;        // bit k: record events around ProfKernel k
     bool capturing = false;
     std::vector<bte::ProfEntry> pending;       // direct launches and replays not yet read
     std::vector<bte::ProfEntry> cap_prof;      // entries of the graph being captured
@@ -133,6 +134,7 @@ struct bte_ctx {
     int conv_stages = 0;       // pipeline depth (blocks in flight per warp); 0 = automatic
     int conv_merge = 4;        // blocks per compensated (TwoSum) merge
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
+    int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
     bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)
     bte::IndicatorTable *ind = nullptr;  // sampled modes of the fallback indicator
     int learned_tol_ppm = 10000;         // fallback when the indicator exceeds 1e-6 * this

@@ -2,211 +2,397 @@
 //   forward:  fhat_k = (2 pi)^{-3/2} dv^3 sum_j f_j exp(-i zeta_k . v_j)
 //   inverse:  Qt_j = Re (2 pi)^{-3/2} dz^3 sum_k Qhat_k exp(+i zeta_k . v_j)
 // (Sec. 3.2, grid of Eq. meshpoints; zeta_k . v_j = 2 pi k'.j' / N.)
-// One CTA per cell does the three one-dimensional passes in shared memory with
-// the N x N phase matrix held there too (no per-term index arithmetic), so a
-// direction costs one launch and one read + one write of the cell. The
-// forward kernel writes fhat straight into the group layout of the
-// convolution ([group][k][lane]); the inverse kernel reads Qhat from it, keeps
-// Qt in shared memory in FP64, and applies the conservation projection of
-// Sec. 3.3 (and optionally the Heun update) before the single write of Q.
+// One CTA per cell, one thread per pencil: each of the three one-dimensional
+// passes loads the N values of a pencil into registers and multiplies them by
+// the N x N phase matrix exp(+-2 pi i (k - N/2)(j - N/2) / N). With both loops
+// unrolled the phase index ((k - N/2)(j - N/2) mod N) is a compile-time
+// constant, so the N roots of unity sit in registers and the matrix costs no
+// memory traffic; shared memory is touched once per value and pass (rows
+// padded to N + 1 against bank conflicts). The forward kernel writes fhat
+// straight into the group layout of the convolution ([group][k][lane]); the
+// inverse kernel reads Qhat from it and applies the conservation projection
+// of Sec. 3.3 (and optionally the Heun update) before the single write of Q.
+//
+// FP64 runs at about 1/70 of the FP32 rate here, so the five moments of Qt
+// are accumulated in double-float arithmetic (pairs of FP32 numbers combined
+// by error-free TwoSum / TwoProduct steps, relative error ~1e-13 over the
+// reduction tree) and only the final correction Q = Qt - C^T lambda and the
+// time update run in FP64.
+#include <cooperative_groups.h>
+
 #include "project.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace bte {
 
 namespace {
 
-template <int N>
+template <int N, int C_ = 4>
 struct FusedShape {
-    static constexpr int M = N * N * N;
-    static constexpr int NT = N == 16 ? 1024 : (N == 12 ? 576 : 512);  // multiple of N and of 32
-    static constexpr int WP = N + 1;          // padded phase-matrix row
-    static constexpr size_t smem = 2 * sizeof(float2) * M + sizeof(float2) * N * WP;
+    static constexpr int M = N * N * N, NN = N * N, H = N / 2;
+    static constexpr int C = C_;         // CTAs per cell (one thread-block cluster)
+    static constexpr int JR = N / C;     // slab rows (j1 or k2 values) per CTA
+    static constexpr int NP = NN / C;    // pencils per CTA and pass
+    static constexpr int NT = (NP + 31) / 32 * 32;
+    static constexpr int NW = NT / 32;
+    static constexpr int P = N + 1;      // padded pencil stride
+    // forward: A (own pencils, padded) + B (own slab, read by the cluster)
+    static constexpr size_t smem_fwd = sizeof(float2) * (NP * P + JR * NN);
+    // inverse: A (own slab, read by the cluster) + B (own pencils, padded) + R (FP32 Qt, padded) + base
+    static constexpr size_t smem_inv = sizeof(float2) * (JR * NN + NP * P) + sizeof(float) * NP * P +
+                                       sizeof(double) * NP;
+    static_assert(N % C == 0, "slabs must split evenly");
 };
 
-// W[k][j] = exp(sgn * 2 pi i (k - h)(j - h) / N)
+// phase index of W[k][j] = root[((k - N/2)(j - N/2)) mod N]
 template <int N>
-__device__ __forceinline__ void fill_phase(float2 *W, const float2 *__restrict__ root, float sgn) {
-    const int h = N / 2;
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        const int k = idx / N, j = idx % N;
-        int t = ((k - h) * (j - h)) % N;
-        if (t < 0) t += N;
-        const float2 w = root[t];
-        W[k * (N + 1) + j] = make_float2(w.x, sgn * w.y);
+__host__ __device__ constexpr int phase(int k, int j) {
+    return (((k - N / 2) * (j - N / 2)) % N + N) % N;
+}
+
+// y_k = sum_j x_j W[k][j], W = root (CONJ: conjugated), complex in and out.
+// Inputs outer, outputs inner: the N accumulators are independent, so
+// consecutive FMAs never wait on each other.
+template <int N, bool CONJ>
+__device__ __forceinline__ void pencil_cc(const float2 (&x)[N], float2 (&y)[N], const float2 (&rt)[N]) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float wr = rt[phase<N>(k, j)].x;
+            const float wi = CONJ ? -rt[phase<N>(k, j)].y : rt[phase<N>(k, j)].y;
+            y[k].x = fmaf(x[j].x, wr, y[k].x);
+            y[k].x = fmaf(-x[j].y, wi, y[k].x);
+            y[k].y = fmaf(x[j].x, wi, y[k].y);
+            y[k].y = fmaf(x[j].y, wr, y[k].y);
+        }
     }
+}
+
+// real input (forward first pass)
+template <int N>
+__device__ __forceinline__ void pencil_rc(const float (&x)[N], float2 (&y)[N], const float2 (&rt)[N]) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            y[k].x = fmaf(x[j], rt[phase<N>(k, j)].x, y[k].x);
+            y[k].y = fmaf(x[j], -rt[phase<N>(k, j)].y, y[k].y);
+        }
+    }
+}
+
+// real part of the output (inverse last pass)
+template <int N>
+__device__ __forceinline__ void pencil_cr(const float2 (&x)[N], float (&y)[N], const float2 (&rt)[N]) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) y[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            y[k] = fmaf(x[j].x, rt[phase<N>(k, j)].x, y[k]);
+            y[k] = fmaf(-x[j].y, rt[phase<N>(k, j)].y, y[k]);
+        }
+    }
+}
+
+// Cluster barrier without memory ordering: only keeps every CTA of the
+// cluster resident until all of them got here (their remote reads of this
+// CTA's shared memory have completed, since the values were consumed).
+__device__ __forceinline__ void cluster_barrier_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 }  // namespace
 
-template <int N>
-__global__ void __launch_bounds__(FusedShape<N>::NT)
+// Cell = cluster of C CTAs; CTA r owns the slab j1 in [r JR, (r+1) JR) of the
+// first two passes and the slab k2 in [r JR, (r+1) JR) of the last one, whose
+// pencils it reads from the owners' shared memory (distributed shared memory).
+template <int N, int C_>
+__global__ void __cluster_dims__(C_, 1, 1) __launch_bounds__(FusedShape<N, C_>::NT)
 dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, DftSeg s,
                      const float2 *__restrict__ root, float scale, float2 *__restrict__ G, int *status) {
-    using S = FusedShape<N>;
-    constexpr int M = S::M, NN = N * N;
+    using S = FusedShape<N, C_>;
+    constexpr int M = S::M, NN = S::NN, P = S::P, JR = S::JR, C = S::C;
+    cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) char smem_raw[];
-    float2 *A = reinterpret_cast<float2 *>(smem_raw);
-    float2 *B = A + M;
-    float2 *W = B + M;
-    const int sl = blockIdx.x;
+    float2 *A = reinterpret_cast<float2 *>(smem_raw);  // [jl][j2] rows of P, index k3
+    float2 *B = A + S::NP * P;                          // [jl][k2][k3]
+    const int r = (int)cl.block_rank(), sl = blockIdx.x / C, t = threadIdx.x;
     const int64_t off = slot_off[s.s0 + sl];
     float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
-    if (off < 0) {  // padding lane of a group: zero fhat
-        for (int e = threadIdx.x; e < M; e += blockDim.x) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);
+    if (off < 0) {  // padding lane of a group (the whole cluster leaves here): zero fhat
+        for (int e = r * (M / C) + t; e < (r + 1) * (M / C); e += S::NT) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);
         return;
     }
-    fill_phase<N>(W, root, -1.f);
-    float *R = reinterpret_cast<float *>(B);
+    float2 rt[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) rt[i] = root[i];
+    const bool act = t < S::NP;
     bool bad = false;
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const double x = f[off + e];
-        bad |= !isfinite(x);
-        R[e] = (float)x;
+    if (act) {  // along j3, pencil (j1, j2), real input
+        const int jl = t / N, j2 = t % N;
+        float x[N];
+        const double *fp = f + off + (int64_t)((r * JR + jl) * N + j2) * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double d = fp[j];
+            bad |= !isfinite(d);
+            x[j] = (float)d;
+        }
+        float2 y[N];
+        pencil_rc<N>(x, y, rt);
+#pragma unroll
+        for (int k = 0; k < N; ++k) A[t * P + k] = y[k];
     }
     if (bad) atomicOr(status, ST_NONFINITE);
     __syncthreads();
-    // pass along j3 (real input): A[row][k3] = sum_j3 R[row][j3] W[k3][j3]
-    {
-        const int k3 = threadIdx.x % N, rg = threadIdx.x / N;
-        float2 w[N];
+    if (act) {  // along j2, pencil (j1, k3)
+        const int jl = t / N, k3 = t % N;
+        float2 x[N], y[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) w[j] = W[k3 * S::WP + j];
-        for (int row = rg; row < NN; row += S::NT / N) {
-            float re = 0.f, im = 0.f;
+        for (int j = 0; j < N; ++j) x[j] = A[(jl * N + j) * P + k3];
+        pencil_cc<N, true>(x, y, rt);
 #pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const float x = R[row * N + j];
-                re = fmaf(x, w[j].x, re);
-                im = fmaf(x, w[j].y, im);
-            }
-            A[row * N + k3] = make_float2(re, im);
-        }
+        for (int k = 0; k < N; ++k) B[(jl * N + k) * N + k3] = y[k];
     }
-    __syncthreads();
-    // pass along j2: B[j1][k2][k3] = sum_j2 A[j1][j2][k3] W[k2][j2]
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int k3 = e % N, k2 = (e / N) % N, j1 = e / NN;
-        const float2 *a = A + j1 * NN + k3;
-        const float2 *w = W + k2 * S::WP;
-        float re = 0.f, im = 0.f;
+    cl.sync();
+    if (act) {  // along j1, pencil (k2, k3), rows from every CTA of the cluster, into the group layout
+        const int k2 = r * JR + t / N, k3 = t % N;
+        const float2 *src[C];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const float2 x = a[j * N], ww = w[j];
-            re = fmaf(x.x, ww.x, fmaf(-x.y, ww.y, re));
-            im = fmaf(x.y, ww.x, fmaf(x.x, ww.y, im));
-        }
-        B[e] = make_float2(re, im);
-    }
-    __syncthreads();
-    // pass along j1 into the group layout, scaled
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int k1 = e / NN, rest = e % NN;
-        const float2 *b = B + rest;
-        const float2 *w = W + k1 * S::WP;
-        float re = 0.f, im = 0.f;
+        for (int o = 0; o < C; ++o) src[o] = cl.map_shared_rank(B, o);
+        float2 x[N], y[N];
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const float2 x = b[j * NN], ww = w[j];
-            re = fmaf(x.x, ww.x, fmaf(-x.y, ww.y, re));
-            im = fmaf(x.y, ww.x, fmaf(x.x, ww.y, im));
-        }
-        g[(int64_t)e * kLanes] = make_float2(scale * re, scale * im);
+        for (int j = 0; j < N; ++j) x[j] = src[j / JR][((j % JR) * N + k2) * N + k3];
+        pencil_cc<N, true>(x, y, rt);
+        const int pk = k2 * N + k3;
+#pragma unroll
+        for (int k = 0; k < N; ++k) g[(int64_t)(k * NN + pk) * kLanes] = make_float2(scale * y[k].x, scale * y[k].y);
     }
+    cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
 }
 
 // mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q)
-template <int N>
-__global__ void __launch_bounds__(FusedShape<N>::NT)
+// CTA r owns the slab k2 in [r JR, (r+1) JR) of the first pass and j1 in
+// [r JR, (r+1) JR) of the other two; the second pass reads the first pass's
+// rows from the whole cluster, and the moment partials of the CTAs are added
+// in rank order by every CTA (the same lambda everywhere).
+template <int N, int C_>
+__global__ void __cluster_dims__(C_, 1, 1) __launch_bounds__(FusedShape<N, C_>::NT)
 dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ slot_off, DftSeg s,
                      const float2 *__restrict__ root, float scale, double *__restrict__ q, ProjArgs pa,
                      int mode, const double *__restrict__ x, double *__restrict__ y,
                      const double *__restrict__ qp, double a) {
-    using S = FusedShape<N>;
-    constexpr int M = S::M, NN = N * N;
+    using S = FusedShape<N, C_>;
+    constexpr int M = S::M, NN = S::NN, P = S::P, H = S::H, JR = S::JR, C = S::C, NP = S::NP;
+    cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) char smem_raw[];
-    float2 *A = reinterpret_cast<float2 *>(smem_raw);
-    float2 *B = A + M;
-    float2 *W = B + M;
-    __shared__ ProjShared psh;
-    const int sl = blockIdx.x;
+    float2 *A = reinterpret_cast<float2 *>(smem_raw);  // [kl][j1][k3], read by the cluster
+    float2 *B = A + JR * NN;                            // [jl][j2] rows of P, index k3
+    float *R = reinterpret_cast<float *>(B + NP * P);   // Qt, [jl][j2] rows of P, index j3
+    double *base = reinterpret_cast<double *>(R + NP * P);
+    __shared__ float red[32][10];
+    __shared__ float part[10];
+    __shared__ double sg[N], lam[5];
+    const int r = (int)cl.block_rank(), sl = blockIdx.x / C, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t off = slot_off[s.s0 + sl];
-    if (off < 0) return;
-    fill_phase<N>(W, root, 1.f);
+    if (off < 0) return;  // the whole cluster leaves
+    // the time-update operands of the own slab are loaded first, so that their
+    // memory latency overlaps the three passes
+    constexpr int MS = M / C, IT = (MS + S::NT - 1) / S::NT;
+    const double *xo = x ? x + off + (int64_t)r * MS : nullptr;
+    double *yo = y ? y + off + (int64_t)r * MS : nullptr;
+    const double *qpo = qp ? qp + off + (int64_t)r * MS : nullptr;
+    double u[IT], w[IT];
+    if (mode == 2) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = t + i * S::NT;
+            u[i] = e < MS ? xo[e] : 0.0;
+        }
+    } else if (mode == 3) {
+#pragma unroll
+        for (int i = 0; i < IT; ++i) {
+            const int e = t + i * S::NT;
+            u[i] = e < MS ? yo[e] : 0.0;
+            w[i] = e < MS ? qpo[e] : 0.0;
+        }
+    }
+    float2 rt[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) rt[i] = root[i];
+    const bool act = t < NP;
     const float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
-    for (int e = threadIdx.x; e < M; e += blockDim.x) A[e] = g[(int64_t)e * kLanes];
-    __syncthreads();
-    // along k1: B[j1][k2][k3] = sum_k1 A[k1][k2][k3] W[j1][k1]
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int j1 = e / NN, rest = e % NN;
-        const float2 *b = A + rest;
-        const float2 *w = W + j1 * S::WP;
-        float re = 0.f, im = 0.f;
+    if (act) {  // along k1, pencil (k2, k3), from the group layout
+        const int pk = (r * JR + t / N) * N + t % N;
+        float2 xx[N], yy[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const float2 xx = b[k * NN], ww = w[k];
-            re = fmaf(xx.x, ww.x, fmaf(-xx.y, ww.y, re));
-            im = fmaf(xx.y, ww.x, fmaf(xx.x, ww.y, im));
-        }
-        B[e] = make_float2(re, im);
+        for (int k = 0; k < N; ++k) xx[k] = g[(int64_t)(k * NN + pk) * kLanes];
+        pencil_cc<N, false>(xx, yy, rt);
+        const int kl = t / N, k3 = t % N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) A[(kl * N + j) * N + k3] = yy[j];
     }
-    __syncthreads();
-    // along k2: A[j1][j2][k3] = sum_k2 B[j1][k2][k3] W[j2][k2]
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int k3 = e % N, j2 = (e / N) % N, j1 = e / NN;
-        const float2 *b = B + j1 * NN + k3;
-        const float2 *w = W + j2 * S::WP;
-        float re = 0.f, im = 0.f;
+    cl.sync();
+    if (act) {  // along k2, pencil (j1, k3), rows from every CTA of the cluster
+        const int j1 = r * JR + t / N, k3 = t % N;
+        const float2 *src[C];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const float2 xx = b[k * N], ww = w[k];
-            re = fmaf(xx.x, ww.x, fmaf(-xx.y, ww.y, re));
-            im = fmaf(xx.y, ww.x, fmaf(xx.x, ww.y, im));
-        }
-        A[e] = make_float2(re, im);
+        for (int o = 0; o < C; ++o) src[o] = cl.map_shared_rank(A, o);
+        float2 xx[N], yy[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) xx[k] = src[k / JR][((k % JR) * N + j1) * N + k3];
+        pencil_cc<N, false>(xx, yy, rt);
+        const int jl = t / N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) B[(jl * N + j) * P + k3] = yy[j];
     }
-    __syncthreads();
-    // along k3, real part, into FP64 (reusing B's storage: 8 bytes per value)
-    double *D = reinterpret_cast<double *>(B);
-    {
-        const int j3 = threadIdx.x % N, rg = threadIdx.x / N;
-        float2 w[N];
+    cl.sync();  // all remote reads of A are done (no CTA may leave earlier)
+    // along k3, real part, pencil (j1, j2); per-pencil moment sums in double-float
+    Df mom[5];
+    if (act) {
+        float2 xx[N];
+        float rr[N];
 #pragma unroll
-        for (int k = 0; k < N; ++k) w[k] = W[j3 * S::WP + k];
-        for (int row = rg; row < NN; row += S::NT / N) {
-            float re = 0.f;
+        for (int k = 0; k < N; ++k) xx[k] = B[t * P + k];
+        pencil_cr<N>(xx, rr, rt);
+        Df s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const float2 xx = A[row * N + k];
-                re = fmaf(xx.x, w[k].x, fmaf(-xx.y, w[k].y, re));
+        for (int j = 0; j < N; ++j) {
+            rr[j] *= scale;
+            R[t * P + j] = rr[j];
+            df_add(s0, rr[j]);
+            df_add_prod(s1, (float)(j - H), rr[j]);
+            df_add_prod(s2, (float)((j - H) * (j - H)), rr[j]);
+        }
+        const int w1 = r * JR + t / N - H, w2 = t % N - H;
+        mom[0] = s0;
+        mom[1] = df_mul_int(s0, (float)w1);
+        mom[2] = df_mul_int(s0, (float)w2);
+        mom[3] = s1;
+        mom[4] = df_add(df_mul_int(s0, (float)(w1 * w1 + w2 * w2)), s2);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] = Df{0.f, 0.f};
+    }
+    if (mode != 0) {
+        // moments: warp trees, warp 0 over the CTA's warps, then the cluster's partials in rank order
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
+        if (S::NW > 1) {
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < 5; ++i) {
+                    red[warp][2 * i] = mom[i].hi;
+                    red[warp][2 * i + 1] = mom[i].lo;
+                }
+            __syncthreads();
+            if (warp == 0) {
+#pragma unroll
+                for (int i = 0; i < 5; ++i)
+                    mom[i] = lane < S::NW ? Df{red[lane][2 * i], red[lane][2 * i + 1]} : Df{0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
             }
-            D[row * N + j3] = (double)(scale * re);
+        }
+        if (t == 0)
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                part[2 * i] = mom[i].hi;
+                part[2 * i + 1] = mom[i].lo;
+            }
+        cl.sync();
+        if (warp == 0) {
+            double mu = 0.0;
+            if (lane < 5) {
+                Df m{0.f, 0.f};
+#pragma unroll
+                for (int o = 0; o < C; ++o) {
+                    const float *po = cl.map_shared_rank(part, o);
+                    m = df_add(m, Df{po[2 * lane], po[2 * lane + 1]});
+                }
+                // mu = (sum q, dv sum w_d q (d = 1..3), dv^2 sum |w|^2 q), w = j - N/2
+                const double sc = lane == 0 ? 1.0 : (lane == 4 ? pa.dv * pa.dv : pa.dv);
+                mu = ((double)m.hi + (double)m.lo) * sc;
+            }
+            double m5[5];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) m5[i] = __shfl_sync(0xffffffffu, mu, i);
+            if (lane < 5) {
+                double l = 0.0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) l = fma(pa.ainv[lane * 5 + k], m5[k], l);
+                lam[lane] = l;
+            }
+        }
+        cl.sync();  // every CTA has read the partials before any leaves; lambda is visible
+        // correction C^T lambda = base(j1, j2) + g(j3)
+        const double dv = pa.dv;
+        if (t < N) {
+            const double v = dv * (double)(t - H);
+            sg[t] = fma(lam[3], v, lam[4] * v * v);
+        }
+        if (act) {
+            const double v1 = dv * (double)(r * JR + t / N - H), v2 = dv * (double)(t % N - H);
+            base[t] = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
         }
     }
     __syncthreads();
-    double *qo = q + off;
+    // coalesced output of the own slab: local value e = (pencil p, j3)
+    double *qo = q + off + (int64_t)r * MS;
     if (mode == 0) {
-        for (int e = threadIdx.x; e < M; e += blockDim.x) qo[e] = D[e];
+        for (int e = t; e < MS; e += S::NT) qo[e] = (double)R[(e / N) * P + e % N];
         return;
     }
-    project_cell(D, qo, pa, mode - 1, x ? x + off : nullptr, y ? y + off : nullptr,
-                 qp ? qp + off : nullptr, a, psh);
+#pragma unroll
+    for (int i = 0; i < IT; ++i) {
+        const int e = t + i * S::NT;
+        if (e < MS) {
+            const int p = e / N, j3 = e % N;
+            const double v = (double)R[p * P + j3] - (base[p] + sg[j3]);
+            qo[e] = v;
+            if (mode == 2) yo[e] = fma(a, v, u[i]);
+            else if (mode == 3) yo[e] = fma(a, w[i] + v, u[i]);
+        }
+    }
 }
 
 namespace {
-template <int N>
+template <int N, int C>
 void fwd_launch(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale,
                 float2 *G, int *status, cudaStream_t st) {
-    using S = FusedShape<N>;
-    dft_fwd_fused_kernel<N><<<s.nslots, S::NT, S::smem, st>>>(f, slot_off, s, root, (float)scale, G, status);
+    using S = FusedShape<N, C>;
+    dft_fwd_fused_kernel<N, C><<<s.nslots * C, S::NT, S::smem_fwd, st>>>(f, slot_off, s, root, (float)scale, G,
+                                                                        status);
 }
-template <int N>
+template <int N, int C>
 void inv_launch(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale,
                 double *q, const ProjArgs &pa, int mode, const double *x, double *y, const double *qp, double a,
                 cudaStream_t st) {
-    using S = FusedShape<N>;
-    dft_inv_fused_kernel<N><<<s.nslots, S::NT, S::smem, st>>>(G, slot_off, s, root, (float)scale, q, pa, mode, x,
-                                                                y, qp, a);
+    using S = FusedShape<N, C>;
+    dft_inv_fused_kernel<N, C><<<s.nslots * C, S::NT, S::smem_inv, st>>>(G, slot_off, s, root, (float)scale, q, pa,
+                                                                        mode, x, y, qp, a);
 }
+template <int N, int C>
+void prepare_one() {
+    using S = FusedShape<N, C>;
+    cudaFuncSetAttribute(dft_fwd_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_fwd);
+    cudaFuncSetAttribute(dft_inv_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_inv);
+}
+template <int N>
+void prepare_n() {
+    prepare_one<N, 1>();
+    prepare_one<N, 2>();
+    prepare_one<N, 4>();
+}
+int norm_split(int split) { return split == 1 || split == 2 ? split : 4; }
 }  // namespace
 
 bool fused_dft_supported(int N) { return N == 8 || N == 12 || N == 16; }
@@ -214,47 +400,40 @@ bool fused_dft_supported(int N) { return N == 8 || N == 12 || N == 16; }
 void fused_dft_prepare(int N) {
     // sets the shared-memory attributes (must happen outside stream capture)
     switch (N) {
-        case 8: {
-            using S = FusedShape<8>;
-            cudaFuncSetAttribute(dft_fwd_fused_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            cudaFuncSetAttribute(dft_inv_fused_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            break;
-        }
-        case 12: {
-            using S = FusedShape<12>;
-            cudaFuncSetAttribute(dft_fwd_fused_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            cudaFuncSetAttribute(dft_inv_fused_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            break;
-        }
-        case 16: {
-            using S = FusedShape<16>;
-            cudaFuncSetAttribute(dft_fwd_fused_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            cudaFuncSetAttribute(dft_inv_fused_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem);
-            break;
-        }
+        case 8: prepare_n<8>(); break;
+        case 12: prepare_n<12>(); break;
+        case 16: prepare_n<16>(); break;
         default: break;
     }
 }
 
+#define BTE_SPLIT_DISPATCH(FN, N, ...)                 \
+    switch (norm_split(split)) {                       \
+        case 1: FN<N, 1>(__VA_ARGS__); break;          \
+        case 2: FN<N, 2>(__VA_ARGS__); break;          \
+        default: FN<N, 4>(__VA_ARGS__); break;         \
+    }
+
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
-                              double scale, float2 *G, int *status, cudaStream_t st) {
+                              double scale, float2 *G, int *status, cudaStream_t st, int split) {
     switch (s.N) {
-        case 8: fwd_launch<8>(f, slot_off, s, root, scale, G, status, st); break;
-        case 12: fwd_launch<12>(f, slot_off, s, root, scale, G, status, st); break;
-        case 16: fwd_launch<16>(f, slot_off, s, root, scale, G, status, st); break;
+        case 8: BTE_SPLIT_DISPATCH(fwd_launch, 8, f, slot_off, s, root, scale, G, status, st) break;
+        case 12: BTE_SPLIT_DISPATCH(fwd_launch, 12, f, slot_off, s, root, scale, G, status, st) break;
+        case 16: BTE_SPLIT_DISPATCH(fwd_launch, 16, f, slot_off, s, root, scale, G, status, st) break;
         default: break;
     }
 }
 
 void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
-                              const double *qp, double a, cudaStream_t st) {
+                              const double *qp, double a, cudaStream_t st, int split) {
     switch (s.N) {
-        case 8: inv_launch<8>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
-        case 12: inv_launch<12>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
-        case 16: inv_launch<16>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
+        case 8: BTE_SPLIT_DISPATCH(inv_launch, 8, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 12: BTE_SPLIT_DISPATCH(inv_launch, 12, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 16: BTE_SPLIT_DISPATCH(inv_launch, 16, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
         default: break;
     }
 }
+#undef BTE_SPLIT_DISPATCH
 
 }  // namespace bte

@@ -71,11 +71,12 @@ void launch_moments(const double *f, const int64_t *slot_off, int s0, int nslots
 // Inverse mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q).
 bool fused_dft_supported(int N);
 void fused_dft_prepare(int N);  // outside stream capture
+// split: CTAs (a thread-block cluster) per cell, 1, 2 or 4 (other values: 4)
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
-                              double scale, float2 *G, int *status, cudaStream_t st);
+                              double scale, float2 *G, int *status, cudaStream_t st, int split = 4);
 void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
-                              const double *qp, double a, cudaStream_t st);
+                              const double *qp, double a, cudaStream_t st, int split = 4);
 
 // Transport (Sec. 3.4) on nx uniform cells of M values. mw_*: wall Maxwellians
 // per velocity (device, M doubles), den_*: sum over the incoming half of |v.n| M_w.

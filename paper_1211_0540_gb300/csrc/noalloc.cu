@@ -144,7 +144,7 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
     DftSeg ds{N, 0, (int)nslots, 0};
     const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
     const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
-    launch_dft_forward_fused(f, d_off, ds, t->d_root32, sf, d_F, c->d_status, st);
+    launch_dft_forward_fused(f, d_off, ds, t->d_root32, sf, d_F, c->d_status, st, c->dft_split);
     ConvParams p{};
     p.items = d_items;
     p.nitems = (int)n;
@@ -161,7 +161,8 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
         pa.N = N;
         pa.dv = t->dv;
         std::memcpy(pa.ainv, t->ainv, sizeof(pa.ainv));
-        launch_dft_inverse_fused(d_Q, d_off, ds, t->d_root32, si, Q, pa, 1, nullptr, nullptr, nullptr, 0.0, st);
+        launch_dft_inverse_fused(d_Q, d_off, ds, t->d_root32, si, Q, pa, 1, nullptr, nullptr, nullptr, 0.0, st,
+                                 c->dft_split);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

@@ -16,6 +16,64 @@ struct ProjShared {
     double tot[5];
 };
 
+// Double-float ("Df") numbers: hi + lo as an unevaluated sum of two FP32
+// values. The building blocks are error-free: TwoSum (Knuth) gives s + e = a + b
+// exactly and fmaf(w, x, -p) the exact error of p = w x. The _rn intrinsics
+// keep the compiler from contracting a product into a following add.
+struct Df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc += x
+__device__ __forceinline__ void df_add(Df &acc, float x) {
+    float s, e;
+    two_sum_f(acc.hi, x, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, e);
+}
+
+// acc += w x
+__device__ __forceinline__ void df_add_prod(Df &acc, float w, float x) {
+    const float p = __fmul_rn(w, x);
+    const float pe = fmaf(w, x, -p);
+    df_add(acc, p);
+    acc.lo = __fadd_rn(acc.lo, pe);
+}
+
+__device__ __forceinline__ Df df_add(Df a, Df b) {
+    float s, e;
+    two_sum_f(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    Df r;
+    two_sum_f(s, e, r.hi, r.lo);
+    return r;
+}
+
+// w a for a small integer w (w hi is split exactly, w lo rounds at 2^-48 of the value)
+__device__ __forceinline__ Df df_mul_int(Df a, float w) {
+    const float p = __fmul_rn(w, a.hi);
+    const float pe = fmaf(w, a.hi, -p);
+    Df r;
+    two_sum_f(p, fmaf(w, a.lo, pe), r.hi, r.lo);
+    return r;
+}
+
+// sum over the 32 lanes (every lane receives it)
+__device__ __forceinline__ Df df_warp_sum(Df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const Df w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+
 // Block-wide sum of 5 values in a fixed order; result valid in all threads.
 // Only the first `active` threads hold data: the other warps skip the
 // shuffles, and five threads add the per-warp partials (FP64 is slow here, so

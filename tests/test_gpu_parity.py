@@ -274,6 +274,12 @@ def test_profiling_and_launch_count_with_graphs(bte):
             c.step(f, 0.01, 1.0, stream=s)
     n, ms = c.profile_read("conv32", s)
     assert n == 6 and ms > 0.0
+    # reading one kernel leaves the others pending
+    for name in ("forward", "inverse"):
+        n, ms = c.profile_read(name, s)
+        assert n == 6 and ms > 0.0, name
+    n, ms = c.profile_read("*", s)  # the six collide calls of the three steps
+    assert n == 6 and ms > 0.0
     # per step: 2 x (fused forward DFT + convolution + fused inverse DFT with projection)
     assert c.launch_count() - n0 == 3 * 6
     c.collide(f, stream=s)
