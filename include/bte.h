@@ -189,7 +189,7 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *                      default: the deepest ring up to 2 that keeps the
  *                      resident CTAs per SM of a one-block ring);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
- *                      (TwoSum) merges (>= 1);
+ *                      (TwoSum) merges (>= 1, default 16);
  *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units;
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
  *                      transforms of N <= 16: 1, 2 or 4 (default 4);

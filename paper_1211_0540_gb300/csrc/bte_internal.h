@@ -132,7 +132,7 @@ struct bte_ctx {
     std::map<std::tuple<int, double, double>, bte::WallTable> walls;  // (N, dv, T_w) -> M_w
     int conv_warps = 4;        // warps per CTA of the convolution kernel
     int conv_stages = 0;       // pipeline depth (blocks in flight per warp); 0 = automatic
-    int conv_merge = 4;        // blocks per compensated (TwoSum) merge
+    int conv_merge = 16;       // blocks per compensated (TwoSum) merge
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
     bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)

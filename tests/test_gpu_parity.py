@@ -73,13 +73,14 @@ def run_collide(bte, N, lam, f, mode, raw=False):
 def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
     f = inputs.homogeneous_cells(N, L, ncells, seed=100 + N + ncells)
     c = ctx_for(bte, ((N, L, lam),))
+    impl0, merge0 = c.get_option("conv_impl"), c.get_option("conv_merge")
     c.set_option("conv_impl", impl)
-    c.set_option("conv_merge", 1 + impl)
+    c.set_option("conv_merge", (1 + impl) * (1 + impl))  # 1, 4, 9: merges inside and across blocks
     try:
         Qg = run_collide(bte, N, lam, f, bte.FP32)
     finally:
-        c.set_option("conv_impl", 2)
-        c.set_option("conv_merge", 4)
+        c.set_option("conv_impl", impl0)
+        c.set_option("conv_merge", merge0)
     Qo = oracle.collide(N, L, lam, f)
     err = np.linalg.norm(Qg - Qo, axis=1) / loss_norm(N, lam, f)
     assert err.max() <= TOL32, err.max()
