@@ -409,9 +409,11 @@ def main():
 # ---------------------------------------------------------------------------
 # Secondary workloads (one JSON line each; the headline is wall-heating).
 
-def _timed_steps(torch, fn, steps, stream, flush):
-    """Device time of each call of fn, L2 flushed before each (outside the events)."""
+def _timed_steps(torch, fn, steps, stream, flush, tag="timed"):
+    """Device time of each call of fn, L2 flushed before each (outside the events);
+    the calls sit in an NVTX range named tag (profilers can select them)."""
     ev = []
+    torch.cuda.nvtx.range_push(tag)
     with torch.cuda.stream(stream):
         for i in range(steps):
             flush.fill_(i & 0xff)
@@ -422,6 +424,7 @@ def _timed_steps(torch, fn, steps, stream, flush):
             e1.record(stream)
             ev.append((e0, e1))
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     return [a.elapsed_time(b) for a, b in ev]
 
 
@@ -669,17 +672,17 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     sampler.start()
     n0 = ctx.launch_count()
     ms_l = _timed_steps(torch, lambda: ctx.collide(fw, Ql, mode=bte.LEARNED, stream=stream), args.steps,
-                        stream, flush)
+                        stream, flush, tag="learned")
     launches = ctx.launch_count() - n0
     clocks = sampler.stop()
     st = ctx.learned_stats(reset=True)
     ms_f = _timed_steps(torch, lambda: ctx.collide(fw, Q32, mode=bte.FP32, stream=stream), args.steps,
-                        stream, flush)
+                        stream, flush, tag="fp32")
     Q64 = torch.empty_like(fw)
     with torch.cuda.stream(stream):
         ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream)
     ms_64 = _timed_steps(torch, lambda: ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream), 1,
-                         stream, flush)
+                         stream, flush, tag="fp64")
     Qnn = ctx.collide(fw, mode=bte.LEARNED, fallback=False, stream=stream)
     ctx.sync_status(stream)
     a32, al, ann = (x.cpu().numpy().reshape(nx, M) for x in (Q32, Ql, Qnn))

@@ -468,23 +468,17 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
     bte_status s;
     if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * (size_t)B->nslots * (2 * c->ind->S + 1))) != BTE_OK)
         return s;
-    // 1. surrogate in chunks of up to 8192 cells
+    // 1. surrogate in chunks of up to 8192 cells, 2. its output projected (fused)
     const int64_t chunk = 8192;
     for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
         const int n = (int)std::min<int64_t>(chunk, ncells - c0);
         if (!m->ensure_batch(n)) return fail(c, BTE_ENOMEM, "learned mode: activations");
-        std::vector<int64_t> rows(n);
-        for (int i = 0; i < n; ++i) rows[i] = (c0 + i) * cell_M(t);
-        cudaError_t e = cudaMemcpyAsync(m->rowoff, rows.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: upload");
-        if (m->run(f, nullptr, n, false, c->d_status, st)) return fail(c, BTE_ECUDA, "learned mode: surrogate");
-        launch_mlp_post(m->Y, m->rho, m->rowoff, n, m->M, m->s_out, Q, st);
+        const int64_t o = c0 * cell_M(t);
+        if (m->run(f + o, nullptr, n, false, c->d_status, st, m->rowuni))
+            return fail(c, BTE_ECUDA, "learned mode: surrogate");
+        launch_post_project(m->Y, m->rho, n, t->N, m->s_out, proj_args(t), Q + o, st);
         count_launches(c, 5);
     }
-    // 2. conservation projection
-    launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(t), 0, nullptr, nullptr, nullptr, 0.0, st);
-    count_launches(c, 1);
     if (flags & BTE_FLAG_NO_FALLBACK) {
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned mode: launch");
@@ -499,7 +493,7 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
     float *e2 = (float *)c->scratch[SC_MISC];
     float *d2 = e2 + (size_t)B->nslots * c->ind->S;
     float *ind = d2 + (size_t)B->nslots * c->ind->S;
-    launch_indicator(*c->ind, (const float2 *)c->scratch[SC_F], (const float2 *)c->scratch[SC_QH], t->N, sg.eoff,
+    launch_indicator(*c->ind, *t, (const float2 *)c->scratch[SC_F], (const float2 *)c->scratch[SC_QH], sg.eoff,
                      sg.nslots, sg.nvalid, e2, d2, ind, st);
     count_launches(c, 4);
     std::vector<float> h(B->nslots);

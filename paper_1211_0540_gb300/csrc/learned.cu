@@ -1,58 +1,115 @@
 // Learned collision path (mode BTE_LEARNED): surrogate -> conservation
 // projection -> residual indicator -> exact fallback.
 //
-// Indicator (per cell). The exact operator is evaluated at S sampled Fourier
-// modes zeta_k (fixed, seeded, drawn from |k'|_inf <= N/4 without zeta = 0):
+// Indicator (per cell). The exact operator is evaluated on S sampled zeta
+// pencils (k1, k2) (fixed, seeded, |k1'|, |k2'| <= N/4), all N modes k3 of each:
 //   Qhat(k)  = sum_m Ghat(xi_m, zeta_k) dz^3 fhat_m fhat_{k-m+N/2}     (Sec. 3.2)
 //   Qhat-(k) = the same sum with the loss term of Ghat only,
 // and compared with the forward transform of the projected surrogate output:
 //   ind = ||Fhat[P Q_nn](k) - Qhat(k)||_S / ||Qhat-(k)||_S,
-// i.e. the parity metric of the fast path restricted to S modes. Cells with
-// ind > tol are recomputed with the FP32 operator. Cost of the check: S
-// zeta points out of N^3 of the convolution (64 / 4096 = 1.6 % at N = 16).
+// i.e. the parity metric of the fast path restricted to S N modes. Cells with
+// ind > tol are recomputed with the FP32 operator. Cost of the check: S of the
+// N^2 pencils of the convolution (4 / 256 = 1.6 % at N = 16).
 #include <algorithm>
 #include <cmath>
 #include <random>
 #include <vector>
 
-#include "kernels.h"
 #include "learned.h"
+#include "project.cuh"
 
 namespace bte {
 
 namespace {
 
-// One warp per (sample, group): lane = cell. Accumulates the exact and loss
-// sums at the sampled mode and the squared differences.
-__global__ void __launch_bounds__(32) indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN,
-                                                       const float2 *__restrict__ W, const int *__restrict__ woff,
-                                                       const int *__restrict__ kidx, int N, int64_t eoff,
-                                                       int nslots, float *err2, float *den2) {
-    const int s = blockIdx.x, g = blockIdx.y, lane = threadIdx.x;
-    const int M = N * N * N, h = N / 2;
-    const int k = kidx[s];
-    const int k1 = k / (N * N), k2 = (k / N) % N, k3 = k % N;
-    const float2 *Fg = F + eoff + (int64_t)g * M * kLanes;
-    const float2 *w = W + woff[s];
-    float fr = 0.f, fi = 0.f, lr = 0.f, li = 0.f;
-    for (int m1 = max(0, k1 - h + 1); m1 <= min(N - 1, k1 + h); ++m1)
-        for (int m2 = max(0, k2 - h + 1); m2 <= min(N - 1, k2 + h); ++m2)
-            for (int m3 = max(0, k3 - h + 1); m3 <= min(N - 1, k3 + h); ++m3) {
-                const float2 ww = *w++;
-                const float2 a = Fg[(int64_t)((m1 * N + m2) * N + m3) * kLanes + lane];
-                const int n = ((k1 - m1 + h) * N + (k2 - m2 + h)) * N + (k3 - m3 + h);
-                const float2 b = Fg[(int64_t)n * kLanes + lane];
-                const float pr = a.x * b.x - a.y * b.y, pi = a.x * b.y + a.y * b.x;
-                fr = fmaf(ww.x, pr, fr);
-                fi = fmaf(ww.x, pi, fi);
-                lr = fmaf(ww.y, pr, lr);
-                li = fmaf(ww.y, pi, li);
+// One CTA of kIndWarps warps per (sampled pencil, group), lane = cell: the
+// warps take the pencil's kept (m1, m2) blocks in turn (the block layout of the
+// FP32 table: unordered pairs, weights Ghat(k,m) + Ghat(k,n)); each block's a
+// and b rows are loaded once into registers and serve all N outputs k3, with
+// the full and the loss weights side by side. Partial sums are added across
+// the warps in a fixed order, then compared with the transform of the
+// projected surrogate output.
+constexpr int kIndWarps = 8;
+
+template <int N>
+__global__ void __launch_bounds__(32 * kIndWarps)
+indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, const float *__restrict__ Wfull,
+                 const float *__restrict__ Wloss, const uint32_t *__restrict__ desc, const IndPencil *__restrict__ pens,
+                 int cpad, int64_t eoff, int nslots, float *err2, float *den2) {
+    constexpr int M = N * N * N, H = N / 2;
+    extern __shared__ __align__(16) float red[];  // [kIndWarps][4 N][32]
+    const int p = blockIdx.x, g = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const IndPencil pen = pens[p];
+    const int k1 = pen.kk / N, k2 = pen.kk % N;
+    const float2 *Fg = F + eoff + (int64_t)g * M * kLanes + lane;
+    float acc[4 * N];  // full (re, im) per k3, then loss (re, im) per k3
+#pragma unroll
+    for (int i = 0; i < 4 * N; ++i) acc[i] = 0.f;
+    for (int b = warp; b < pen.nblocks; b += kIndWarps) {
+        const uint32_t d = desc[pen.desc_off + b];
+        const int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16), n1 = k1 - m1 + H, n2 = k2 - m2 + H;
+        float2 av[N], bv[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            av[i] = Fg[(int64_t)((m1 * N + m2) * N + i) * kLanes];
+            bv[i] = Fg[(int64_t)((n1 * N + n2) * N + i) * kLanes];
+        }
+        const float4 *wf = reinterpret_cast<const float4 *>(Wfull + pen.wofs_full + (size_t)b * cpad);
+        const float4 *wl = reinterpret_cast<const float4 *>(Wloss + pen.wofs_loss + (size_t)b * cpad);
+        float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = f4;
+        int wi = 0;
+#pragma unroll
+        for (int m3 = 0; m3 < N; ++m3)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const int n3 = j - m3 + H;
+                if (n3 >= 0 && n3 < N) {
+                    if ((wi & 3) == 0) {
+                        f4 = wf[wi >> 2];
+                        l4 = wl[wi >> 2];
+                    }
+                    const int q = wi & 3;
+                    const float wF = q == 0 ? f4.x : q == 1 ? f4.y : q == 2 ? f4.z : f4.w;
+                    const float wL = q == 0 ? l4.x : q == 1 ? l4.y : q == 2 ? l4.z : l4.w;
+                    ++wi;
+                    const float pr = av[m3].x * bv[n3].x - av[m3].y * bv[n3].y;
+                    const float pi = av[m3].x * bv[n3].y + av[m3].y * bv[n3].x;
+                    acc[2 * j] = fmaf(wF, pr, acc[2 * j]);
+                    acc[2 * j + 1] = fmaf(wF, pi, acc[2 * j + 1]);
+                    acc[2 * N + 2 * j] = fmaf(wL, pr, acc[2 * N + 2 * j]);
+                    acc[2 * N + 2 * j + 1] = fmaf(wL, pi, acc[2 * N + 2 * j + 1]);
+                }
             }
-    const float2 q = QN[eoff + (int64_t)g * M * kLanes + (int64_t)k * kLanes + lane];
-    const float dr = q.x - fr, di = q.y - fi;
-    const int slot = g * kLanes + lane;
-    err2[(size_t)s * nslots + slot] = dr * dr + di * di;
-    den2[(size_t)s * nslots + slot] = lr * lr + li * li;
+    }
+#pragma unroll
+    for (int i = 0; i < 4 * N; ++i) red[(warp * 4 * N + i) * kLanes + lane] = acc[i];
+    __syncthreads();
+    if (warp == 0) {
+        float e = 0.f, dn = 0.f;
+        const float2 *qn = QN + eoff + (int64_t)g * M * kLanes + (int64_t)pen.kk * N * kLanes + lane;
+        for (int j = 0; j < N; ++j) {
+            float fr = 0.f, fi = 0.f, lr = 0.f, li = 0.f;
+            for (int w = 0; w < kIndWarps; ++w) {
+                const float *rw = red + (size_t)w * 4 * N * kLanes + lane;
+                fr += rw[(2 * j) * kLanes];
+                fi += rw[(2 * j + 1) * kLanes];
+                lr += rw[(2 * N + 2 * j) * kLanes];
+                li += rw[(2 * N + 2 * j + 1) * kLanes];
+            }
+            const float2 q = qn[(int64_t)j * kLanes];
+            const float dr = q.x - fr, di = q.y - fi;
+            e += dr * dr + di * di;
+            dn += lr * lr + li * li;
+        }
+        const int slot = g * kLanes + lane;
+        err2[(size_t)p * nslots + slot] = e;
+        den2[(size_t)p * nslots + slot] = dn;
+    }
+}
+
+template <int N>
+constexpr size_t ind_smem() {
+    return sizeof(float) * kIndWarps * 4 * N * kLanes;
 }
 
 __global__ void indicator_reduce_kernel(const float *__restrict__ err2, const float *__restrict__ den2, int S,
@@ -67,42 +124,149 @@ __global__ void indicator_reduce_kernel(const float *__restrict__ err2, const fl
     ind[c] = c < nvalid ? sqrtf(e) / fmaxf(sqrtf(d), 1e-30f) : 0.f;
 }
 
+// Surrogate output to the caller's cells with the conservation projection of
+// Sec. 3.3 fused in: Q = P_N(c Y), c = rho^2 / s_out per cell. One CTA per
+// cell, one thread per pencil (j1, j2): the moments of Y are accumulated in
+// double-float FP32 (the values are FP32), mu(Q) = c mu(Y) and lambda are
+// formed in FP64, and Q_j = c Y_j - C_j^T lambda is written in FP64 on a
+// coalesced mapping (about four FP64 operations per value).
+template <int N>
+__global__ void __launch_bounds__((N * N + 31) / 32 * 32)
+post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho, float s_out, ProjArgs pa,
+                    double *__restrict__ Q) {
+    constexpr int M = N * N * N, NN = N * N, H = N / 2, NT = (NN + 31) / 32 * 32, NW = NT / 32;
+    const int r = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const float *y = Y + (size_t)r * M;
+    double *q = Q + (size_t)r * M;
+    __shared__ float red[NW][10];
+    __shared__ double base[NN], sg[N], lam[5];
+    const double c = rho[r] * rho[r] / (double)s_out;
+    Df mom[5];
+    if (t < NN) {
+        Df s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
+        const float *yp = y + t * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float v = yp[j];
+            df_add(s0, v);
+            df_add_prod(s1, (float)(j - H), v);
+            df_add_prod(s2, (float)((j - H) * (j - H)), v);
+        }
+        const int w1 = t / N - H, w2 = t % N - H;
+        mom[0] = s0;
+        mom[1] = df_mul_int(s0, (float)w1);
+        mom[2] = df_mul_int(s0, (float)w2);
+        mom[3] = s1;
+        mom[4] = df_add(df_mul_int(s0, (float)(w1 * w1 + w2 * w2)), s2);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] = Df{0.f, 0.f};
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            red[warp][2 * i] = mom[i].hi;
+            red[warp][2 * i + 1] = mom[i].lo;
+        }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] = lane < NW ? Df{red[lane][2 * i], red[lane][2 * i + 1]} : Df{0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
+        double mu = 0.0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            if (lane == i) mu = ((double)mom[i].hi + (double)mom[i].lo) * c;
+        mu *= lane == 0 ? 1.0 : (lane == 4 ? pa.dv * pa.dv : pa.dv);
+        double m5[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) m5[i] = __shfl_sync(0xffffffffu, mu, i);
+        if (lane < 5) {
+            double l = 0.0;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) l = fma(pa.ainv[lane * 5 + k], m5[k], l);
+            lam[lane] = l;
+        }
+    }
+    __syncthreads();
+    const double dv = pa.dv;
+    if (t < N) {
+        const double v = dv * (double)(t - H);
+        sg[t] = fma(lam[3], v, lam[4] * v * v);
+    }
+    if (t < NN) {
+        const double v1 = dv * (double)(t / N - H), v2 = dv * (double)(t % N - H);
+        base[t] = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
+    }
+    __syncthreads();
+    for (int e = t; e < M; e += NT) q[e] = fma(c, (double)y[e], -(base[e / N] + sg[e % N]));
+}
+
 }  // namespace
 
-int build_indicator_table(const Table &t, int S, uint64_t seed, IndicatorTable &out) {
+int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTable &out) {
     const int N = t.N, h = N / 2, q = N / 4;
+    const int S = std::max(1, modes / N);
     const double dz3 = t.dz * t.dz * t.dz;
     const double c = std::sqrt(2.0 / 3.14159265358979323846);
     std::mt19937_64 rng(seed);
     std::uniform_int_distribution<int> d(-q, q);
-    std::vector<int> ks;
-    while ((int)ks.size() < S) {
-        const int a = d(rng), b = d(rng), e = d(rng);
-        if (a == 0 && b == 0 && e == 0) continue;
-        const int k = ((a + h) * N + (b + h)) * N + (e + h);
-        if (std::find(ks.begin(), ks.end(), k) == ks.end()) ks.push_back(k);
+    std::vector<int> kks;
+    while ((int)kks.size() < S) {
+        const int kk = (d(rng) + h) * N + (d(rng) + h);
+        if (std::find(kks.begin(), kks.end(), kk) == kks.end()) kks.push_back(kk);
     }
-    std::vector<float2> w;
-    std::vector<int> off;
-    for (int k : ks) {
-        off.push_back((int)w.size());
-        const int k1 = k / (N * N), k2 = (k / N) % N, k3 = k % N;
-        for (int m1 = std::max(0, k1 - h + 1); m1 <= std::min(N - 1, k1 + h); ++m1)
-            for (int m2 = std::max(0, k2 - h + 1); m2 <= std::min(N - 1, k2 + h); ++m2)
-                for (int m3 = std::max(0, k3 - h + 1); m3 <= std::min(N - 1, k3 + h); ++m3) {
-                    const int s = (m1 - h) * (m1 - h) + (m2 - h) * (m2 - h) + (m3 - h) * (m3 - h);
-                    const double full = t.ghat(k1, k2, k3, m1, m2, m3) * dz3;
-                    const double loss = -c * t.J[s] * dz3;
-                    w.push_back(make_float2((float)full, (float)loss));
+    // loss weights of the sampled pencils in the FP32 table's block layout (one k3 tile, N <= 16)
+    const int cpad = t.cpad[0];
+    std::vector<float> wl;
+    std::vector<IndPencil> pens;
+    std::vector<uint32_t> desc(t.n_desc);
+    if (cudaMemcpy(desc.data(), t.d_desc, sizeof(uint32_t) * t.n_desc, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    for (int kk : kks) {
+        IndPencil pn{};
+        pn.kk = kk;
+        pn.desc_off = (int)t.desc_off[kk];
+        pn.nblocks = (int)t.nblocks[kk];
+        pn.wofs_full = t.wofs[kk];
+        pn.wofs_loss = wl.size();
+        const int k1 = kk / N, k2 = kk % N;
+        for (int b = 0; b < pn.nblocks; ++b) {
+            const uint32_t dd = desc[pn.desc_off + b];
+            const int m1 = (int)(dd & 0xffffu), m2 = (int)(dd >> 16), n1 = k1 - m1 + h, n2 = k2 - m2 + h;
+            const bool pair = !(m1 == n1 && m2 == n2);
+            const size_t base = wl.size();
+            wl.resize(base + cpad, 0.0f);
+            size_t wi = base;
+            for (int m3 = 0; m3 < N; ++m3)
+                for (int k3 = 0; k3 < N; ++k3) {
+                    const int n3 = k3 - m3 + h;
+                    if (n3 < 0 || n3 >= N) continue;
+                    const int sm = (m1 - h) * (m1 - h) + (m2 - h) * (m2 - h) + (m3 - h) * (m3 - h);
+                    double g = -c * t.J[sm];
+                    if (pair) {
+                        const int sn = (n1 - h) * (n1 - h) + (n2 - h) * (n2 - h) + (n3 - h) * (n3 - h);
+                        g += -c * t.J[sn];
+                    }
+                    wl[wi++] = (float)(g * dz3);
                 }
+        }
+        pens.push_back(pn);
     }
     out.S = S;
-    cudaError_t e = cudaMalloc(&out.d_w, sizeof(float2) * w.size());
-    if (e == cudaSuccess) e = cudaMalloc(&out.d_off, sizeof(int) * S);
-    if (e == cudaSuccess) e = cudaMalloc(&out.d_k, sizeof(int) * S);
-    if (e == cudaSuccess) e = cudaMemcpy(out.d_w, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(out.d_off, off.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(out.d_k, ks.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&out.d_wloss, sizeof(float) * std::max<size_t>(wl.size(), 4));
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_pen, sizeof(IndPencil) * S);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_wloss, wl.data(), sizeof(float) * wl.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_pen, pens.data(), sizeof(IndPencil) * S, cudaMemcpyHostToDevice);
+    // shared memory of the cross-warp reduction (set outside any stream capture)
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(indicator_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ind_smem<8>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(indicator_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ind_smem<12>());
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(indicator_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ind_smem<16>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return -1;
@@ -111,18 +275,41 @@ int build_indicator_table(const Table &t, int S, uint64_t seed, IndicatorTable &
 }
 
 void free_indicator_table(IndicatorTable &t) {
-    cudaFree(t.d_w);
-    cudaFree(t.d_off);
-    cudaFree(t.d_k);
-    t.d_w = nullptr;
-    t.d_off = nullptr;
-    t.d_k = nullptr;
+    cudaFree(t.d_wloss);
+    cudaFree(t.d_pen);
+    t.d_wloss = nullptr;
+    t.d_pen = nullptr;
 }
 
-void launch_indicator(const IndicatorTable &it, const float2 *F, const float2 *QN, int N, int64_t eoff, int nslots,
-                      int nvalid, float *err2, float *den2, float *ind, cudaStream_t st) {
+void launch_post_project(const float *Y, const double *rho, int B, int N, float s_out, const ProjArgs &pa, double *Q,
+                         cudaStream_t st) {
+    switch (N) {
+        case 8: post_project_kernel<8><<<B, 64, 0, st>>>(Y, rho, s_out, pa, Q); break;
+        case 12: post_project_kernel<12><<<B, 160, 0, st>>>(Y, rho, s_out, pa, Q); break;
+        case 16: post_project_kernel<16><<<B, 256, 0, st>>>(Y, rho, s_out, pa, Q); break;
+        default: break;
+    }
+}
+
+void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
+                      int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st) {
     dim3 grid(it.S, nslots / kLanes);
-    indicator_kernel<<<grid, 32, 0, st>>>(F, QN, it.d_w, it.d_off, it.d_k, N, eoff, nslots, err2, den2);
+    switch (t.N) {
+        case 8:
+            indicator_kernel<8><<<grid, 32 * kIndWarps, ind_smem<8>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
+                                                                           it.d_pen, t.cpad[0], eoff, nslots, err2, den2);
+            break;
+        case 12:
+            indicator_kernel<12><<<grid, 32 * kIndWarps, ind_smem<12>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
+                                                                             it.d_pen, t.cpad[0], eoff, nslots, err2,
+                                                                             den2);
+            break;
+        default:
+            indicator_kernel<16><<<grid, 32 * kIndWarps, ind_smem<16>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
+                                                                             it.d_pen, t.cpad[0], eoff, nslots, err2,
+                                                                             den2);
+            break;
+    }
     indicator_reduce_kernel<<<(nslots + 255) / 256, 256, 0, st>>>(err2, den2, it.S, nslots, nvalid, ind);
 }
 

@@ -3,21 +3,33 @@
 
 #include <cstdint>
 
-#include "bte_internal.h"
+#include "kernels.h"
 
 namespace bte {
 
-struct IndicatorTable {
-    int S = 0;
-    float2 *d_w = nullptr;  // per sample: (full, loss) weights times dz^3 over the valid box of k
-    int *d_off = nullptr;   // first weight of each sample
-    int *d_k = nullptr;     // sampled zeta indices
+// Sampled pencils of the indicator: for pencil i, the kept (m1, m2) blocks of
+// zeta pencil kk = k1 N + k2 (descriptors and full weights of the FP32 table)
+// and the loss-term weights of the same blocks (d_wloss + wofs_loss).
+struct IndPencil {
+    int kk, desc_off, nblocks, pad;
+    uint64_t wofs_full, wofs_loss;
 };
 
-int build_indicator_table(const Table &t, int S, uint64_t seed, IndicatorTable &out);
+struct IndicatorTable {
+    int S = 0;                     // sampled pencils (S x N sampled modes)
+    float *d_wloss = nullptr;      // loss weights of the sampled pencils (pair-symmetrised, times dz^3)
+    IndPencil *d_pen = nullptr;
+};
+
+// modes: about this many sampled modes (pencils = modes / N, at least 1)
+int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTable &out);
 void free_indicator_table(IndicatorTable &t);
-// ind[slot] for the slots of one segment (eoff: its offset in the group buffers).
-void launch_indicator(const IndicatorTable &it, const float2 *F, const float2 *QN, int N, int64_t eoff, int nslots,
-                      int nvalid, float *err2, float *den2, float *ind, cudaStream_t st);
+// Q = P_N(rho^2 Y / s_out) for B contiguous cells of N^3 values (N <= 16).
+void launch_post_project(const float *Y, const double *rho, int B, int N, float s_out, const ProjArgs &pa, double *Q,
+                         cudaStream_t st);
+// ind[slot] for the slots of one segment (eoff: its offset in the group buffers);
+// err2, den2: S * nslots floats of scratch.
+void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
+                      int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st);
 
 }  // namespace bte

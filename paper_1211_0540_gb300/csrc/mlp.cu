@@ -1,4 +1,4 @@
-// Learned surrogate of the collision operator (a BASELINE-mandated addition; the
+// Learned surrogate of the collision operator (an addition to the method: the
 // paper has no learned part): a residual MLP trained on (f, Q(f)) pairs that
 // the operator itself produces.
 //   x  = s_in  * f / rho                (rho = sum f dv^3, the cell's mass)
@@ -20,8 +20,8 @@
 #include <vector>
 
 #include "gemm_tc.h"
-#include "kernels.h"
 #include "mlp.h"
+#include "project.cuh"
 
 namespace bte {
 
@@ -37,30 +37,44 @@ __device__ __forceinline__ float gelu_grad(float x) {
 }
 
 // One CTA per batch row: rho, x (bf16, optionally transposed) and the target.
+// Each value is converted to FP32 once (kept in shared memory, M <= 4096) and
+// rho is summed in double-float FP32: its ~1e-7 relative precision only
+// scales the surrogate's input and output, whose conservation the projection
+// restores exactly.
 __global__ void __launch_bounds__(kT) prep_kernel(const double *__restrict__ f, const int64_t *__restrict__ off,
                                                    int B, int M, double dv3, float s_in, __nv_bfloat16 *X,
                                                    __nv_bfloat16 *Xt, int ldt, double *rho_out,
                                                    const double *__restrict__ Q, float s_out, float *T) {
-    const int r = blockIdx.x;
+    const int r = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const double *fr = f + off[r];
-    __shared__ double red[kT / 32];
+    __shared__ float xs[4096];
+    __shared__ float red[kT / 32][2];
     __shared__ double rho_s;
-    double s = 0.0;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) s += fr[j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    Df s{0.f, 0.f};
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        const float v = (float)fr[j];
+        xs[j] = v;
+        df_add(s, v);
+    }
+    s = df_warp_sum(s);
+    if (lane == 0) {
+        red[warp][0] = s.hi;
+        red[warp][1] = s.lo;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < kT / 32; ++w) t += red[w];
-        rho_s = t * dv3;
-        if (rho_out) rho_out[r] = rho_s;
+    if (warp == 0) {
+        s = lane < kT / 32 ? Df{red[lane][0], red[lane][1]} : Df{0.f, 0.f};
+        s = df_warp_sum(s);
+        if (lane == 0) {
+            rho_s = ((double)s.hi + (double)s.lo) * dv3;
+            if (rho_out) rho_out[r] = rho_s;
+        }
     }
     __syncthreads();
     const double rho = rho_s;
     const float a = (float)((double)s_in / rho);
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const __nv_bfloat16 x = __float2bfloat16_rn((float)fr[j] * a);
+        const __nv_bfloat16 x = __float2bfloat16_rn(xs[j] * a);
         X[(size_t)r * M + j] = x;
         if (Xt) Xt[(size_t)j * ldt + r] = x;
     }
@@ -192,6 +206,8 @@ bool Mlp::ensure_batch(int B) {
         return cudaMemset(*p, 0, bytes) == cudaSuccess;
     };
     const size_t bm = (size_t)Bp * M, bh = (size_t)Bp * H;
+    std::vector<int64_t> uni((size_t)Bp);
+    for (int i = 0; i < Bp; ++i) uni[i] = (int64_t)i * M;
     bool ok = A((void **)&X, 2 * bm) && A((void **)&Xt, 2 * bm) && A((void **)&H1, 2 * bh) && A((void **)&H1t, 2 * bh) &&
               A((void **)&H2, 2 * bh) && A((void **)&H2t, 2 * bh) && A((void **)&dY, 2 * bm) &&
               A((void **)&dYt, 2 * bm) && A((void **)&dZ2, 2 * bh) && A((void **)&dZ2t, 2 * bh) &&
@@ -199,7 +215,8 @@ bool Mlp::ensure_batch(int B) {
               A((void **)&Y, 4 * bm) && A((void **)&T, 4 * bm) && A((void **)&dYf, 4 * bm) &&
               A((void **)&dH2, 4 * bh) && A((void **)&dH1, 4 * bh) && A((void **)&dZf, 4 * bh) &&
               A((void **)&rho, 8 * (size_t)Bp) && A((void **)&loss_rows, 8 * (size_t)Bp) &&
-              A((void **)&rowoff, 8 * (size_t)Bp);
+              A((void **)&rowoff, 8 * (size_t)Bp) && A((void **)&rowuni, 8 * (size_t)Bp) &&
+              cudaMemcpy(rowuni, uni.data(), 8 * (size_t)Bp, cudaMemcpyHostToDevice) == cudaSuccess;
     if (ok) bcap = Bp;
     return ok;
 }

@@ -24,7 +24,8 @@ struct Mlp {
     float *Z1 = nullptr, *Z2 = nullptr, *Y = nullptr, *T = nullptr, *dYf = nullptr, *dH2 = nullptr, *dH1 = nullptr,
           *dZf = nullptr;
     double *rho = nullptr, *loss_rows = nullptr;
-    int64_t *rowoff = nullptr;
+    int64_t *rowoff = nullptr;  // row offsets of the current call (uploaded)
+    int64_t *rowuni = nullptr;  // i * M for i < bcap: rows of a contiguous block of cells
     std::vector<void *> allocs, act_allocs;
 
     ~Mlp();
