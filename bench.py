@@ -160,6 +160,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def max_over_ranks(value, device):
+    """Largest value over the ranks of the default process group: the job's
+    time is the slowest rank's. A plain float with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, total_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (total_ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -268,12 +285,8 @@ def main():
         dist.barrier()
     clocks = sampler.stop()
     ctx.sync_status(stream)
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = EVALS_PER_STEP * args.steps * world / (total_ms * 1e-3)
+    total_ms = max_over_ranks(float(sum(step_ms)), "cuda")
+    value = job_rate(EVALS_PER_STEP * args.steps, world, total_ms)
 
     # per-stage device times, in a separate pass (events around every stage
     # lengthen the step, so the timed steps above carry them around conv32 only)
@@ -310,12 +323,8 @@ def main():
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
     ctx.profile_read("*", stream)
-    e2e_total = float(sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = EVALS_PER_STEP * args.steps * world / (e2e_total * 1e-3)
+    e2e_total = max_over_ranks(float(sum(e2e_ms)), "cuda")
+    e2e_value = job_rate(EVALS_PER_STEP * args.steps, world, e2e_total)
     nbytes = f.numel() * 8
 
     # plain FP64 GPU operator on the same state (the metric's comparator)

@@ -291,3 +291,15 @@ def test_profiling_and_launch_count_with_graphs(bte):
     assert float(x.sum()) == 8.0
     c.sync_status(s)
     c.close()
+
+
+@pytest.mark.gpu
+def test_collide_matches_golden_fixture(bte):
+    """Both GPU paths against the stored oracle fixture (tests/golden)."""
+    from test_oracle_golden import load_golden
+    d, f, Qref = load_golden()
+    N, lam = d["N"], d["lambda"]
+    Qg64 = run_collide(bte, N, lam, f, bte.FP64_PLAIN)[0]
+    Qg32 = run_collide(bte, N, lam, f, bte.FP32)[0]
+    assert np.abs(Qg64 - Qref).max() <= TOL64 * np.abs(Qref).max()
+    assert np.linalg.norm(Qg32 - Qref) / float(d["loss_norm"]) <= TOL32
