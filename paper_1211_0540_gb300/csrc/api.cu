@@ -62,8 +62,21 @@ bte_status cuda_fail(bte_ctx *c, cudaError_t e, const char *what) {
     return fail(c, BTE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Forget every captured step graph (they bake in scratch pointers, options and
+// profiling events); the next bte_step captures again. Waits for the device.
+void drop_graphs(bte_ctx *c) {
+    cudaDeviceSynchronize();
+    for (auto &kv : c->graphs) {
+        cudaGraphExecDestroy(kv.second.exec);
+        for (auto &pe : kv.second.prof) c->ev_free.push_back({pe.a, pe.b});
+    }
+    c->graphs.clear();
+    c->pending.clear();
+}
+
 bte_status ensure_scratch(bte_ctx *c, int id, size_t bytes) {
     if (c->scratch_bytes[id] >= bytes) return BTE_OK;
+    if (c->scratch[id]) drop_graphs(c);  // graphs captured earlier hold the old buffer
     cudaFree(c->scratch[id]);
     c->scratch[id] = nullptr;
     c->scratch_bytes[id] = 0;
@@ -574,7 +587,7 @@ void bte_destroy(bte_ctx *c) {
         free_indicator_table(*c->ind);
         delete c->ind;
     }
-    for (int i = 0; i < 8; ++i) cudaFree(c->scratch[i]);
+    for (int i = 0; i < bte_ctx::kScratch; ++i) cudaFree(c->scratch[i]);
     cudaFree(c->d_status);
     cudaFree(c->d_counter);
     cudaFree(c->d_wall);
@@ -836,13 +849,7 @@ bte_status bte_set_option(bte_ctx *c, const char *name, int value) {
     if (!slot) return fail(c, BTE_EINVAL, std::string("unknown option ") + name);
     if (value < lo || value > hi) return fail(c, BTE_EINVAL, std::string("option out of range: ") + name);
     if (*slot != value) {
-        cudaDeviceSynchronize();
-        for (auto &kv : c->graphs) {
-            cudaGraphExecDestroy(kv.second.exec);
-            for (auto &pe : kv.second.prof) c->ev_free.push_back({pe.a, pe.b});
-        }
-        c->graphs.clear();
-        c->pending.clear();
+        drop_graphs(c);
         *slot = value;
     }
     return BTE_OK;

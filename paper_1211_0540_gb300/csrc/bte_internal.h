@@ -116,8 +116,9 @@ struct bte_ctx {
     int *d_status = nullptr;
     unsigned *d_counter = nullptr;
     // grow-only scratch
-    void *scratch[8] = {nullptr};
-    size_t scratch_bytes[8] = {0};
+    static constexpr int kScratch = 16;
+    void *scratch[kScratch] = {nullptr};
+    size_t scratch_bytes[kScratch] = {0};
     std::map<std::string, bte::Batch *> batches;
     std::map<bte::GraphKey, bte::GraphRec> graphs;
     // profiling / launch accounting

@@ -303,3 +303,27 @@ def test_collide_matches_golden_fixture(bte):
     Qg32 = run_collide(bte, N, lam, f, bte.FP32)[0]
     assert np.abs(Qg64 - Qref).max() <= TOL64 * np.abs(Qref).max()
     assert np.linalg.norm(Qg32 - Qref) / float(d["loss_norm"]) <= TOL32
+
+
+def test_step_graph_survives_scratch_growth(bte):
+    """A step graph captured on a small batch is replayed correctly after a
+    larger batch has grown (reallocated) the scratch buffers it used."""
+    N, lam = 8, 1.0
+    c = bte.Context(0)
+    c.init_weights([(N, L, lam)])
+    s = torch.cuda.Stream()
+    f_small = inputs.homogeneous_cells(N, L, 5, seed=31)
+    ft = torch.from_numpy(f_small.copy()).cuda()
+    ref = f_small.copy()
+    with torch.cuda.stream(s):
+        c.step(ft, 0.01, 1.0, mode=bte.FP32, stream=s)  # captured
+    ref = oracle.rk2_homogeneous(N, L, lam, ref, 0.01, 1.0)
+    big = torch.from_numpy(inputs.homogeneous_cells(N, L, 300, seed=32)).cuda()
+    c.collide(big, mode=bte.FP32, stream=s)  # grows the scratch buffers
+    with torch.cuda.stream(s):
+        c.step(ft, 0.01, 1.0, mode=bte.FP32, stream=s)  # same key as the first capture
+    c.sync_status(s)
+    ref = oracle.rk2_homogeneous(N, L, lam, ref, 0.01, 1.0)
+    d = np.abs(ft.cpu().numpy() - ref).max() / np.abs(f_small).max()
+    assert d <= 1e-7, d
+    c.close()
