@@ -566,9 +566,6 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk,
                      "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
                      "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
-        "stage_ms_per_step": dict({k: v / args.steps for k, v in part_ms.items()},
-                                  note="separate pass with events around every stage (each figure includes "
-                                       "the graph's launch gap before the stage)"),
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
         "accuracy": {"rel_l2_loss_norm_max": float(rel.max()), "rel_l2_loss_norm_median": float(np.median(rel)),
                      "rel_l2_plain_max": float(relp.max()), "cells_checked": pick.tolist(),

@@ -62,16 +62,28 @@ bte_status cuda_fail(bte_ctx *c, cudaError_t e, const char *what) {
     return fail(c, BTE_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Events recorded inside captured graphs belong to the graphs; replays also
+// list them in c->pending, so pending entries return to the free pool only
+// when no graph owns their events (an event must be destroyed exactly once).
+bool owned_by_graph(const bte_ctx *c, cudaEvent_t ev) {
+    for (const auto &kv : c->graphs)
+        for (const ProfEntry &pe : kv.second.prof)
+            if (pe.a == ev) return true;
+    return false;
+}
+
 // Forget every captured step graph (they bake in scratch pointers, options and
 // profiling events); the next bte_step captures again. Waits for the device.
 void drop_graphs(bte_ctx *c) {
     cudaDeviceSynchronize();
+    for (const ProfEntry &pe : c->pending)
+        if (!owned_by_graph(c, pe.a)) c->ev_free.push_back({pe.a, pe.b});
+    c->pending.clear();
     for (auto &kv : c->graphs) {
         cudaGraphExecDestroy(kv.second.exec);
         for (auto &pe : kv.second.prof) c->ev_free.push_back({pe.a, pe.b});
     }
     c->graphs.clear();
-    c->pending.clear();
 }
 
 bte_status ensure_scratch(bte_ctx *c, int id, size_t bytes) {
@@ -472,7 +484,7 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
     const Segment &sg = B->segs[0];
     const Table *t = c->tables[0];
-    if (!fused_dft_supported(t->N)) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
+    if (t->N > 16) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
     if (!c->ind) {
         c->ind = new IndicatorTable();
         if (build_indicator_table(*t, c->learned_samples, 12345, *c->ind) != 0)
@@ -559,15 +571,7 @@ bte_status bte_create(bte_ctx **ctx, int device) {
 void bte_destroy(bte_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
-    cudaDeviceSynchronize();
-    for (auto &kv : c->graphs) {
-        cudaGraphExecDestroy(kv.second.exec);
-        for (auto &pe : kv.second.prof) {
-            cudaEventDestroy(pe.a);
-            cudaEventDestroy(pe.b);
-        }
-    }
-    for (auto &pe : c->pending) c->ev_free.push_back({pe.a, pe.b});
+    drop_graphs(c);  // graph-owned events move to the free pool once, pending entries too
     for (auto &ab : c->ev_free) {
         cudaEventDestroy(ab.first);
         cudaEventDestroy(ab.second);

@@ -1,4 +1,5 @@
-// Fused per-cell transforms for N <= 16 (the whole cell fits in shared memory).
+// Fused per-cell transforms (N = 8, 12, 16, 24, 32): a cell's slabs live in the
+// shared memory of a thread-block cluster.
 //   forward:  fhat_k = (2 pi)^{-3/2} dv^3 sum_j f_j exp(-i zeta_k . v_j)
 //   inverse:  Qt_j = Re (2 pi)^{-3/2} dz^3 sum_k Qhat_k exp(+i zeta_k . v_j)
 // (Sec. 3.2, grid of Eq. meshpoints; zeta_k . v_j = 2 pi k'.j' / N.)
@@ -19,6 +20,9 @@
 // reduction tree) and only the final correction Q = Qt - C^T lambda and the
 // time update run in FP64.
 #include <cooperative_groups.h>
+
+#include <cmath>
+#include <map>
 
 #include "project.cuh"
 
@@ -44,6 +48,18 @@ struct FusedShape {
                                        sizeof(double) * NP;
     static_assert(N % C == 0, "slabs must split evenly");
 };
+
+// Roots of unity exp(2 pi i t / N) in constant memory, one array per N: with
+// the unrolled loops the index is a compile-time constant and every use is a
+// constant-bank operand of the FMA (no registers, no loads).
+__constant__ float2 c_root8[8], c_root12[12], c_root16[16], c_root24[24], c_root32[32];
+
+template <int N> struct CRoot;
+template <> struct CRoot<8> { static __device__ const float2 (&get())[8] { return c_root8; } };
+template <> struct CRoot<12> { static __device__ const float2 (&get())[12] { return c_root12; } };
+template <> struct CRoot<16> { static __device__ const float2 (&get())[16] { return c_root16; } };
+template <> struct CRoot<24> { static __device__ const float2 (&get())[24] { return c_root24; } };
+template <> struct CRoot<32> { static __device__ const float2 (&get())[32] { return c_root32; } };
 
 // phase index of W[k][j] = root[((k - N/2)(j - N/2)) mod N]
 template <int N>
@@ -131,9 +147,7 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
         for (int e = r * (M / C) + t; e < (r + 1) * (M / C); e += S::NT) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);
         return;
     }
-    float2 rt[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) rt[i] = root[i];
+    const float2(&rt)[N] = CRoot<N>::get();
     const bool act = t < S::NP;
     bool bad = false;
     if (act) {  // along j3, pencil (j1, j2), real input
@@ -207,11 +221,13 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
     // the time-update operands of the own slab are loaded first, so that their
     // memory latency overlaps the three passes
     constexpr int MS = M / C, IT = (MS + S::NT - 1) / S::NT;
+    constexpr bool PF = IT <= 16;  // prefetch while the operands fit in registers
     const double *xo = x ? x + off + (int64_t)r * MS : nullptr;
     double *yo = y ? y + off + (int64_t)r * MS : nullptr;
     const double *qpo = qp ? qp + off + (int64_t)r * MS : nullptr;
-    double u[IT], w[IT];
-    if (mode == 2) {
+    double u[PF ? IT : 1], w[PF ? IT : 1];
+    if (!PF) {
+    } else if (mode == 2) {
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
             const int e = t + i * S::NT;
@@ -225,9 +241,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
             w[i] = e < MS ? qpo[e] : 0.0;
         }
     }
-    float2 rt[N];
-#pragma unroll
-    for (int i = 0; i < N; ++i) rt[i] = root[i];
+    const float2(&rt)[N] = CRoot<N>::get();
     const bool act = t < NP;
     const float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
     if (act) {  // along k1, pencil (k2, k3), from the group layout
@@ -351,15 +365,26 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
         for (int e = t; e < MS; e += S::NT) qo[e] = (double)R[(e / N) * P + e % N];
         return;
     }
+    if constexpr (PF) {
 #pragma unroll
-    for (int i = 0; i < IT; ++i) {
-        const int e = t + i * S::NT;
-        if (e < MS) {
+        for (int i = 0; i < IT; ++i) {
+            const int e = t + i * S::NT;
+            if (e < MS) {
+                const int p = e / N, j3 = e % N;
+                const double v = (double)R[p * P + j3] - (base[p] + sg[j3]);
+                qo[e] = v;
+                if (mode == 2) yo[e] = fma(a, v, u[i]);
+                else if (mode == 3) yo[e] = fma(a, w[i] + v, u[i]);
+            }
+        }
+    } else {
+#pragma unroll 4
+        for (int e = t; e < MS; e += S::NT) {
             const int p = e / N, j3 = e % N;
             const double v = (double)R[p * P + j3] - (base[p] + sg[j3]);
             qo[e] = v;
-            if (mode == 2) yo[e] = fma(a, v, u[i]);
-            else if (mode == 3) yo[e] = fma(a, w[i] + v, u[i]);
+            if (mode == 2) yo[e] = fma(a, v, xo[e]);
+            else if (mode == 3) yo[e] = fma(a, qpo[e] + v, yo[e]);
         }
     }
 }
@@ -393,18 +418,36 @@ void prepare_n() {
     prepare_one<N, 4>();
 }
 int norm_split(int split) { return split == 1 || split == 2 ? split : 4; }
+
+template <int N>
+void upload_roots(const float2 (&sym)[N]) {
+    float2 h[N];
+    for (int t = 0; t < N; ++t) {
+        const double th = 2.0 * 3.14159265358979323846 * t / N;
+        h[t] = make_float2((float)std::cos(th), (float)std::sin(th));
+    }
+    cudaMemcpyToSymbol(sym, h, sizeof(h));
+}
 }  // namespace
 
-bool fused_dft_supported(int N) { return N == 8 || N == 12 || N == 16; }
+bool fused_dft_supported(int N) { return N == 8 || N == 12 || N == 16 || N == 24 || N == 32; }
 
 void fused_dft_prepare(int N) {
-    // sets the shared-memory attributes (must happen outside stream capture)
+    // roots of unity (constant memory is per device) and shared-memory
+    // attributes; must happen outside stream capture
+    static std::map<int, unsigned> done;  // device -> bit N of the uploaded root tables
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (N < 0 || N > 32 || (done[dev] >> N) & 1u) return;
     switch (N) {
-        case 8: prepare_n<8>(); break;
-        case 12: prepare_n<12>(); break;
-        case 16: prepare_n<16>(); break;
-        default: break;
+        case 8: upload_roots<8>(c_root8); prepare_n<8>(); break;
+        case 12: upload_roots<12>(c_root12); prepare_n<12>(); break;
+        case 16: upload_roots<16>(c_root16); prepare_n<16>(); break;
+        case 24: upload_roots<24>(c_root24); prepare_one<24, 4>(); break;
+        case 32: upload_roots<32>(c_root32); prepare_one<32, 8>(); break;
+        default: return;
     }
+    done[dev] |= 1u << N;
 }
 
 #define BTE_SPLIT_DISPATCH(FN, N, ...)                 \
@@ -420,6 +463,8 @@ void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const Df
         case 8: BTE_SPLIT_DISPATCH(fwd_launch, 8, f, slot_off, s, root, scale, G, status, st) break;
         case 12: BTE_SPLIT_DISPATCH(fwd_launch, 12, f, slot_off, s, root, scale, G, status, st) break;
         case 16: BTE_SPLIT_DISPATCH(fwd_launch, 16, f, slot_off, s, root, scale, G, status, st) break;
+        case 24: fwd_launch<24, 4>(f, slot_off, s, root, scale, G, status, st); break;
+        case 32: fwd_launch<32, 8>(f, slot_off, s, root, scale, G, status, st); break;
         default: break;
     }
 }
@@ -431,6 +476,8 @@ void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const Df
         case 8: BTE_SPLIT_DISPATCH(inv_launch, 8, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
         case 12: BTE_SPLIT_DISPATCH(inv_launch, 12, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
         case 16: BTE_SPLIT_DISPATCH(inv_launch, 16, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 24: inv_launch<24, 4>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
+        case 32: inv_launch<32, 8>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
         default: break;
     }
 }

@@ -52,7 +52,7 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
     if (!f || !Q || f == Q) return set_err(c, BTE_EINVAL, "bte_collide_noalloc: bad f or Q");
     if (c->tables.empty()) return set_err(c, BTE_ESTATE, "bte_collide_noalloc: no weight tables");
     const Table *t = c->tables[0];
-    if (!fused_dft_supported(t->N))
+    if (t->N > 16 || !fused_dft_supported(t->N))
         return set_err(c, BTE_EINVAL, "bte_collide_noalloc: table 0 must have N = 8, 12 or 16");
     if (ncells <= 0) return set_err(c, BTE_EINVAL, "bte_collide_noalloc: ncells must be > 0");
     const int N = t->N;

@@ -327,3 +327,22 @@ def test_step_graph_survives_scratch_growth(bte):
     d = np.abs(ft.cpu().numpy() - ref).max() / np.abs(f_small).max()
     assert d <= 1e-7, d
     c.close()
+
+
+def test_close_with_unread_profile_entries(bte):
+    """Closing a context while graph replays' profile entries are still pending
+    (only one kernel read) releases every event exactly once."""
+    N = 8
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.profile_enable(True)
+    f = torch.from_numpy(inputs.homogeneous_cells(N, L, 40, seed=3)).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            c.step(f, 0.01, 1.0, stream=s)
+    n, _ = c.profile_read("conv32", s)
+    assert n == 6
+    c.close()  # forward/inverse/collide entries of the replays are still pending
+    d = bte.Context(0)  # the runtime is still usable
+    d.close()
