@@ -350,8 +350,12 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         const int on = prof_begin(c, PK_CONV64, st, &pe_conv);
         for (const Segment &sg : B->segs) {
             const Table *t = c->tables[sg.table];
-            launch_conv64((const double2 *)c->scratch[SC_F], (double2 *)c->scratch[SC_QH], t->d_w64, t->d_w64_off,
-                          t->N, sg.eoff, sg.nslots / kLanes, st);
+            if (2 * sg.nvalid <= sg.nslots)  // groups less than half full: lanes over the box instead of cells
+                launch_conv64_cells((const double2 *)c->scratch[SC_F], (double2 *)c->scratch[SC_QH], t->d_w64,
+                                    t->d_w64_off, B->d_slot_off, sg.s0, sg.nslots, t->N, sg.eoff, st);
+            else
+                launch_conv64((const double2 *)c->scratch[SC_F], (double2 *)c->scratch[SC_QH], t->d_w64,
+                              t->d_w64_off, t->N, sg.eoff, sg.nslots / kLanes, st);
             count_launches(c, 1);
         }
         prof_end(c, on, pe_conv, st);

@@ -60,6 +60,9 @@ cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t
 // Plain FP64 convolution of one segment.
 void launch_conv64(const double2 *F, double2 *Qh, const double *W, const uint64_t *Woff, int N,
                    int64_t eoff, int ngroups, cudaStream_t st);
+// the same for a segment with few valid cells: one warp per (valid slot, zeta)
+void launch_conv64_cells(const double2 *F, double2 *Qh, const double *W, const uint64_t *Woff,
+                         const int64_t *slot_off, int s0, int nslots, int N, int64_t eoff, cudaStream_t st);
 
 void launch_project(double *Q, const int64_t *slot_off, int s0, int nslots, const ProjArgs &pa,
                     int mode, const double *X, double *Y, const double *Qp, double a,
