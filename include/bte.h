@@ -193,6 +193,12 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units;
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
  *                      transforms of N <= 16: 1, 2 or 4 (default 4);
+ *       "debug_conv_stall" testing only: 1 makes every warp of the
+ *                      cooperative convolution (conv_impl 1, 2) skip the
+ *                      copies of its first block, so that its bounded wait runs
+ *                      out: the call completes after about two seconds, the
+ *                      next bte_sync_status returns BTE_ETIMEOUT and the
+ *                      context stays usable (the test of the timeout path);
  *       "profile_mask" which kernels bte_profile_enable times, bit k for
  *                      conv32 (0), conv64 (1), collide (2), forward (3),
  *                      inverse (4), transport (5); default 63 (all).

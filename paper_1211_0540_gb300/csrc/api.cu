@@ -375,6 +375,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         }
         p.status = c->d_status;
         p.merge = c->conv_merge;
+        p.stall = c->debug_conv_stall;
         e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(c, e, "queue reset");
         const int on = prof_begin(c, PK_CONV32, st, &pe_conv);
@@ -842,6 +843,7 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 2; return &c->conv_impl; }
     if (!std::strcmp(name, "dft_split")) { *lo = 1; *hi = 4; return &c->dft_split; }
+    if (!std::strcmp(name, "debug_conv_stall")) { *lo = 0; *hi = 1; return &c->debug_conv_stall; }
     if (!std::strcmp(name, "profile_mask")) { *lo = 0; *hi = 63; return &c->prof_mask; }
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
     if (!std::strcmp(name, "conv_stages")) { *lo = 0; *hi = 4; return &c->conv_stages; }

@@ -136,6 +136,7 @@ struct bte_ctx {
     int conv_merge = 16;       // blocks per compensated (TwoSum) merge
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
+    int debug_conv_stall = 0;  // testing only: make the convolution's waits run out
     bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)
     bte::IndicatorTable *ind = nullptr;  // sampled modes of the fallback indicator
     int learned_tol_ppm = 10000;         // fallback when the indicator exceeds 1e-6 * this

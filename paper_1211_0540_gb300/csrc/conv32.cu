@@ -340,7 +340,8 @@ __device__ bool coop_item(WarpRing &r, const ConvItem &it, const ConvParams &p, 
     const int S = p.stages;
     const int mine = nb > warp ? (nb - warp + nwarps - 1) / nwarps : 0;
     if (lane == 0)
-        for (int s = 0; s < S && s < mine; ++s) issue_block<K>(r, s, it, p, warp + s * nwarps);
+        for (int s = 0; s < S && s < mine; ++s)
+            if (!(p.stall && s == 0)) issue_block<K>(r, s, it, p, warp + s * nwarps);
     __syncwarp();
 
     float hi[2 * T], lo[2 * T];

@@ -43,6 +43,7 @@ struct ConvParams {
     int stages;     // pipeline depth per warp (1..4)
     int merge;      // blocks per TwoSum merge
     int warp_smem;  // bytes of ring per warp
+    int stall;      // testing the timeout path: each warp never issues its first block
 };
 int conv_stage_bytes(int kind);
 struct ConvLaunch {
