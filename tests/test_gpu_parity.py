@@ -346,3 +346,32 @@ def test_close_with_unread_profile_entries(bte):
     c.close()  # forward/inverse/collide entries of the replays are still pending
     d = bte.Context(0)  # the runtime is still usable
     d.close()
+
+
+@pytest.mark.parametrize("split", [1, 2, 4])
+@pytest.mark.parametrize("N,ncells", [(8, 40), (12, 33), (16, 35)])
+def test_fused_transform_cluster_split(bte, N, ncells, split):
+    """The fused transforms with a cell on 1, 2 or 4 CTAs (dft_split): raw and
+    projected operator and one Heun step against the oracle."""
+    lam = 1.0
+    f = inputs.homogeneous_cells(N, L, ncells, seed=500 + N + split)
+    c = ctx_for(bte, ((N, L, lam),))
+    split0 = c.get_option("dft_split")
+    c.set_option("dft_split", split)
+    try:
+        Qp = run_collide(bte, N, lam, f, bte.FP32)
+        Qr = run_collide(bte, N, lam, f, bte.FP32, raw=True)
+        ft = torch.from_numpy(f.copy()).cuda()
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            c.step(ft, 0.01, 1.0, mode=bte.FP32, stream=s)
+        c.sync_status(s)
+    finally:
+        c.set_option("dft_split", split0)
+    Qo, Qto, _ = oracle.collide(N, L, lam, f, want_raw=True)
+    norm = loss_norm(N, lam, f)
+    assert (np.linalg.norm(Qp - Qo, axis=1) / norm).max() <= TOL32
+    assert (np.linalg.norm(Qr - Qto, axis=1) / norm).max() <= TOL32
+    ref = oracle.rk2_homogeneous(N, L, lam, f, 0.01, 1.0)
+    assert np.abs(ft.cpu().numpy() - ref).max() / np.abs(f).max() <= 1e-7
