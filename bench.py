@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use the library's default configuration")
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
     ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
@@ -244,13 +245,16 @@ def main():
     if args.dft_split is not None:
         ctx.set_option("dft_split", args.dft_split)
     ctx.set_option("profile_mask", 1)  # timed steps: events around the convolution only
-    ctx.profile_enable(True)
     tr = dict(nx=NX, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=TW,
               Tw_right=1.0)
     f0 = inputs.wall_heating_initial(N, L, NX)
     f = torch.from_numpy(f0).cuda()
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    tuned = None
+    if not args.no_autotune and args.conv_impl is None and args.dft_split is None:
+        tuned = ctx.autotune(f, reps=3, stream=stream)  # untimed: picks the launch configuration
+    ctx.profile_enable(True)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -378,6 +382,7 @@ def main():
         "config": {"workload": WORKLOAD, "cells": NX, "N": N, "L": L, "lambda": LAM, "eps": EPS,
                    "dt": DT, "l2": "flushed (512 MB write) before every timed step",
                    "arith": "FP32 convolution (TwoSum-compensated), FP32 DFTs, FP64 projection/state",
+                   "autotuned": tuned,
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -520,6 +525,7 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
     Q = torch.empty_like(f)
+    tuned = None if args.no_autotune else ctx.autotune(f, reps=2, stream=stream)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -567,6 +573,7 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                      "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
                      "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
+        "autotuned": tuned,
         "accuracy": {"rel_l2_loss_norm_max": float(rel.max()), "rel_l2_loss_norm_median": float(np.median(rel)),
                      "rel_l2_plain_max": float(relp.max()), "cells_checked": pick.tolist(),
                      "moment_rel_max": _moment_rel(oracle, n, Qg)},
@@ -590,6 +597,7 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     inst = [(ids[(n, lam)], o) for (n, lam, _), o in zip(items, offs)]
     dt, eps = 0.01, 1.0
     f = torch.from_numpy(buf).cuda()
+    tuned = None if args.no_autotune else ctx.autotune(f, inst=inst, reps=2, stream=stream)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -631,7 +639,7 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
           "{0,1} w.p. .5/.5 (8 tables), BKW or bi-Maxwellian data (seed 4); one Heun step of the whole batch "
           "(2 evals per instance) replayed from one CUDA graph")
     return _line(args, "cell-collision evals/s, uneven batch (FP32 operator)", value, UNIT, tot / args.steps, wl, {
-        "instances_by_N": mix, "evals_per_step": evals,
+        "instances_by_N": mix, "evals_per_step": evals, "autotuned": tuned,
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution, all sizes in one launch)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "conv_ms_per_launch": conv_ms,

@@ -206,6 +206,31 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
+/* Autotuner of the FP32 path. For the batch described by (inst, ninst) (as in
+ * bte_collide) it runs one projected FP32 collide of f per candidate
+ * configuration -- convolution variant 1 or 2, 3 or 4 warps per CTA, 1 or 2
+ * blocks in flight per warp, compensated merge every 16 or 32 blocks, and for
+ * N <= 16 one or four CTAs per cell in the fused transforms -- times reps
+ * repetitions with CUDA events on `stream`, and keeps the fastest as this
+ * context's configuration for batches of the same shape (the same set of
+ * grid sizes and number of 32-cell slots); it takes precedence over the
+ * options until any conv_* or dft_split option is set. f (DEVICE, read only) is
+ * the input the timing runs on; results go to internal scratch. out_cfg (HOST,
+ * 5 ints, optional) receives (conv_impl, conv_warps, conv_stages, conv_merge,
+ * dft_split), out_ms (optional) the time of one collide. Synchronous; drops
+ * captured step graphs. Errors: as bte_collide, BTE_ETIMEOUT / BTE_ENONFINITE
+ * from the trial runs. */
+bte_status bte_autotune(bte_ctx *ctx, const double *f, const bte_instance *inst, int64_t ninst, int reps,
+                        int *out_cfg, double *out_ms, void *stream);
+
+/* The tuning cache as a small JSON file: the GPU name and one entry per batch
+ * shape. bte_tune_load applies the entries only if they were tuned on a GPU
+ * of the same name (else it loads nothing and returns BTE_OK); *loaded (HOST,
+ * optional) receives the number of entries applied. Errors: BTE_EINVAL
+ * (unreadable, malformed or out-of-range file; nothing is applied). */
+bte_status bte_tune_save(const bte_ctx *ctx, const char *path);
+bte_status bte_tune_load(bte_ctx *ctx, const char *path, int *loaded);
+
 /* BF16 GEMM on the tensor cores (tcgen05 + TMA), the building block of the
  * learned surrogate's training and inference:
  *   D[M, N] = A[M, K] . B[N, K]^T (+ bias[N]),  A, B: device bf16, row-major with K

@@ -28,7 +28,8 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "b
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
            "bte_mlp_set_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
-           "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats"]
+           "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_autotune", "bte_tune_save",
+           "bte_tune_load"]
 
 
 class Grid(ctypes.Structure):
@@ -101,6 +102,10 @@ def load(path=None):
         "bte_mlp_infer": (c_int, [vp, vp, vp, c_i64, vp]),
         "bte_learned_stats": (c_int, [vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_d),
                                       c_int]),
+        "bte_autotune": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_int, ctypes.POINTER(c_int),
+                                 ctypes.POINTER(c_d), vp]),
+        "bte_tune_save": (c_int, [vp, ctypes.c_char_p]),
+        "bte_tune_load": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -323,6 +328,26 @@ class Context:
         n = f.numel() // self.mlp_info()["ndim"]
         self._rc(self._lib.bte_mlp_infer(self._h, _ptr(f), _ptr(Q), n, _stream(stream)), "bte_mlp_infer")
         return Q
+
+    def autotune(self, f, inst=None, reps=3, stream=None):
+        """Time the candidate FP32 configurations on f (batch shape of inst) and keep
+        the fastest for batches of this shape. Returns the chosen configuration."""
+        _check_f64(f, "f")
+        arr, n = self._inst(inst, f)
+        cfg = (ctypes.c_int * 5)()
+        ms = ctypes.c_double()
+        self._rc(self._lib.bte_autotune(self._h, _ptr(f), arr, n, int(reps), cfg, ctypes.byref(ms),
+                                        _stream(stream)), "bte_autotune")
+        return dict(conv_impl=cfg[0], conv_warps=cfg[1], conv_stages=cfg[2], conv_merge=cfg[3],
+                    dft_split=cfg[4], ms=ms.value)
+
+    def tune_save(self, path):
+        self._rc(self._lib.bte_tune_save(self._h, str(path).encode()), "bte_tune_save")
+
+    def tune_load(self, path):
+        n = ctypes.c_int()
+        self._rc(self._lib.bte_tune_load(self._h, str(path).encode(), ctypes.byref(n)), "bte_tune_load")
+        return n.value
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

@@ -279,6 +279,24 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
     return BTE_OK;
 }
 
+// Batch shape key of the tuning cache: the convolution kinds and the slots.
+std::string tune_key(const Batch *B) {
+    return "k" + std::to_string(B->kinds_mask) + ":s" + std::to_string(B->nslots);
+}
+
+// The FP32 configuration of a batch: the autotuned one for its shape, else the options.
+ConvCfg cfg_of(const bte_ctx *c, const Batch *B) {
+    auto it = c->tuned.find(tune_key(B));
+    if (it != c->tuned.end()) return it->second;
+    ConvCfg g;
+    g.impl = c->conv_impl;
+    g.warps = c->conv_warps;
+    g.stages = c->conv_stages;
+    g.merge = c->conv_merge;
+    g.split = c->dft_split;
+    return g;
+}
+
 ProjArgs proj_args(const Table *t) {
     ProjArgs pa;
     pa.N = t->N;
@@ -307,7 +325,8 @@ bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
         }
     } else if (mode == BTE_FP32) {
         ConvLaunch L;
-        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
+        const ConvCfg g = cfg_of(c, B);
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, g.warps, g.stages, g.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
     }
     return BTE_OK;
@@ -322,6 +341,7 @@ enum Post { POST_RAW = 0, POST_PROJECT = 1, POST_STAGE1 = 2, POST_STAGE2 = 3 };
 bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, int post,
                            const double *x, double *y, const double *qp, double a, cudaStream_t st) {
     const bool fp64 = mode == BTE_FP64_PLAIN;
+    const ConvCfg cfg = cfg_of(c, B);
     ProfEntry pe_all{}, pe_conv{}, pe_fwd{}, pe_inv{};
     const int on_all = prof_begin(c, PK_COLLIDE, st, &pe_all);
     const int on_fwd = prof_begin(c, PK_FORWARD, st, &pe_fwd);
@@ -335,7 +355,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             count_launches(c, 3);
         } else if (fused_dft_supported(t->N)) {
             launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status,
-                                     st, c->dft_split);
+                                     st, cfg.split);
             count_launches(c, 1);
         } else {
             launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
@@ -361,7 +381,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         prof_end(c, on, pe_conv, st);
     } else {
         ConvLaunch L;
-        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
+        cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, cfg.warps, cfg.stages, cfg.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
         ConvParams p{};
         p.items = B->d_items;
@@ -374,7 +394,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             p.D[i] = c->tables[i]->d_desc;
         }
         p.status = c->d_status;
-        p.merge = c->conv_merge;
+        p.merge = cfg.merge;
         p.stall = c->debug_conv_stall;
         e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st);
         if (e != cudaSuccess) return cuda_fail(c, e, "queue reset");
@@ -398,7 +418,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
         if (!fp64 && fused_dft_supported(t->N)) {
             launch_dft_inverse_fused((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si, Q,
-                                     proj_args(t), post, x, y, qp, a, st, c->dft_split);
+                                     proj_args(t), post, x, y, qp, a, st, cfg.split);
             count_launches(c, 1);
             continue;
         }
@@ -562,6 +582,10 @@ bte_status bte_create(bte_ctx **ctx, int device) {
     bte_ctx *c = new bte_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    {
+        cudaDeviceProp prop{};
+        if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->gpu_name = prop.name;
+    }
     if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_counter, 64) != cudaSuccess ||
         cudaMalloc(&c->d_wall, 2 * sizeof(double)) != cudaSuccess) {
         bte_destroy(c);
@@ -862,6 +886,8 @@ bte_status bte_set_option(bte_ctx *c, const char *name, int value) {
         drop_graphs(c);
         *slot = value;
     }
+    // an explicit choice of the FP32 path's configuration replaces the tuned ones
+    if (!std::strncmp(name, "conv_", 5) || !std::strcmp(name, "dft_split")) c->tuned.clear();
     return BTE_OK;
 }
 
@@ -898,6 +924,146 @@ bte_status bte_sync_status(bte_ctx *c, void *stream) {
     if (st & ST_TIMEOUT) return fail(c, BTE_ETIMEOUT, "a bounded wait in a kernel ran out");
     if (st & ST_BADDESC) return fail(c, BTE_ECUDA, "a convolution block descriptor was out of range");
     if (st & ST_NONFINITE) return fail(c, BTE_ENONFINITE, "non-finite value in the input f");
+    return BTE_OK;
+}
+
+bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, int64_t ninst, int reps,
+                        int *out_cfg, double *out_ms, void *stream) {
+    if (!c || !f || ninst <= 0) return fail(c, BTE_EINVAL, "bte_autotune: bad arguments");
+    if (c->tables.empty()) return fail(c, BTE_ESTATE, "bte_autotune: no weight tables");
+    cudaSetDevice(c->device);
+    reps = reps < 1 ? 1 : (reps > 100 ? 100 : reps);
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch *B = nullptr;
+    bte_status s = get_batch(c, inst, ninst, &B);
+    if (s != BTE_OK) return s;
+    if ((s = ensure_scratch(c, SC_Q2, sizeof(double) * (size_t)B->extent)) != BTE_OK) return s;
+    double *Qtmp = (double *)c->scratch[SC_Q2];
+    bool small_n = true;
+    for (const Segment &sg : B->segs) small_n = small_n && c->tables[sg.table]->N <= 16;
+    const std::string key = tune_key(B);
+    const bool had = c->tuned.count(key) != 0;
+    const ConvCfg before = had ? c->tuned[key] : ConvCfg{};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "bte_autotune: events");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(c, cudaGetLastError(), "bte_autotune: events");
+    }
+    ConvCfg best;
+    best.ms = -1.0;
+    bte_status err = BTE_OK;
+    for (int impl : {2, 1})
+        for (int warps : {4, 3})
+            for (int stages : {1, 2})
+                for (int merge : {16, 32})
+                    for (int split : {4, 1}) {
+                        if (!small_n && split != 4) continue;
+                        ConvCfg g;
+                        g.impl = impl;
+                        g.warps = warps;
+                        g.stages = stages;
+                        g.merge = merge;
+                        g.split = split;
+                        c->tuned[key] = g;
+                        if ((err = prepare(c, B, BTE_FP32, false, false)) != BTE_OK) break;
+                        if ((err = enqueue_collide(c, B, f, Qtmp, BTE_FP32, POST_PROJECT, nullptr, nullptr, nullptr,
+                                                   0.0, st)) != BTE_OK)
+                            break;  // warm-up (kernel attributes, caches)
+                        cudaEventRecord(e0, st);
+                        for (int r = 0; r < reps && err == BTE_OK; ++r)
+                            err = enqueue_collide(c, B, f, Qtmp, BTE_FP32, POST_PROJECT, nullptr, nullptr, nullptr,
+                                                  0.0, st);
+                        cudaEventRecord(e1, st);
+                        cudaError_t ce = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                        if (ce != cudaSuccess) err = cuda_fail(c, ce, "bte_autotune: timing");
+                        if (err != BTE_OK) break;
+                        g.ms = ms / reps;
+                        if (best.ms < 0.0 || g.ms < best.ms) best = g;
+                    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (const ProfEntry &pe : c->pending)  // profile entries of the trial runs are not the caller's
+        if (!owned_by_graph(c, pe.a)) c->ev_free.push_back({pe.a, pe.b});
+    c->pending.clear();
+    if (err == BTE_OK) err = bte_sync_status(c, stream);
+    if (err != BTE_OK || best.ms < 0.0) {
+        if (had) c->tuned[key] = before;
+        else c->tuned.erase(key);
+        return err != BTE_OK ? err : fail(c, BTE_ECUDA, "bte_autotune: no configuration ran");
+    }
+    c->tuned[key] = best;
+    drop_graphs(c);  // captured steps used the previous configuration
+    if ((s = prepare(c, B, BTE_FP32, false, false)) != BTE_OK) return s;
+    if (out_cfg) {
+        out_cfg[0] = best.impl;
+        out_cfg[1] = best.warps;
+        out_cfg[2] = best.stages;
+        out_cfg[3] = best.merge;
+        out_cfg[4] = best.split;
+    }
+    if (out_ms) *out_ms = best.ms;
+    return BTE_OK;
+}
+
+bte_status bte_tune_save(const bte_ctx *c, const char *path) {
+    if (!c || !path) return BTE_EINVAL;
+    FILE *fp = std::fopen(path, "w");
+    if (!fp) return fail(const_cast<bte_ctx *>(c), BTE_EINVAL, std::string("bte_tune_save: cannot write ") + path);
+    std::fprintf(fp, "{\n\"gpu\": \"%s\",\n\"entries\": [\n", c->gpu_name.c_str());
+    size_t i = 0;
+    for (const auto &kv : c->tuned) {
+        const ConvCfg &g = kv.second;
+        std::fprintf(fp, "{\"key\": \"%s\", \"impl\": %d, \"warps\": %d, \"stages\": %d, \"merge\": %d, "
+                         "\"split\": %d, \"ms\": %.6f}%s\n",
+                     kv.first.c_str(), g.impl, g.warps, g.stages, g.merge, g.split, g.ms,
+                     ++i < c->tuned.size() ? "," : "");
+    }
+    std::fprintf(fp, "]\n}\n");
+    const bool ok = std::fclose(fp) == 0;
+    return ok ? BTE_OK : fail(const_cast<bte_ctx *>(c), BTE_EINVAL, "bte_tune_save: write failed");
+}
+
+bte_status bte_tune_load(bte_ctx *c, const char *path, int *loaded) {
+    if (!c || !path) return BTE_EINVAL;
+    if (loaded) *loaded = 0;
+    FILE *fp = std::fopen(path, "r");
+    if (!fp) return fail(c, BTE_EINVAL, std::string("bte_tune_load: cannot read ") + path);
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof buf, fp)) > 0) text.append(buf, n);
+    std::fclose(fp);
+    // the format bte_tune_save writes: one entry per line
+    const size_t g0 = text.find("\"gpu\": \"");
+    if (g0 == std::string::npos) return fail(c, BTE_EINVAL, "bte_tune_load: not a tuning cache");
+    const size_t g1 = text.find('"', g0 + 8);
+    if (g1 == std::string::npos) return fail(c, BTE_EINVAL, "bte_tune_load: not a tuning cache");
+    const std::string gpu = text.substr(g0 + 8, g1 - (g0 + 8));
+    if (gpu != c->gpu_name) return BTE_OK;  // tuned on another GPU: nothing applies
+    std::map<std::string, ConvCfg> got;
+    size_t pos = 0;
+    while ((pos = text.find("{\"key\": \"", pos)) != std::string::npos) {
+        const size_t eol = text.find('\n', pos);
+        const std::string line = text.substr(pos, eol == std::string::npos ? std::string::npos : eol - pos);
+        char key[128] = {0};
+        ConvCfg g;
+        if (std::sscanf(line.c_str(),
+                        "{\"key\": \"%127[^\"]\", \"impl\": %d, \"warps\": %d, \"stages\": %d, \"merge\": %d, "
+                        "\"split\": %d, \"ms\": %lf}",
+                        key, &g.impl, &g.warps, &g.stages, &g.merge, &g.split, &g.ms) != 7)
+            return fail(c, BTE_EINVAL, "bte_tune_load: malformed entry: " + line);
+        if (g.impl < 0 || g.impl > 2 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
+            (g.split != 1 && g.split != 2 && g.split != 4))
+            return fail(c, BTE_EINVAL, "bte_tune_load: out-of-range entry: " + line);
+        got[key] = g;
+        pos += 10;
+    }
+    drop_graphs(c);
+    for (auto &kv : got) c->tuned[kv.first] = kv.second;
+    if (loaded) *loaded = (int)got.size();
     return BTE_OK;
 }
 

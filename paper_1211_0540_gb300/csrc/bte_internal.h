@@ -86,6 +86,13 @@ struct GraphKey {
     bool operator<(const GraphKey &o) const;
 };
 
+// One configuration of the FP32 path (convolution variant and launch shape,
+// compensated-merge interval, CTAs per cell of the fused transforms).
+struct ConvCfg {
+    int impl = 2, warps = 4, stages = 0, merge = 16, split = 4;
+    double ms = 0.0;  // measured time of one collide of the batch when tuned
+};
+
 struct Batch;  // device-side description of one instance layout (defined in api.cu)
 struct Mlp;    // learned surrogate (mlp.h)
 struct IndicatorTable;
@@ -137,6 +144,8 @@ struct bte_ctx {
     int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
     int debug_conv_stall = 0;  // testing only: make the convolution's waits run out
+    std::string gpu_name;      // device name (key of saved tuning caches)
+    std::map<std::string, bte::ConvCfg> tuned;  // autotuned configuration per batch shape
     bte::Mlp *mlp = nullptr;   // learned surrogate (bte_mlp_init)
     bte::IndicatorTable *ind = nullptr;  // sampled modes of the fallback indicator
     int learned_tol_ppm = 10000;         // fallback when the indicator exceeds 1e-6 * this

@@ -375,3 +375,42 @@ def test_fused_transform_cluster_split(bte, N, ncells, split):
     assert (np.linalg.norm(Qr - Qto, axis=1) / norm).max() <= TOL32
     ref = oracle.rk2_homogeneous(N, L, lam, f, 0.01, 1.0)
     assert np.abs(ft.cpu().numpy() - ref).max() / np.abs(f).max() <= 1e-7
+
+
+def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
+    """bte_autotune keeps a valid configuration for the batch shape; the operator
+    stays within the FP32 bar; the cache saved to JSON reproduces the same
+    results in a fresh context; foreign or malformed caches are handled."""
+    N, lam, ncells = 12, 1.0, 70
+    f = inputs.homogeneous_cells(N, L, ncells, seed=61)
+    ft = torch.from_numpy(f).cuda()
+    c = bte.Context(0)
+    c.init_weights([(N, L, lam)])
+    cfg = c.autotune(ft, reps=2)
+    assert cfg["conv_impl"] in (1, 2) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
+    assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 4) and cfg["ms"] > 0.0
+    Q = c.collide(ft)
+    c.sync_status()
+    Qo = oracle.collide(N, L, lam, f)
+    assert (np.linalg.norm(Q.cpu().numpy() - Qo, axis=1) / loss_norm(N, lam, f)).max() <= TOL32
+    path = tmp_path / "tune.json"
+    c.tune_save(path)
+    d = bte.Context(0)
+    d.init_weights([(N, L, lam)])
+    assert d.tune_load(path) == 1
+    Q2 = d.collide(ft)
+    d.sync_status()
+    assert np.array_equal(Q.cpu().numpy(), Q2.cpu().numpy())  # same configuration, same arithmetic
+    other = tmp_path / "other.json"
+    other.write_text(path.read_text().replace('"gpu": "', '"gpu": "another GPU '))
+    assert d.tune_load(other) == 0
+    bad = tmp_path / "bad.json"
+    bad.write_text(path.read_text().replace('"impl": ', '"impl": x'))
+    with pytest.raises(bte.BteError):
+        d.tune_load(bad)
+    c.set_option("conv_merge", 8)  # an explicit option replaces the tuned configuration
+    Q3 = c.collide(ft)
+    c.sync_status()
+    assert (np.linalg.norm(Q3.cpu().numpy() - Qo, axis=1) / loss_norm(N, lam, f)).max() <= TOL32
+    c.close()
+    d.close()
