@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default configuration")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON tuning cache: loaded if it exists (no tuning), else written after tuning; "
+                         "lets a profiler run the configuration a plain run chose")
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
     ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
@@ -190,6 +193,22 @@ def oracle_strang_step(f, oracle):
                               bc_right=oracle.BC_SPECULAR, Tw_left=TW, Tw_right=1.0)
 
 
+def tune(args, ctx, f, stream, inst=None, reps=3):
+    """The FP32 configuration of this run: none (--no-autotune), the one stored in
+    --tune-cache, or a fresh bte_autotune (saved to --tune-cache if given)."""
+    if args.no_autotune:
+        return None
+    if args.tune_cache and os.path.exists(args.tune_cache):
+        if ctx.tune_load(args.tune_cache) > 0:
+            with open(args.tune_cache) as fh:
+                entries = json.load(fh)["entries"]
+            return dict(entries[0], source=args.tune_cache)
+    cfg = ctx.autotune(f, inst=inst, reps=reps, stream=stream)
+    if args.tune_cache:
+        ctx.tune_save(args.tune_cache)
+    return cfg
+
+
 def run_reference(args):
     """The FP64 CPU oracle, as it stands, on the same Strang step."""
     rank, world, _ = dist_env()
@@ -252,8 +271,8 @@ def main():
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     tuned = None
-    if not args.no_autotune and args.conv_impl is None and args.dft_split is None:
-        tuned = ctx.autotune(f, reps=3, stream=stream)  # untimed: picks the launch configuration
+    if args.conv_impl is None and args.dft_split is None:
+        tuned = tune(args, ctx, f, stream, reps=10)  # untimed: picks the launch configuration
     ctx.profile_enable(True)
 
     with torch.cuda.stream(stream):
@@ -525,7 +544,7 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
     Q = torch.empty_like(f)
-    tuned = None if args.no_autotune else ctx.autotune(f, reps=2, stream=stream)
+    tuned = tune(args, ctx, f, stream, reps=2)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -597,7 +616,7 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     inst = [(ids[(n, lam)], o) for (n, lam, _), o in zip(items, offs)]
     dt, eps = 0.01, 1.0
     f = torch.from_numpy(buf).cuda()
-    tuned = None if args.no_autotune else ctx.autotune(f, inst=inst, reps=2, stream=stream)
+    tuned = tune(args, ctx, f, stream, inst=inst, reps=2)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
