@@ -41,7 +41,7 @@ WORKLOAD = ("sudden wall heating: 128 cells x N=16^3 velocities (L=6, hard spher
             "Tw=2 diffuse / specular), one Strang step = 2 transport half steps + RK2 over "
             "128 cells = 256 collision evals")
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-WORKLOADS = ("wall-heating", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16")
+WORKLOADS = ("wall-heating", "wall-heating-200", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16")
 SMS, FP32_LANES = 152, 128
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -751,6 +751,63 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "gpu_launches": launches, "clocks": clocks})
 
 
+def run_wall200(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """The wall-heating slab over 200 Strang steps with the FP32 path and with the
+    plain FP64 operator: conservation drift of each trajectory, the FP32 state's
+    deviation from the FP64 one, and the FP32 operator against the oracle on
+    sampled cells of the final state."""
+    nsteps = 200
+    ctx.init_weights([(N, L, LAM)])
+    tr = dict(nx=NX, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=TW,
+              Tw_right=1.0)
+    f0 = inputs.wall_heating_initial(N, L, NX)
+    tuned = tune(args, ctx, torch.from_numpy(f0).cuda(), stream, reps=5)
+    out, ms = {}, {}
+    sampler.start()
+    for name, mode in (("fp32", bte.FP32), ("fp64_plain", bte.FP64_PLAIN)):
+        f = torch.from_numpy(f0.copy()).cuda()
+        with torch.cuda.stream(stream):
+            ctx.step(f, DT, EPS, transport=tr, mode=mode, stream=stream)  # capture, then restart
+        ctx.sync_status(stream)
+        f.copy_(torch.from_numpy(f0))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(nsteps):
+                ctx.step(f, DT, EPS, transport=tr, mode=mode, stream=stream)
+            e1.record(stream)
+        ctx.sync_status(stream)
+        ms[name] = e0.elapsed_time(e1)
+        out[name] = f.cpu().numpy().reshape(NX, -1)
+    clocks = sampler.stop()
+    m0 = oracle.moments(N, L, f0).sum(axis=0)
+    drift = {}
+    for name, fs in out.items():
+        m = oracle.moments(N, L, fs).sum(axis=0)
+        # mass is conserved by the walls; momentum and energy change through the walls
+        drift[name] = {"mass_rel": float(abs(m[0] - m0[0]) / m0[0])}
+    dev = float(np.abs(out["fp32"] - out["fp64_plain"]).max() / np.abs(out["fp64_plain"]).max())
+    pick = [0, 1, 2, 8, 64, NX - 1]
+    Qg = ctx.collide(torch.from_numpy(out["fp32"]).cuda().reshape(-1), mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    Qg = Qg.cpu().numpy().reshape(NX, -1)
+    Qo = oracle.collide(N, L, LAM, out["fp32"][pick])
+    Qm = oracle.collide(N, L, LAM, out["fp32"][pick], part=1, project=False)
+    rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+    value = EVALS_PER_STEP * nsteps / (ms["fp32"] * 1e-3)
+    wl = ("sudden wall heating, 200 Strang steps (the run of the paper's Sec. 5 set-up at Kn = 0.1): 128 "
+          "cells, N = 16, L = 6, hard spheres, Tw = 2 diffuse / specular, CFL 0.5; FP32 path and plain "
+          "FP64 operator from the same initial state")
+    return _line(args, METRIC, value, UNIT, ms["fp32"] / nsteps, wl, {
+        "steps": nsteps, "fp64_plain": {"value": EVALS_PER_STEP * nsteps / (ms["fp64_plain"] * 1e-3), "unit": UNIT},
+        "autotuned": tuned, "conservation": drift,
+        "accuracy": {"state_max_dev_fp32_vs_fp64_rel": dev,
+                     "final_state_Q_rel_l2_loss_norm_max": float(rel.max()), "cells_checked": pick},
+        "clocks": clocks})
+
+
 def run_secondary(args):
     import torch
 
@@ -770,7 +827,7 @@ def run_secondary(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)
     fn = {"homog-1cell": run_homog1, "sweep-n32": run_sweep32, "uneven-4096": run_uneven,
-          "learned-n16": run_learned}[args.workload]
+          "learned-n16": run_learned, "wall-heating-200": run_wall200}[args.workload]
     line = fn(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler)
     print(json.dumps(line), flush=True)
     ctx.close()
