@@ -183,7 +183,8 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 /* Tuning options of the FP32 convolution (read by the autotuner and tests).
  * name: "conv_impl"   0 = one warp per work item, 1 = all warps of a CTA share
  *                      an item (reduced in shared memory), 2 = as 1 with packed
- *                      f32x2 arithmetic;
+ *                      f32x2 arithmetic, 3 = as 2 with up to 255 registers per
+ *                      thread (2 CTAs per SM);
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
  *       "conv_stages" blocks in flight per warp (1..4; 0 = automatic, the
  *                      default: the deepest ring up to 2 that keeps the
@@ -208,7 +209,7 @@ bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
 /* Autotuner of the FP32 path. For the batch described by (inst, ninst) (as in
  * bte_collide) it runs one projected FP32 collide of f per candidate
- * configuration -- convolution variant 1 or 2, 3 or 4 warps per CTA, 1 or 2
+ * configuration -- convolution variant 1, 2 or 3, 3 or 4 warps per CTA, 1 or 2
  * blocks in flight per warp, compensated merge every 16 or 32 blocks, and for
  * N <= 16 one or four CTAs per cell in the fused transforms -- times reps
  * repetitions with CUDA events on `stream`, and keeps the fastest as this

@@ -439,8 +439,8 @@ __device__ __forceinline__ bool coop_run(WarpRing &r, const ConvItem &it, const 
     return !*abort_flag;
 }
 
-template <unsigned MASK, bool PACKED>
-__global__ void __launch_bounds__(128, 3) conv32_coop_kernel(ConvParams p) {
+template <unsigned MASK, bool PACKED, int MINB = 3>
+__global__ void __launch_bounds__(128, MINB) conv32_coop_kernel(ConvParams p) {
     extern __shared__ __align__(128) char smem[];
     __shared__ int s_item, s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -540,8 +540,9 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
             default: L.fn = conv32_kernel<127u>; break;
         }
     } else {
-        const bool packed = impl == 2;
-#define BTE_PICK(M) L.fn = packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>
+        const bool packed = impl >= 2;
+#define BTE_PICK(M)                                                                             \
+    L.fn = impl == 3 ? conv32_coop_kernel<M, true, 2> : (packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>)
         switch (kinds_mask) {
             case 1u: BTE_PICK(1u); break;
             case 2u: BTE_PICK(2u); break;
