@@ -207,6 +207,24 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 bte_status bte_set_option(bte_ctx *ctx, const char *name, int value);
 bte_status bte_get_option(const bte_ctx *ctx, const char *name, int *value);
 
+/* Checkpoint of a solver state (no counterpart in the paper: long runs stop
+ * and resume). bte_state_save writes the n FP64 values of the DEVICE array f
+ * (e.g. the cells of a slab, instance-ordered as the caller keeps them), the
+ * time t and the step counter to `path`: a header (magic "BTESTATE", format
+ * version, n, t, step, the FNV-1a hash of this context's weight grids (N, L,
+ * lambda of every table, in order)), the values, and the FNV-1a checksum of
+ * header and values. bte_state_load reads it into the DEVICE array f (n values,
+ * which must equal the stored count) and returns t and step (HOST, optional).
+ * Both synchronise `stream`. The kernels reduce in a fixed order, so steps
+ * taken after a load reproduce the uninterrupted run bit for bit.
+ * Errors: BTE_EINVAL (unreadable/unwritable file, bad magic or version,
+ * checksum mismatch, n differs), BTE_ESTATE (the file was written under other
+ * weight grids), BTE_ECUDA. */
+bte_status bte_state_save(bte_ctx *ctx, const char *path, const double *f, int64_t n, double t, int64_t step,
+                          void *stream);
+bte_status bte_state_load(bte_ctx *ctx, const char *path, double *f, int64_t n, double *t, int64_t *step,
+                          void *stream);
+
 /* Autotuner of the FP32 path. For the batch described by (inst, ninst) (as in
  * bte_collide) it runs one projected FP32 collide of f per candidate
  * configuration -- convolution variant 1, 2 or 3, 3 or 4 warps per CTA, 1 or 2

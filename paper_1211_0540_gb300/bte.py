@@ -29,7 +29,7 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "b
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
            "bte_mlp_set_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
            "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_autotune", "bte_tune_save",
-           "bte_tune_load"]
+           "bte_tune_load", "bte_state_save", "bte_state_load"]
 
 
 class Grid(ctypes.Structure):
@@ -106,6 +106,8 @@ def load(path=None):
                                  ctypes.POINTER(c_d), vp]),
         "bte_tune_save": (c_int, [vp, ctypes.c_char_p]),
         "bte_tune_load": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
+        "bte_state_save": (c_int, [vp, ctypes.c_char_p, vp, c_i64, c_d, c_i64, vp]),
+        "bte_state_load": (c_int, [vp, ctypes.c_char_p, vp, c_i64, ctypes.POINTER(c_d), ctypes.POINTER(c_i64), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -348,6 +350,20 @@ class Context:
         n = ctypes.c_int()
         self._rc(self._lib.bte_tune_load(self._h, str(path).encode(), ctypes.byref(n)), "bte_tune_load")
         return n.value
+
+    def save_state(self, path, f, t=0.0, step=0, stream=None):
+        """Checkpoint f (device, FP64), the time and the step counter to path."""
+        _check_f64(f, "f")
+        self._rc(self._lib.bte_state_save(self._h, str(path).encode(), _ptr(f), f.numel(), float(t), int(step),
+                                          _stream(stream)), "bte_state_save")
+
+    def load_state(self, path, f, stream=None):
+        """Read a checkpoint into f (device, FP64, same size); returns (t, step)."""
+        _check_f64(f, "f")
+        t, step = ctypes.c_double(), ctypes.c_int64()
+        self._rc(self._lib.bte_state_load(self._h, str(path).encode(), _ptr(f), f.numel(), ctypes.byref(t),
+                                          ctypes.byref(step), _stream(stream)), "bte_state_load")
+        return t.value, step.value
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

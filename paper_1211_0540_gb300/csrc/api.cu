@@ -1008,6 +1008,90 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
     return BTE_OK;
 }
 
+namespace {
+struct StateHeader {
+    char magic[8];     // "BTESTATE"
+    uint32_t version;  // 1
+    uint32_t pad;
+    int64_t n;
+    double t;
+    int64_t step;
+    uint64_t grids;    // FNV-1a of the context's (N, L, lambda) list
+};
+static_assert(sizeof(StateHeader) == 48, "state header layout");
+
+uint64_t grids_hash(const bte_ctx *c) {
+    uint64_t h = 1469598103934665603ull;
+    for (const Table *t : c->tables) {
+        const double v[3] = {(double)t->N, t->L, t->lam};
+        h = fnv1a(v, sizeof v, h);
+    }
+    return h;
+}
+}  // namespace
+
+bte_status bte_state_save(bte_ctx *c, const char *path, const double *f, int64_t n, double t, int64_t step,
+                          void *stream) {
+    if (!c || !path || !f || n <= 0) return fail(c, BTE_EINVAL, "bte_state_save: bad arguments");
+    cudaSetDevice(c->device);
+    std::vector<double> h((size_t)n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), f, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bte_state_save: copy");
+    StateHeader hd{};
+    std::memcpy(hd.magic, "BTESTATE", 8);
+    hd.version = 1;
+    hd.n = n;
+    hd.t = t;
+    hd.step = step;
+    hd.grids = grids_hash(c);
+    uint64_t sum = fnv1a(&hd, sizeof hd);
+    sum = fnv1a(h.data(), sizeof(double) * h.size(), sum);
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(c, BTE_EINVAL, std::string("bte_state_save: cannot write ") + path);
+    bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 && std::fwrite(h.data(), sizeof(double), h.size(), fp) == h.size() &&
+              std::fwrite(&sum, sizeof sum, 1, fp) == 1;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? BTE_OK : fail(c, BTE_EINVAL, "bte_state_save: write failed");
+}
+
+bte_status bte_state_load(bte_ctx *c, const char *path, double *f, int64_t n, double *t, int64_t *step,
+                          void *stream) {
+    if (!c || !path || !f || n <= 0) return fail(c, BTE_EINVAL, "bte_state_load: bad arguments");
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(c, BTE_EINVAL, std::string("bte_state_load: cannot read ") + path);
+    StateHeader hd{};
+    bool ok = std::fread(&hd, sizeof hd, 1, fp) == 1 && std::memcmp(hd.magic, "BTESTATE", 8) == 0 && hd.version == 1;
+    if (!ok) {
+        std::fclose(fp);
+        return fail(c, BTE_EINVAL, "bte_state_load: not a state file (magic or version)");
+    }
+    if (hd.n != n) {
+        std::fclose(fp);
+        return fail(c, BTE_EINVAL, "bte_state_load: the file holds " + std::to_string(hd.n) + " values, not " +
+                                       std::to_string(n));
+    }
+    std::vector<double> h((size_t)n);
+    uint64_t stored = 0;
+    ok = std::fread(h.data(), sizeof(double), h.size(), fp) == h.size() && std::fread(&stored, sizeof stored, 1, fp) == 1;
+    std::fclose(fp);
+    if (!ok) return fail(c, BTE_EINVAL, "bte_state_load: truncated file");
+    uint64_t sum = fnv1a(&hd, sizeof hd);
+    sum = fnv1a(h.data(), sizeof(double) * h.size(), sum);
+    if (sum != stored) return fail(c, BTE_EINVAL, "bte_state_load: checksum mismatch (corrupt file)");
+    if (hd.grids != grids_hash(c))
+        return fail(c, BTE_ESTATE, "bte_state_load: written under other weight grids (N, L, lambda)");
+    cudaSetDevice(c->device);
+    cudaError_t e = cudaMemcpyAsync(f, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "bte_state_load: copy");
+    if (t) *t = hd.t;
+    if (step) *step = hd.step;
+    return BTE_OK;
+}
+
 bte_status bte_tune_save(const bte_ctx *c, const char *path) {
     if (!c || !path) return BTE_EINVAL;
     FILE *fp = std::fopen(path, "w");

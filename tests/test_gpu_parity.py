@@ -414,3 +414,58 @@ def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
     assert (np.linalg.norm(Q3.cpu().numpy() - Qo, axis=1) / loss_norm(N, lam, f)).max() <= TOL32
     c.close()
     d.close()
+
+
+def test_checkpoint_resume_is_bitwise(bte, tmp_path):
+    """Six Strang steps in one run equal three steps, a checkpoint, a fresh
+    context that loads it, and three more steps, bit for bit (the kernels reduce
+    in a fixed order); corrupt files and other weight grids are rejected."""
+    N, nx, lam = 8, 12, 1.0
+    f0 = inputs.wall_heating_initial(N, L, nx)
+    f0 *= (1.0 + 0.1 * np.sin(np.arange(nx) / 3.0))[:, None]
+    dt, eps = 2e-3, 0.1
+    tr = dict(nx=nx, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=2.0, Tw_right=1.0)
+
+    def run(c, f, k):
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for _ in range(k):
+                c.step(f, dt, eps, transport=tr, mode=bte.FP32, stream=s)
+        c.sync_status(s)
+
+    a = bte.Context(0)
+    a.init_weights([(N, L, lam)])
+    fa = torch.from_numpy(f0.copy()).cuda()
+    run(a, fa, 6)
+    b = bte.Context(0)
+    b.init_weights([(N, L, lam)])
+    fb = torch.from_numpy(f0.copy()).cuda()
+    run(b, fb, 3)
+    path = tmp_path / "state.bin"
+    b.save_state(path, fb, t=3 * dt, step=3)
+    b.close()
+    c = bte.Context(0)
+    c.init_weights([(N, L, lam)])
+    fc = torch.zeros_like(fb)
+    t, step = c.load_state(path, fc)
+    assert (t, step) == (3 * dt, 3)
+    run(c, fc, 3)
+    assert np.array_equal(fa.cpu().numpy(), fc.cpu().numpy())
+    raw = bytearray(path.read_bytes())
+    raw[100] ^= 0x01
+    bad = tmp_path / "corrupt.bin"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(bte.BteError) as err:
+        c.load_state(bad, fc)
+    assert err.value.code == -1
+    with pytest.raises(bte.BteError) as err:
+        c.load_state(path, torch.zeros(fc.numel() - N ** 3, dtype=torch.float64, device="cuda"))
+    assert err.value.code == -1
+    d = bte.Context(0)
+    d.init_weights([(N, L, 0.0)])
+    with pytest.raises(bte.BteError) as err:
+        d.load_state(path, fc)
+    assert err.value.code == -6
+    for x in (a, c, d):
+        x.close()
