@@ -9,6 +9,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "kernels.h"
 #include "learned.h"
 #include "mlp.h"
@@ -51,6 +53,15 @@ using namespace bte;
 namespace {
 
 enum ScratchId { SC_T1 = 0, SC_T2, SC_F, SC_QH, SC_FS, SC_Q1, SC_Q2, SC_MISC };
+
+// NVTX range over a host-side stage (enqueue of its launches; inside stream
+// capture it marks the capture, not the replays). A no-op without a profiler.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 bte_status fail(bte_ctx *c, bte_status s, const std::string &msg) {
     if (c) c->err = msg;
@@ -340,32 +351,37 @@ enum Post { POST_RAW = 0, POST_PROJECT = 1, POST_STAGE1 = 2, POST_STAGE2 = 3 };
 // y += a (qp + Q). Scratch must be ready (prepare).
 bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, int post,
                            const double *x, double *y, const double *qp, double a, cudaStream_t st) {
+    NvtxRange range_collide("bte_collide");
     const bool fp64 = mode == BTE_FP64_PLAIN;
     const ConvCfg cfg = cfg_of(c, B);
     ProfEntry pe_all{}, pe_conv{}, pe_fwd{}, pe_inv{};
     const int on_all = prof_begin(c, PK_COLLIDE, st, &pe_all);
-    const int on_fwd = prof_begin(c, PK_FORWARD, st, &pe_fwd);
-    for (const Segment &sg : B->segs) {
-        const Table *t = c->tables[sg.table];
-        DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
-        const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
-        if (fp64) {
-            launch_dft_forward<double2>(f, B->d_slot_off, ds, t->d_root64, sf, (double2 *)c->scratch[SC_T1],
-                                        (double2 *)c->scratch[SC_T2], (double2 *)c->scratch[SC_F], c->d_status, st);
-            count_launches(c, 3);
-        } else if (fused_dft_supported(t->N)) {
-            launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status,
-                                     st, cfg.split);
-            count_launches(c, 1);
-        } else {
-            launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
-                                       (float2 *)c->scratch[SC_T2], (float2 *)c->scratch[SC_F], c->d_status, st);
-            count_launches(c, 3);
+    {
+        NvtxRange range_fwd("bte_forward");
+        const int on_fwd = prof_begin(c, PK_FORWARD, st, &pe_fwd);
+        for (const Segment &sg : B->segs) {
+            const Table *t = c->tables[sg.table];
+            DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
+            const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+            if (fp64) {
+                launch_dft_forward<double2>(f, B->d_slot_off, ds, t->d_root64, sf, (double2 *)c->scratch[SC_T1],
+                                            (double2 *)c->scratch[SC_T2], (double2 *)c->scratch[SC_F], c->d_status, st);
+                count_launches(c, 3);
+            } else if (fused_dft_supported(t->N)) {
+                launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status,
+                                         st, cfg.split);
+                count_launches(c, 1);
+            } else {
+                launch_dft_forward<float2>(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_T1],
+                                           (float2 *)c->scratch[SC_T2], (float2 *)c->scratch[SC_F], c->d_status, st);
+                count_launches(c, 3);
+            }
+            cudaError_t e0 = cudaGetLastError();
+            if (e0 != cudaSuccess) return cuda_fail(c, e0, "forward transform launch");
         }
-        cudaError_t e0 = cudaGetLastError();
-        if (e0 != cudaSuccess) return cuda_fail(c, e0, "forward transform launch");
+        prof_end(c, on_fwd, pe_fwd, st);
     }
-    prof_end(c, on_fwd, pe_fwd, st);
+    NvtxRange range_conv(fp64 ? "bte_conv64" : "bte_conv32");
     if (fp64) {
         const int on = prof_begin(c, PK_CONV64, st, &pe_conv);
         for (const Segment &sg : B->segs) {
@@ -411,6 +427,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             return cuda_fail(c, e, msg);
         }
     }
+    NvtxRange range_inv("bte_inverse");
     const int on_inv = prof_begin(c, PK_INVERSE, st, &pe_inv);
     for (const Segment &sg : B->segs) {
         const Table *t = c->tables[sg.table];
@@ -504,6 +521,7 @@ bte_status check_mode(bte_ctx *c, int mode) {
 // the stream once (the flagged set decides the fallback launch).
 bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int64_t ncells, unsigned flags,
                            cudaStream_t st) {
+    NvtxRange range("bte_learned");
     Mlp *m = c->mlp;
     if (!B->uniform || B->segs.size() != 1 || m->table != 0)
         return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
@@ -743,6 +761,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
     cudaStream_t st = (cudaStream_t)stream;
     auto body = [&]() -> bte_status {
         if (tr) {
+            NvtxRange range_tr("bte_transport");
             ProfEntry pe{};
             const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
             launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
@@ -752,6 +771,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st);
         if (r != BTE_OK) return r;
         if (tr) {
+            NvtxRange range_tr("bte_transport");
             ProfEntry pe{};
             const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
             launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
