@@ -709,6 +709,8 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     launches = ctx.launch_count() - n0
     clocks = sampler.stop()
     st = ctx.learned_stats(reset=True)
+    ms_nn = _timed_steps(torch, lambda: ctx.collide(fw, Ql, mode=bte.LEARNED, fallback=False, stream=stream),
+                         args.steps, stream, flush, tag="surrogate")
     ms_f = _timed_steps(torch, lambda: ctx.collide(fw, Q32, mode=bte.FP32, stream=stream), args.steps,
                         stream, flush, tag="fp32")
     Q64 = torch.empty_like(fw)
@@ -738,6 +740,8 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                  sum(ms_l) / args.steps, wl, {
         "dtype": "bf16",
         "fp32": {"value": v_f, "unit": UNIT}, "fp64_plain": {"value": v_64, "unit": UNIT},
+        "surrogate_only": {"value": nx * args.steps / (sum(ms_nn) * 1e-3), "unit": UNIT,
+                           "note": "surrogate + projection, no indicator and no fallback"},
         "fallback": {"cells": st["cells"], "fallbacks": st["fallbacks"],
                      "rate": st["fallbacks"] / max(st["cells"], 1), "max_indicator": st["max_indicator"]},
         "accuracy": {"norm": "||Q - Q_oracle|| / ||Q_loss_oracle|| on %d sampled cells" % len(pick),

@@ -556,8 +556,8 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
     const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
     launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
                              c->dft_split);
-    launch_dft_forward_fused(Q, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_QH], c->d_status, st,
-                             c->dft_split);
+    launch_dft_forward_pencils(Q, B->d_slot_off, ds, sf, c->ind->d_kk, c->ind->S, (float2 *)c->scratch[SC_QH],
+                               c->d_status, st);  // only the sampled pencils are compared
     float *e2 = (float *)c->scratch[SC_MISC];
     float *d2 = e2 + (size_t)B->nslots * c->ind->S;
     float *ind = d2 + (size_t)B->nslots * c->ind->S;

@@ -193,6 +193,60 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
     cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
 }
 
+// Forward transform of a cell at the modes of a few zeta pencils only (the
+// sampled pencils of the learned path's indicator): the pass along j3 for every
+// (j1, j2) pencil, then for each sampled pencil (k1, k2) and each k3 the double
+// sum over (j1, j2) with phase conj(root(k1', j1') root(k2', j2')). Writes the
+// group layout at those modes only. One CTA per cell (N <= 16).
+template <int N>
+__global__ void __launch_bounds__(FusedShape<N, 1>::NT)
+dft_fwd_pencils_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, DftSeg s, float scale,
+                       const int *__restrict__ kks, int npen, float2 *__restrict__ G, int *status) {
+    using S = FusedShape<N, 1>;
+    constexpr int M = S::M, NN = S::NN, P = S::P, H = S::H;
+    extern __shared__ __align__(16) char smem_raw[];
+    float2 *A = reinterpret_cast<float2 *>(smem_raw);  // [j1][j2] rows of P, index k3
+    const int sl = blockIdx.x, t = threadIdx.x;
+    const int64_t off = slot_off[s.s0 + sl];
+    if (off < 0) return;
+    float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
+    const float2(&rt)[N] = CRoot<N>::get();
+    bool bad = false;
+    if (t < NN) {  // along j3, pencil (j1, j2) = t, real input
+        float x[N];
+        const double *fp = f + off + (int64_t)t * N;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double d = fp[j];
+            bad |= !isfinite(d);
+            x[j] = (float)d;
+        }
+        float2 y[N];
+        pencil_rc<N>(x, y, rt);
+#pragma unroll
+        for (int k = 0; k < N; ++k) A[t * P + k] = y[k];
+    }
+    if (bad) atomicOr(status, ST_NONFINITE);
+    __syncthreads();
+    for (int o = t; o < npen * N; o += S::NT) {
+        const int kk = kks[o / N], k3 = o % N, k1 = kk / N, k2 = kk % N;
+        float re = 0.f, im = 0.f;
+        for (int j1 = 0; j1 < N; ++j1) {
+            const float2 r1 = rt[(((k1 - H) * (j1 - H)) % N + N) % N];
+#pragma unroll
+            for (int j2 = 0; j2 < N; ++j2) {
+                const float2 r2 = rt[(((k2 - H) * (j2 - H)) % N + N) % N];
+                // w = conj(r1 r2)
+                const float wr = r1.x * r2.x - r1.y * r2.y, wi = -(r1.x * r2.y + r1.y * r2.x);
+                const float2 a = A[(j1 * N + j2) * P + k3];
+                re = fmaf(a.x, wr, fmaf(-a.y, wi, re));
+                im = fmaf(a.x, wi, fmaf(a.y, wr, im));
+            }
+        }
+        g[(int64_t)(kk * N + k3) * kLanes] = make_float2(scale * re, scale * im);
+    }
+}
+
 // mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q)
 // CTA r owns the slab k2 in [r JR, (r+1) JR) of the first pass and j1 in
 // [r JR, (r+1) JR) of the other two; the second pass reads the first pass's
@@ -456,6 +510,22 @@ void fused_dft_prepare(int N) {
         case 2: FN<N, 2>(__VA_ARGS__); break;          \
         default: FN<N, 4>(__VA_ARGS__); break;         \
     }
+
+void launch_dft_forward_pencils(const double *f, const int64_t *slot_off, const DftSeg &s, double scale,
+                                const int *kks, int npen, float2 *G, int *status, cudaStream_t st) {
+    switch (s.N) {
+        case 8: dft_fwd_pencils_kernel<8><<<s.nslots, FusedShape<8, 1>::NT, sizeof(float2) * 64 * 9, st>>>(
+                    f, slot_off, s, (float)scale, kks, npen, G, status);
+            break;
+        case 12: dft_fwd_pencils_kernel<12><<<s.nslots, FusedShape<12, 1>::NT, sizeof(float2) * 144 * 13, st>>>(
+                    f, slot_off, s, (float)scale, kks, npen, G, status);
+            break;
+        case 16: dft_fwd_pencils_kernel<16><<<s.nslots, FusedShape<16, 1>::NT, sizeof(float2) * 256 * 17, st>>>(
+                    f, slot_off, s, (float)scale, kks, npen, G, status);
+            break;
+        default: break;
+    }
+}
 
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, float2 *G, int *status, cudaStream_t st, int split) {

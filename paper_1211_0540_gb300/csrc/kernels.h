@@ -75,6 +75,9 @@ void launch_moments(const double *f, const int64_t *slot_off, int s0, int nslots
 // Inverse mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q).
 bool fused_dft_supported(int N);
 void fused_dft_prepare(int N);  // outside stream capture
+// forward transform of N <= 16 cells at the modes of npen zeta pencils kks[] (k1 N + k2) only
+void launch_dft_forward_pencils(const double *f, const int64_t *slot_off, const DftSeg &s, double scale,
+                                const int *kks, int npen, float2 *G, int *status, cudaStream_t st);
 // split: CTAs (a thread-block cluster) per cell, 1, 2 or 4 (other values: 4)
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, float2 *G, int *status, cudaStream_t st, int split = 4);

@@ -263,6 +263,8 @@ int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTab
     if (e == cudaSuccess) e = cudaMalloc(&out.d_pen, sizeof(IndPencil) * S);
     if (e == cudaSuccess) e = cudaMemcpy(out.d_wloss, wl.data(), sizeof(float) * wl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(out.d_pen, pens.data(), sizeof(IndPencil) * S, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&out.d_kk, sizeof(int) * S);
+    if (e == cudaSuccess) e = cudaMemcpy(out.d_kk, kks.data(), sizeof(int) * S, cudaMemcpyHostToDevice);
     // shared memory of the cross-warp reduction (set outside any stream capture)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(indicator_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ind_smem<8>());
     if (e == cudaSuccess) e = cudaFuncSetAttribute(indicator_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ind_smem<12>());
@@ -277,8 +279,10 @@ int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTab
 void free_indicator_table(IndicatorTable &t) {
     cudaFree(t.d_wloss);
     cudaFree(t.d_pen);
+    cudaFree(t.d_kk);
     t.d_wloss = nullptr;
     t.d_pen = nullptr;
+    t.d_kk = nullptr;
 }
 
 void launch_post_project(const float *Y, const double *rho, int B, int N, float s_out, const ProjArgs &pa, double *Q,

@@ -19,6 +19,7 @@ struct IndicatorTable {
     int S = 0;                     // sampled pencils (S x N sampled modes)
     float *d_wloss = nullptr;      // loss weights of the sampled pencils (pair-symmetrised, times dz^3)
     IndPencil *d_pen = nullptr;
+    int *d_kk = nullptr;           // the sampled pencils' k1 N + k2
 };
 
 // modes: about this many sampled modes (pencils = modes / N, at least 1)
