@@ -764,7 +764,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
             NvtxRange range_tr("bte_transport");
             ProfEntry pe{};
             const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
-            launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            launch_transport_half(f, (double *)c->scratch[SC_FS], (double *)c->scratch[SC_Q1], ta, 0.5 * dt, st);
             prof_end(c, on, pe, st);
             count_launches(c, 2);
         }
@@ -774,7 +774,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
             NvtxRange range_tr("bte_transport");
             ProfEntry pe{};
             const int on = prof_begin(c, PK_TRANSPORT, st, &pe);
-            launch_transport_half(f, (double *)c->scratch[SC_FS], ta, 0.5 * dt, st);
+            launch_transport_half(f, (double *)c->scratch[SC_FS], (double *)c->scratch[SC_Q1], ta, 0.5 * dt, st);
             prof_end(c, on, pe, st);
             count_launches(c, 2);
         }

@@ -3,12 +3,13 @@
 //   forward:  fhat_k = (2 pi)^{-3/2} dv^3 sum_j f_j exp(-i zeta_k . v_j)
 //   inverse:  Qt_j = Re (2 pi)^{-3/2} dz^3 sum_k Qhat_k exp(+i zeta_k . v_j)
 // (Sec. 3.2, grid of Eq. meshpoints; zeta_k . v_j = 2 pi k'.j' / N.)
-// One CTA per cell, one thread per pencil: each of the three one-dimensional
-// passes loads the N values of a pencil into registers and multiplies them by
-// the N x N phase matrix exp(+-2 pi i (k - N/2)(j - N/2) / N). With both loops
-// unrolled the phase index ((k - N/2)(j - N/2) mod N) is a compile-time
-// constant, so the N roots of unity sit in registers and the matrix costs no
-// memory traffic; shared memory is touched once per value and pass (rows
+// A cell is one CTA or a cluster of C CTAs, one thread per pencil: each of
+// the three one-dimensional passes loads the N values of a pencil into
+// registers and applies the phases exp(+-2 pi i (k - N/2)(j - N/2) / N) by a
+// mixed-radix FFT (fft_reg.cuh: the centred phases are the plain DFT with
+// the signs (-1)^j on the input and (-1)^k on the output). All indices are
+// compile-time constants, so the roots of unity come from constant memory as
+// FMA operands; shared memory is touched once per value and pass (rows
 // padded to N + 1 against bank conflicts). The forward kernel writes fhat
 // straight into the group layout of the convolution ([group][k][lane]); the
 // inverse kernel reads Qhat from it and applies the conservation projection
@@ -24,6 +25,7 @@
 #include <cmath>
 #include <map>
 
+#include "fft_reg.cuh"
 #include "project.cuh"
 
 namespace cg = cooperative_groups;
@@ -61,61 +63,34 @@ template <> struct CRoot<16> { static __device__ const float2 (&get())[16] { ret
 template <> struct CRoot<24> { static __device__ const float2 (&get())[24] { return c_root24; } };
 template <> struct CRoot<32> { static __device__ const float2 (&get())[32] { return c_root32; } };
 
-// phase index of W[k][j] = root[((k - N/2)(j - N/2)) mod N]
-template <int N>
-__host__ __device__ constexpr int phase(int k, int j) {
-    return (((k - N / 2) * (j - N / 2)) % N + N) % N;
-}
-
-// y_k = sum_j x_j W[k][j], W = root (CONJ: conjugated), complex in and out.
-// Inputs outer, outputs inner: the N accumulators are independent, so
-// consecutive FMAs never wait on each other.
+// y_k = sum_j x_j W[k][j], W[k][j] = root[((k - N/2)(j - N/2)) mod N]
+// (CONJ: conjugated), complex in and out,
+// by the register FFT (the centred phases are a sign modulation of the
+// plain DFT, see fft_reg.cuh).
 template <int N, bool CONJ>
 __device__ __forceinline__ void pencil_cc(const float2 (&x)[N], float2 (&y)[N], const float2 (&rt)[N]) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const float wr = rt[phase<N>(k, j)].x;
-            const float wi = CONJ ? -rt[phase<N>(k, j)].y : rt[phase<N>(k, j)].y;
-            y[k].x = fmaf(x[j].x, wr, y[k].x);
-            y[k].x = fmaf(-x[j].y, wi, y[k].x);
-            y[k].y = fmaf(x[j].x, wi, y[k].y);
-            y[k].y = fmaf(x[j].y, wr, y[k].y);
-        }
-    }
+    for (int j = 0; j < N; ++j) y[j] = x[j];
+    fftr::centred<N, CONJ ? -1 : 1>(y, rt);
 }
 
-// real input (forward first pass)
+// real input, conjugated phases (forward first pass)
 template <int N>
 __device__ __forceinline__ void pencil_rc(const float (&x)[N], float2 (&y)[N], const float2 (&rt)[N]) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            y[k].x = fmaf(x[j], rt[phase<N>(k, j)].x, y[k].x);
-            y[k].y = fmaf(x[j], -rt[phase<N>(k, j)].y, y[k].y);
-        }
-    }
+    for (int j = 0; j < N; ++j) y[j] = make_float2(x[j], 0.f);
+    fftr::centred<N, -1>(y, rt);
 }
 
 // real part of the output (inverse last pass)
 template <int N>
 __device__ __forceinline__ void pencil_cr(const float2 (&x)[N], float (&y)[N], const float2 (&rt)[N]) {
+    float2 z[N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) y[k] = 0.f;
+    for (int j = 0; j < N; ++j) z[j] = x[j];
+    fftr::centred<N, 1>(z, rt);
 #pragma unroll
-    for (int j = 0; j < N; ++j) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            y[k] = fmaf(x[j].x, rt[phase<N>(k, j)].x, y[k]);
-            y[k] = fmaf(-x[j].y, rt[phase<N>(k, j)].y, y[k]);
-        }
-    }
+    for (int k = 0; k < N; ++k) y[k] = z[k].x;
 }
 
 // Cluster barrier without memory ordering: only keeps every CTA of the

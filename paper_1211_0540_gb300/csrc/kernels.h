@@ -97,8 +97,11 @@ struct TransportArgs {
     // filled per sub-step by launch_transport_half:
     double rden_left, rden_right;   // 1 / den (0 when den is 0)
     double kv[kTransportMaxN];      // (tau / dx) v1_i,  v1_i = dv (i - N/2)
+    double kvh[kTransportMaxN];     // kv / 2
     double wv[kTransportMaxN];      // |v1_i|
 };
-void launch_transport_half(double *f, double *f1, const TransportArgs &ta, double tau, cudaStream_t st);
+// One transport half step of the slab f (in place); f1 and fh are scratch of f's size.
+void launch_transport_half(double *f, double *f1, double *fh, const TransportArgs &ta, double tau,
+                           cudaStream_t st);
 
 }  // namespace bte

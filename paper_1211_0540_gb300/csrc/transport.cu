@@ -8,7 +8,8 @@
 // the face values need no division. FP64 arithmetic is expensive on this GPU
 // (about 1/75 of the FP32 rate), so minmod works on the IEEE bit patterns
 // (integer compares), the wall Maxwellians, (tau/dx) v1 and |v1| are tabulated
-// on the host and the update takes six FP64 operations per value.
+// on the host, and a sliding stencil window leaves four FP64 operations per
+// value in the second Heun stage and five in the first.
 // Walls (two ghost cells each side, formed on the fly):
 // - diffuse (Sec. 2.1, Eq. BC): components entering the slab take
 //   sigma_w M_w(v), M_w = (2 pi T_w)^{-3/2} exp(-|v|^2 / (2 T_w)); sigma_w is the
@@ -23,7 +24,8 @@
 namespace bte {
 
 namespace {
-constexpr int kTThreads = 256;
+constexpr int kTThreads = 128;  // consecutive velocities of one cell chunk
+constexpr int kTChunk = 8;      // cells per thread (sliding stencil window)
 
 // minmod(a, b) = 0 if a b <= 0, else the argument of smaller magnitude.
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -72,55 +74,78 @@ __device__ __forceinline__ double ext(const double *__restrict__ f, int x, int j
     return f[(int64_t)(left ? 0 : a.nx - 1) * M + j];
 }
 
-// stage 1: f1 = f + tau R(f)      (src = f)
-// stage 2: f  = (f + f1 + tau R(f1)) / 2   (src = f1)
+// Heun stages of one transport half step, written so that the second stage
+// needs one FMA per value:
+//   stage 1: f1 = f + tau R(f),  h = f + (tau / 2) R(f)       (src = f)
+//   stage 2: f  = h + (tau / 2) R(f1)  (= (f + f1 + tau R(f1)) / 2)   (src = f1)
 // With the upwind side fixed by the sign of v1 only four stencil points are
 // read, e_0..e_3 = cells c-2..c+1 (v1 >= 0) or c-1..c+2 (v1 < 0), and with
 // D_q = e_q - e_{q-1} the two face values of cell c differ by
-//   f_{c+1/2} - f_{c-1/2} = D_2 +- (minmod(D_2, D_3) - minmod(D_1, D_2)) / 2,
-// so tau R = -(tau / dx) v1 (f_{c+1/2} - f_{c-1/2}) costs six FP64 operations.
+//   g = f_{c+1/2} - f_{c-1/2} = D_2 +- (minmod(D_2, D_3) - minmod(D_1, D_2)) / 2,
+// and tau R = -(tau / dx) v1 g. A thread takes kTChunk consecutive cells of
+// one velocity: it loads their kTChunk + 3 stencil points at once, forms each
+// difference D and each minmod once, then per value two operations for g and
+// one FMA per output (two in stage 1).
 template <int STAGE>
-__global__ void __launch_bounds__(kTThreads) transport_stage_kernel(double *__restrict__ f,
-                                                                     double *__restrict__ f1,
+__global__ void __launch_bounds__(kTThreads) transport_stage_kernel(const double *__restrict__ src,
+                                                                     double *__restrict__ out,
+                                                                     double *__restrict__ half,
                                                                      const __grid_constant__ TransportArgs a) {
     const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
-    const int c = blockIdx.y;
-    const double *src = STAGE == 1 ? f : f1;
-    // walls: only the CTAs whose stencil reaches a diffuse ghost need sigma_w
+    const int c0 = blockIdx.y * kTChunk, c1 = min(c0 + kTChunk, a.nx);
+    // walls: only the chunks whose stencil reaches a diffuse ghost need sigma_w
     double sig_l = 0.0, sig_r = 0.0;
-    if (c < 2 && a.bc_left == BTE_BC_DIFFUSE) sig_l = wall_sigma(src, a, 0);
-    if (c >= a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE) sig_r = wall_sigma(src, a, 1);
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
-        const int i = j / NN;
-        const bool pos = i >= h;
-        const int x0 = pos ? c - 2 : c - 1;
-        double e[4];
+    if (c0 < 2 && a.bc_left == BTE_BC_DIFFUSE) sig_l = wall_sigma(src, a, 0);
+    if (c1 > a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE) sig_r = wall_sigma(src, a, 1);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int i = j / NN;
+    const bool pos = i >= h;
+    const double sgn = pos ? 0.5 : -0.5, kv = a.kv[i], kvh = a.kvh[i];
+    const int x0 = pos ? c0 - 2 : c0 - 1;  // first stencil point of cell c0
+    const int ne = c1 - c0 + 3;            // stencil points of the chunk
+    // all loads first (independent, in flight together), then the arithmetic
+    double e[kTChunk + 3];
 #pragma unroll
-        for (int d = 0; d < 4; ++d) e[d] = ext(src, x0 + d, j, i, a, sig_l, sig_r);
-        const double D1 = e[1] - e[0], D2 = e[2] - e[1], D3 = e[3] - e[2];
-        const double g = fma(pos ? 0.5 : -0.5, minmod(D2, D3) - minmod(D1, D2), D2);
-        const double own = pos ? e[2] : e[1];  // src at cell c
-        const int64_t idx = (int64_t)c * M + j;
-        if (STAGE == 1) f1[idx] = fma(-a.kv[i], g, own);
-        else f[idx] = 0.5 * fma(-a.kv[i], g, f[idx] + own);
+    for (int d = 0; d < kTChunk + 3; ++d) e[d] = d < ne ? ext(src, x0 + d, j, i, a, sig_l, sig_r) : 0.0;
+    double D[kTChunk + 2], m[kTChunk + 1];
+#pragma unroll
+    for (int d = 0; d < kTChunk + 2; ++d) D[d] = e[d + 1] - e[d];
+#pragma unroll
+    for (int d = 0; d < kTChunk + 1; ++d) m[d] = minmod(D[d], D[d + 1]);
+#pragma unroll
+    for (int q = 0; q < kTChunk; ++q) {
+        if (c0 + q >= c1) break;
+        // cell c = c0 + q: D_1, D_2, D_3 = D[q], D[q + 1], D[q + 2]
+        const double g = fma(sgn, m[q + 1] - m[q], D[q + 1]);
+        const double own = pos ? e[q + 2] : e[q + 1];  // src at cell c
+        const int64_t idx = (int64_t)(c0 + q) * M + j;
+        if (STAGE == 1) {
+            out[idx] = fma(-kv, g, own);
+            half[idx] = fma(-kvh, g, own);
+        } else {
+            out[idx] = fma(-kvh, g, half[idx]);
+        }
     }
 }
 }  // namespace
 
-void launch_transport_half(double *f, double *f1, const TransportArgs &ta, double tau, cudaStream_t st) {
+void launch_transport_half(double *f, double *f1, double *fh, const TransportArgs &ta, double tau,
+                           cudaStream_t st) {
     const int M = ta.N * ta.N * ta.N, h = ta.N / 2;
     TransportArgs a = ta;
     const double k = tau / ta.dx;
     for (int i = 0; i < kTransportMaxN; ++i) {
         const double v1 = i < ta.N ? ta.dv * (i - h) : 0.0;
         a.kv[i] = k * v1;
+        a.kvh[i] = 0.5 * a.kv[i];
         a.wv[i] = v1 < 0.0 ? -v1 : v1;
     }
     a.rden_left = ta.den_left > 0.0 ? 1.0 / ta.den_left : 0.0;
     a.rden_right = ta.den_right > 0.0 ? 1.0 / ta.den_right : 0.0;
-    dim3 grid((M + kTThreads - 1) / kTThreads, ta.nx);
-    transport_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, a);
-    transport_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f, f1, a);
+    dim3 grid((M + kTThreads - 1) / kTThreads, (ta.nx + kTChunk - 1) / kTChunk);
+    transport_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, fh, a);
+    transport_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f1, f, fh, a);
 }
 
 }  // namespace bte
