@@ -38,22 +38,33 @@ __device__ __forceinline__ double minmod(double a, double b) {
 // sigma_w for the wall of `side` (0 left, 1 right), reduced by the whole CTA.
 // Outgoing components (v.n < 0 for the inward normal n) are i < N/2 at the
 // left wall and i > N/2 at the right wall; |v.n| = |v1_i| is tabulated.
+// The outgoing components form one contiguous range of j (i is the slowest
+// index); four independent loads per step keep the reduction off the memory
+// latency (the wall CTAs would otherwise set the kernel's duration).
 __device__ double wall_sigma(const double *__restrict__ f, const TransportArgs &a, int side) {
     __shared__ double red[kTThreads / 32];
     const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
     const double *fc = f + (int64_t)(side == 0 ? 0 : a.nx - 1) * M;
-    double out = 0.0;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const int i = j / NN;
-        if (side == 0 ? i < h : i > h) out = fma(a.wv[i], fc[j], out);
+    const int j0 = side == 0 ? 0 : (h + 1) * NN, j1 = side == 0 ? h * NN : M;
+    const int T = blockDim.x;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = j0 + threadIdx.x;
+    for (; j + 3 * T < j1; j += 4 * T) {
+        double x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = fc[j + u * T];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = fma(a.wv[(j + u * T) / NN], x[u], s[u]);
     }
+    for (; j < j1; j += T) s[0] = fma(a.wv[j / NN], fc[j], s[0]);
+    double out = (s[0] + s[1]) + (s[2] + s[3]);
     for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = out;
     __syncthreads();
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
     __syncthreads();
-    return s * (side == 0 ? a.rden_left : a.rden_right);
+    return tot * (side == 0 ? a.rden_left : a.rden_right);
 }
 
 // Value of the extended array at cell x in [-2, nx + 1], velocity j.
