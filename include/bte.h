@@ -184,7 +184,10 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  * name: "conv_impl"   0 = one warp per work item, 1 = all warps of a CTA share
  *                      an item (reduced in shared memory), 2 = as 1 with packed
  *                      f32x2 arithmetic, 3 = as 2 with up to 255 registers per
- *                      thread (2 CTAs per SM);
+ *                      thread (2 CTAs per SM), 4 (default) = as 2 with each
+ *                      warp's compensated sums in shared memory instead of
+ *                      registers (the b-row stays in registers as packed
+ *                      operands for the whole block);
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
  *       "conv_stages" blocks in flight per warp (1..4; 0 = automatic, the
  *                      default: the deepest ring up to 2 that keeps the
@@ -195,7 +198,7 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
  *                      transforms of N <= 16: 1, 2 or 4 (default 4);
  *       "debug_conv_stall" testing only: 1 makes every warp of the
- *                      cooperative convolution (conv_impl 1, 2) skip the
+ *                      cooperative convolution (conv_impl 1..4) skip the
  *                      copies of its first block, so that its bounded wait runs
  *                      out: the call completes after about two seconds, the
  *                      next bte_sync_status returns BTE_ETIMEOUT and the

@@ -885,7 +885,7 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 }
 
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
-    if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 3; return &c->conv_impl; }
+    if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 4; return &c->conv_impl; }
     if (!std::strcmp(name, "dft_split")) { *lo = 1; *hi = 4; return &c->dft_split; }
     if (!std::strcmp(name, "debug_conv_stall")) { *lo = 0; *hi = 1; return &c->debug_conv_stall; }
     if (!std::strcmp(name, "profile_mask")) { *lo = 0; *hi = 63; return &c->prof_mask; }
@@ -973,7 +973,7 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
     ConvCfg best;
     best.ms = -1.0;
     bte_status err = BTE_OK;
-    for (int impl : {2, 1, 3})
+    for (int impl : {2, 4, 1, 3})
         for (int warps : {4, 3})
             for (int stages : {1, 2})
                 for (int merge : {16, 32})
@@ -1159,7 +1159,7 @@ bte_status bte_tune_load(bte_ctx *c, const char *path, int *loaded) {
                         "\"split\": %d, \"ms\": %lf}",
                         key, &g.impl, &g.warps, &g.stages, &g.merge, &g.split, &g.ms) != 7)
             return fail(c, BTE_EINVAL, "bte_tune_load: malformed entry: " + line);
-        if (g.impl < 0 || g.impl > 3 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
+        if (g.impl < 0 || g.impl > 4 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
             (g.split != 1 && g.split != 2 && g.split != 4))
             return fail(c, BTE_EINVAL, "bte_tune_load: out-of-range entry: " + line);
         got[key] = g;

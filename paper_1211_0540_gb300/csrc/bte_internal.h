@@ -89,7 +89,7 @@ struct GraphKey {
 // One configuration of the FP32 path (convolution variant and launch shape,
 // compensated-merge interval, CTAs per cell of the fused transforms).
 struct ConvCfg {
-    int impl = 2, warps = 4, stages = 0, merge = 16, split = 4;
+    int impl = 4, warps = 4, stages = 0, merge = 16, split = 4;
     double ms = 0.0;  // measured time of one collide of the batch when tuned
 };
 
@@ -141,7 +141,8 @@ struct bte_ctx {
     int conv_warps = 4;        // warps per CTA of the convolution kernel
     int conv_stages = 0;       // pipeline depth (blocks in flight per warp); 0 = automatic
     int conv_merge = 16;       // blocks per compensated (TwoSum) merge
-    int conv_impl = 2;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2
+    int conv_impl = 4;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2,
+                               // 3 as 2 at 2 CTAs/SM, 4 as 2 with the compensated sums in shared memory
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
     int debug_conv_stall = 0;  // testing only: make the convolution's waits run out
     std::string gpu_name;      // device name (key of saved tuning caches)

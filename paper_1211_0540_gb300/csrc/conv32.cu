@@ -407,13 +407,13 @@ __device__ bool coop_item(WarpRing &r, const ConvItem &it, const ConvParams &p, 
 // Cross-warp reduction of the partials (fixed warp order) and the store.
 template <class K>
 __device__ __forceinline__ void coop_reduce(const ConvItem &it, const ConvParams &p, int lane, int warp,
-                                            int nwarps, const char *ring0, int warp_smem) {
+                                            int nwarps, const char *ring0, int warp_smem, int sums_off = 0) {
     constexpr int T = K::T;
     float2 *Q = p.Qh + it.fofs + ((size_t)(it.k1 * K::N + it.k2) * K::N + K::K0) * kLanes + lane;
     for (int t = warp; t < T; t += nwarps) {
         float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
         for (int w = 0; w < nwarps; ++w) {
-            const float *red = reinterpret_cast<const float *>(ring0 + (size_t)w * warp_smem);
+            const float *red = reinterpret_cast<const float *>(ring0 + (size_t)w * warp_smem + sums_off);
             two_sum(sr, lr, red[(2 * t) * kLanes + lane]);
             lr += red[(2 * T + 2 * t) * kLanes + lane];
             two_sum(si, li, red[(2 * t + 1) * kLanes + lane]);
@@ -437,6 +437,169 @@ __device__ __forceinline__ bool coop_run(WarpRing &r, const ConvItem &it, const 
     // the rings are next written by TMA (async proxy) after these generic accesses
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return !*abort_flag;
+}
+
+// ---------------------------------------------------------------------------
+// v4: as v2, with the compensated (hi, lo) sums of each warp in shared memory
+// (4T x 32 floats after the warp's ring) instead of registers: they are
+// touched only at a merge (every `merge` blocks). The registers freed let the
+// block loop keep the b-row as packed (re, im) and (-im, re) operands for the
+// whole block (N <= 16), so a pair costs its three packed FMA-pipe
+// instructions and the (w, w) operand only. One-block rings keep 3 CTAs per
+// SM (4 warps x (one 8.75 KB stage + 8 KB of sums) at N = 16).
+// ---------------------------------------------------------------------------
+template <class K>
+__device__ __forceinline__ void conv_block_packed_h(const char *st, int lane, uint64_t (&part)[K::T]) {
+    const float2 *A = reinterpret_cast<const float2 *>(st);
+    const float2 *B = A + K::N * kLanes;
+    const float4 *W4 = reinterpret_cast<const float4 *>(B + K::N * kLanes);
+    uint64_t bb[K::N], bs[K::N];
+#pragma unroll
+    for (int n = 0; n < K::N; ++n) {
+        const float2 b = B[n * kLanes + lane];
+        bb[n] = pk2(b.x, b.y);
+        bs[n] = pk2(-b.y, b.x);
+    }
+    float4 w4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    int wi = 0;
+#pragma unroll
+    for (int m3 = 0; m3 < K::N; ++m3) {
+        const float2 a = A[m3 * kLanes + lane];
+        const uint64_t aR = pk2(a.x, a.x), aI = pk2(a.y, a.y);
+#pragma unroll
+        for (int j = 0; j < K::T; ++j) {
+            const int n3 = K::K0 + j - m3 + K::H;
+            if (n3 >= 0 && n3 < K::N) {
+                if ((wi & 3) == 0) w4 = W4[wi >> 2];
+                const float w = (wi & 3) == 0 ? w4.x : (wi & 3) == 1 ? w4.y : (wi & 3) == 2 ? w4.z : w4.w;
+                ++wi;
+                uint64_t pr = fmul2(aR, bb[n3]);
+                pr = ffma2(aI, bs[n3], pr);
+                part[j] = ffma2(pk2(w, w), pr, part[j]);
+            }
+        }
+    }
+}
+
+// Bytes of a warp's shared (hi, lo) sums: 4T x 32 floats with T <= 16.
+constexpr int kSumsBytes = 4 * 16 * kLanes * 4;
+
+// One item by all warps of the CTA, sums in shared memory at r.base + ring
+// bytes. Returns false if this warp timed out.
+template <class K>
+__device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane, int warp,
+                             int nwarps, float *sums) {
+    constexpr int T = K::T;
+    const int nb = (int)it.nblocks;
+    const int S = p.stages;
+    const int mine = nb > warp ? (nb - warp + nwarps - 1) / nwarps : 0;
+    if (lane == 0)
+        for (int s = 0; s < S && s < mine; ++s)
+            if (!(p.stall && s == 0)) issue_block<K>(r, s, it, p, warp + s * nwarps);
+#pragma unroll
+    for (int q = 0; q < 4 * T; ++q) sums[q * kLanes + lane] = 0.f;
+    __syncwarp();
+    uint64_t pp[T];
+#pragma unroll
+    for (int i = 0; i < T; ++i) pp[i] = 0ull;
+
+    bool ok = true;
+    int since = 0, i = 0;
+    for (; i < mine; ++i) {
+        const int s = i % S;
+        bool got = mbar_wait_bounded(r.bars + 8u * s, (r.phase >> s) & 1u);
+        got = __all_sync(0xffffffffu, got);
+        if (!got) {
+            ok = false;
+            break;
+        }
+        r.phase ^= (1u << s);
+        if (K::N <= 16) conv_block_packed_h<K>(r.base + s * r.stage_bytes, lane, pp);
+        else conv_block_packed<K>(r.base + s * r.stage_bytes, lane, pp);
+        if (++since == p.merge || i == mine - 1) {
+            since = 0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const float2 v = up2(pp[t]);
+                float *h = sums + (2 * t) * kLanes + lane, *l = sums + (2 * T + 2 * t) * kLanes + lane;
+                float hr = h[0], lr = l[0], hi = h[kLanes], li = l[kLanes];
+                two_sum(hr, lr, v.x);
+                two_sum(hi, li, v.y);
+                h[0] = hr;
+                l[0] = lr;
+                h[kLanes] = hi;
+                l[kLanes] = li;
+                pp[t] = 0ull;
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && i + S < mine) issue_block<K>(r, s, it, p, warp + (i + S) * nwarps);
+    }
+    if (!ok) {
+        const int last = mine < i + S ? mine : i + S;
+        for (int jj = i; jj < last; ++jj) {
+            const int s = jj % S;
+            if (mbar_wait_bounded(r.bars + 8u * s, (r.phase >> s) & 1u)) r.phase ^= (1u << s);
+        }
+        __syncwarp();
+    }
+    return ok;
+}
+
+template <class K>
+__device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
+                                            int warp, int nwarps, char *ring0, int *abort_flag, float *sums,
+                                            int sums_off) {
+    const bool ok = coop_item_sm<K>(r, it, p, lane, warp, nwarps, sums);
+    if (!ok && lane == 0) {
+        atomicOr(p.status, ST_TIMEOUT);
+        *abort_flag = 1;
+    }
+    __syncthreads();
+    if (!*abort_flag) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off);
+    __syncthreads();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    return !*abort_flag;
+}
+
+template <unsigned MASK>
+__global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ int s_item, s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int ring = p.warp_smem - kSumsBytes;
+    WarpRing r;
+    r.base = smem + (size_t)warp * p.warp_smem;
+    r.stage_bytes = ring / p.stages;
+    r.bars = smem_u32(smem + (size_t)nwarps * p.warp_smem) + 8u * kMaxStages * warp;
+    r.phase = 0;
+    float *sums = reinterpret_cast<float *>(r.base + ring);
+    if (lane == 0) {
+        for (int s = 0; s < p.stages; ++s) mbar_init(r.bars + 8u * s, 1);
+        fence_mbar_init();
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.counter, 1u);
+        __syncthreads();
+        const int idx = s_item;
+        if (idx >= p.nitems || s_abort) break;
+        const ConvItem it = p.items[idx];
+        bool ok = true;
+        switch (it.kind) {
+            case 0: if (MASK & 1u) ok = coop_run_sm<K8>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 1: if (MASK & 2u) ok = coop_run_sm<K12>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 2: if (MASK & 4u) ok = coop_run_sm<K16>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 3: if (MASK & 8u) ok = coop_run_sm<K24a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 4: if (MASK & 16u) ok = coop_run_sm<K24b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 5: if (MASK & 32u) ok = coop_run_sm<K32a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 6: if (MASK & 64u) ok = coop_run_sm<K32b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            default: break;
+        }
+        if (!ok) break;
+    }
 }
 
 template <unsigned MASK, bool PACKED, int MINB = 3>
@@ -523,7 +686,7 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     for (int k = 0; k < kNumKinds; ++k)
         if (kinds_mask & (1u << k)) stage = stage > conv_stage_bytes(k) ? stage : conv_stage_bytes(k);
     L.stages = stages > kMaxStages ? kMaxStages : stages;
-    L.warp_smem = stage * L.stages;
+    L.warp_smem = stage * L.stages + (impl == 4 ? kSumsBytes : 0);
     const int max_smem = 227 * 1024;
     const int max_warps = impl == 0 ? 8 : 4;
     int warps = warps_per_cta < 1 ? 1 : (warps_per_cta > max_warps ? max_warps : warps_per_cta);
@@ -542,7 +705,9 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     } else {
         const bool packed = impl >= 2;
 #define BTE_PICK(M)                                                                             \
-    L.fn = impl == 3 ? conv32_coop_kernel<M, true, 2> : (packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>)
+    L.fn = impl == 4   ? conv32_sums_kernel<M>                                                 \
+           : impl == 3 ? conv32_coop_kernel<M, true, 2>                                        \
+                       : (packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>)
         switch (kinds_mask) {
             case 1u: BTE_PICK(1u); break;
             case 2u: BTE_PICK(2u); break;

@@ -53,7 +53,8 @@ struct ConvLaunch {
 };
 // kinds_mask: bit i set when items of kind i are present. Sets the kernel's
 // shared-memory attribute: call outside stream capture.
-// impl: 0 = one warp per item, 1 = CTA-cooperative items, 2 = cooperative + packed f32x2.
+// impl: 0 = one warp per item, 1 = CTA-cooperative items, 2 = cooperative + packed f32x2,
+// 3 = as 2 at 2 CTAs per SM, 4 = as 2 with the compensated sums in shared memory.
 cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages, int impl,
                              ConvLaunch *out);
 cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t st);

@@ -25,10 +25,12 @@ def bte():
     return b
 
 
-def test_bounded_wait_reports_timeout_and_context_recovers(bte):
+@pytest.mark.parametrize("impl", [2, 4])  # sums in registers / in shared memory
+def test_bounded_wait_reports_timeout_and_context_recovers(bte, impl):
     N, lam = 8, 1.0
     c = bte.Context(0)
     c.init_weights([(N, L, lam)])
+    c.set_option("conv_impl", impl)
     f = inputs.homogeneous_cells(N, L, 40, seed=41)
     ft = torch.from_numpy(f).cuda()
     s = torch.cuda.Stream()

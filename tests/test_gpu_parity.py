@@ -67,7 +67,7 @@ def run_collide(bte, N, lam, f, mode, raw=False):
     return Q.cpu().numpy().reshape(f.shape)
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2, 3])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("N,ncells,lam", [(8, 5, 1.0), (8, 70, 0.0), (12, 37, 1.0), (16, 33, 1.0),
                                           (24, 3, 1.0)])
 def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
@@ -75,7 +75,7 @@ def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
     c = ctx_for(bte, ((N, L, lam),))
     impl0, merge0 = c.get_option("conv_impl"), c.get_option("conv_merge")
     c.set_option("conv_impl", impl)
-    c.set_option("conv_merge", (1 + impl) * (1 + impl))  # 1, 4, 9: merges inside and across blocks
+    c.set_option("conv_merge", (1 + impl) * (1 + impl))  # 1, 4, 9, 16, 25: merges inside and across blocks
     try:
         Qg = run_collide(bte, N, lam, f, bte.FP32)
     finally:
@@ -387,7 +387,7 @@ def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
     c = bte.Context(0)
     c.init_weights([(N, L, lam)])
     cfg = c.autotune(ft, reps=2)
-    assert cfg["conv_impl"] in (1, 2, 3) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
+    assert cfg["conv_impl"] in (1, 2, 3, 4) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
     assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 4) and cfg["ms"] > 0.0
     Q = c.collide(ft)
     c.sync_status()
