@@ -85,6 +85,7 @@ def parse():
                          "lets a profiler run the configuration a plain run chose")
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
+    ap.add_argument("--conv-warps", type=int, default=None, help="warps per CTA of the convolution (conv_warps)")
     ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
                     help="wall-heating (the headline line) or one of the secondary workloads")
@@ -263,6 +264,8 @@ def main():
     ctx.init_weights([(N, L, LAM)])
     if args.conv_impl is not None:
         ctx.set_option("conv_impl", args.conv_impl)
+    if args.conv_warps is not None:
+        ctx.set_option("conv_warps", args.conv_warps)
     if args.dft_split is not None:
         ctx.set_option("dft_split", args.dft_split)
     ctx.set_option("profile_mask", 1)  # timed steps: events around the convolution only
@@ -273,7 +276,7 @@ def main():
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     tuned = None
-    if args.conv_impl is None and args.dft_split is None:
+    if args.conv_impl is None and args.conv_warps is None and args.dft_split is None:
         tuned = tune(args, ctx, f, stream, reps=10)  # untimed: picks the launch configuration
     ctx.profile_enable(True)
 
@@ -840,6 +843,8 @@ def run_secondary(args):
     ctx = bte.Context(local)
     if args.conv_impl is not None:
         ctx.set_option("conv_impl", args.conv_impl)
+    if args.conv_warps is not None:
+        ctx.set_option("conv_warps", args.conv_warps)
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)

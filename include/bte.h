@@ -230,7 +230,7 @@ bte_status bte_state_load(bte_ctx *ctx, const char *path, double *f, int64_t n, 
 
 /* Autotuner of the FP32 path. For the batch described by (inst, ninst) (as in
  * bte_collide) it runs one projected FP32 collide of f per candidate
- * configuration -- convolution variant 1, 2 or 3, 3 or 4 warps per CTA, 1 or 2
+ * configuration -- convolution variant 1, 2, 3 or 4, 3 or 4 warps per CTA, 1 or 2
  * blocks in flight per warp, compensated merge every 16 or 32 blocks, and for
  * N <= 16 one or four CTAs per cell in the fused transforms -- times reps
  * repetitions with CUDA events on `stream`, and keeps the fastest as this

@@ -973,7 +973,7 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
     ConvCfg best;
     best.ms = -1.0;
     bte_status err = BTE_OK;
-    for (int impl : {2, 4, 1, 3})
+    for (int impl : {4, 2, 1, 3})
         for (int warps : {4, 3})
             for (int stages : {1, 2})
                 for (int merge : {16, 32})
