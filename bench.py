@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--conv-impl", type=int, default=None,
                     help="convolution kernel variant (bte_set_option conv_impl); default: library choice")
     ap.add_argument("--conv-warps", type=int, default=None, help="warps per CTA of the convolution (conv_warps)")
+    ap.add_argument("--conv-split", type=int, default=None, choices=[0, 1],
+                    help="variant 4: cut the costliest pencil items in two (conv_split)")
     ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
                     help="wall-heating (the headline line) or one of the secondary workloads")
@@ -266,6 +268,8 @@ def main():
         ctx.set_option("conv_impl", args.conv_impl)
     if args.conv_warps is not None:
         ctx.set_option("conv_warps", args.conv_warps)
+    if args.conv_split is not None:
+        ctx.set_option("conv_split", args.conv_split)
     if args.dft_split is not None:
         ctx.set_option("dft_split", args.dft_split)
     ctx.set_option("profile_mask", 1)  # timed steps: events around the convolution only
@@ -276,7 +280,7 @@ def main():
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     tuned = None
-    if args.conv_impl is None and args.conv_warps is None and args.dft_split is None:
+    if args.conv_impl is None and args.conv_warps is None and args.conv_split is None and args.dft_split is None:
         tuned = tune(args, ctx, f, stream, reps=10)  # untimed: picks the launch configuration
     ctx.profile_enable(True)
 
@@ -845,6 +849,8 @@ def run_secondary(args):
         ctx.set_option("conv_impl", args.conv_impl)
     if args.conv_warps is not None:
         ctx.set_option("conv_warps", args.conv_warps)
+    if args.conv_split is not None:
+        ctx.set_option("conv_split", args.conv_split)
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)

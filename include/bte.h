@@ -194,6 +194,12 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *                      resident CTAs per SM of a one-block ring);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
  *                      (TwoSum) merges (>= 1, default 16);
+ *       "conv_split"  variant 4: 1 (default) runs the batch's plan in which
+ *                      the costliest pencil items are cut into two block
+ *                      ranges (chosen when the batch is built, by simulating
+ *                      the work queue on 3 CTAs per SM); the half that
+ *                      finishes second adds both halves' sums in a fixed
+ *                      order (deterministic); 0 runs every pencil whole;
  *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units;
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
  *                      transforms of N <= 16: 1, 2 or 4 (default 4);
@@ -231,15 +237,16 @@ bte_status bte_state_load(bte_ctx *ctx, const char *path, double *f, int64_t n, 
 /* Autotuner of the FP32 path. For the batch described by (inst, ninst) (as in
  * bte_collide) it runs one projected FP32 collide of f per candidate
  * configuration -- convolution variant 1, 2, 3 or 4, 3 or 4 warps per CTA, 1 or 2
- * blocks in flight per warp, compensated merge every 16 or 32 blocks, and for
- * N <= 16 one or four CTAs per cell in the fused transforms -- times reps
+ * blocks in flight per warp, compensated merge every 16 or 32 blocks, for
+ * variant 4 with and without split pencil items, and for N <= 16 one or four
+ * CTAs per cell in the fused transforms -- times reps
  * repetitions with CUDA events on `stream`, and keeps the fastest as this
  * context's configuration for batches of the same shape (the same set of
  * grid sizes and number of 32-cell slots); it takes precedence over the
  * options until any conv_* or dft_split option is set. f (DEVICE, read only) is
  * the input the timing runs on; results go to internal scratch. out_cfg (HOST,
- * 5 ints, optional) receives (conv_impl, conv_warps, conv_stages, conv_merge,
- * dft_split), out_ms (optional) the time of one collide. Synchronous; drops
+ * 6 ints, optional) receives (conv_impl, conv_warps, conv_stages, conv_merge,
+ * dft_split, conv_split), out_ms (optional) the time of one collide. Synchronous; drops
  * captured step graphs. Errors: as bte_collide, BTE_ETIMEOUT / BTE_ENONFINITE
  * from the trial runs. */
 bte_status bte_autotune(bte_ctx *ctx, const double *f, const bte_instance *inst, int64_t ninst, int reps,

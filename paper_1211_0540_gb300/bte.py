@@ -336,12 +336,12 @@ class Context:
         the fastest for batches of this shape. Returns the chosen configuration."""
         _check_f64(f, "f")
         arr, n = self._inst(inst, f)
-        cfg = (ctypes.c_int * 5)()
+        cfg = (ctypes.c_int * 6)()
         ms = ctypes.c_double()
         self._rc(self._lib.bte_autotune(self._h, _ptr(f), arr, n, int(reps), cfg, ctypes.byref(ms),
                                         _stream(stream)), "bte_autotune")
         return dict(conv_impl=cfg[0], conv_warps=cfg[1], conv_stages=cfg[2], conv_merge=cfg[3],
-                    dft_split=cfg[4], ms=ms.value)
+                    dft_split=cfg[4], conv_split=cfg[5], ms=ms.value)
 
     def tune_save(self, path):
         self._rc(self._lib.bte_tune_save(self._h, str(path).encode()), "bte_tune_save")

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <queue>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -36,6 +37,14 @@ struct Batch {
     int64_t *d_slot_out = nullptr;
     ConvItem *d_items = nullptr;
     int nitems = 0;
+    // the same work with the costliest items split into two block ranges
+    // (convolution variant 4): items, split codes, partial sums, counters
+    // ([0] the queue, [1 + sid] the halves of split sid that finished)
+    ConvItem *d_items_split = nullptr;
+    int nitems_split = 0, nsplit = 0;
+    int *d_split = nullptr;
+    float *d_part = nullptr;
+    unsigned *d_counters = nullptr;
     unsigned kinds_mask = 0;
     bool uniform = false;
     int uniform_table = 0;
@@ -162,6 +171,115 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull) {
 
 int64_t cell_M(const Table *t) { return (int64_t)t->N * t->N * t->N; }
 
+void free_batch(Batch *B) {
+    cudaFree(B->d_slot_off);
+    cudaFree(B->d_slot_out);
+    cudaFree(B->d_items);
+    cudaFree(B->d_items_split);
+    cudaFree(B->d_split);
+    cudaFree(B->d_part);
+    cudaFree(B->d_counters);
+    delete B;
+}
+
+// Makespan of the atomic queue as list scheduling: items in queue order, each
+// taken by the first of W equal workers to become free (LPT when the costs
+// are sorted in decreasing order).
+double lpt_makespan(const std::vector<double> &cost, int W) {
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int w = 0; w < W; ++w) free_at.push(0.0);
+    double end = 0.0;
+    for (double x : cost) {
+        const double t = free_at.top() + x;
+        free_at.pop();
+        free_at.push(t);
+        end = std::max(end, t);
+    }
+    return end;
+}
+
+// Split plan of the convolution's queue for variant 4 (3 CTAs of 4 warps per
+// SM): the costliest items are cut into two block ranges. Item cost in block
+// times of one CTA: ceil(blocks / 4) plus one for the item's first copies and
+// its reduction. Splits go level by level (all unsplit pieces of the current
+// largest cost at once, at least 8 blocks a half) down to the smallest
+// splittable cost; the level with the shortest simulated makespan is kept
+// (single levels often leave it unchanged, so there is no early stop).
+// out: the items in queue order; code[i] = -1 or 2 sid + half.
+void plan_splits(const bte_ctx *c, const std::vector<ConvItem> &items, std::vector<ConvItem> &out,
+                 std::vector<int> &code) {
+    struct Piece {
+        ConvItem it;
+        int code;
+    };
+    const int W = 3 * c->num_sms;
+    auto cost_of = [](const ConvItem &it) { return (double)((it.nblocks + 3) / 4) + 1.0; };
+    auto order = [&](std::vector<Piece> &v) {
+        std::stable_sort(v.begin(), v.end(),
+                         [&](const Piece &a, const Piece &b) { return cost_of(a.it) > cost_of(b.it); });
+    };
+    auto makespan = [&](const std::vector<Piece> &v) {
+        std::vector<double> cs(v.size());
+        for (size_t i = 0; i < v.size(); ++i) cs[i] = cost_of(v[i].it);
+        return lpt_makespan(cs, W);
+    };
+    std::vector<Piece> cur(items.size());
+    for (size_t i = 0; i < items.size(); ++i) cur[i] = Piece{items[i], -1};
+    out.clear();
+    code.clear();
+    if (items.empty() || items.size() > 65536) {  // large batches have no tail to cut
+        return;
+    }
+    double best = makespan(cur);
+    std::vector<Piece> best_state;  // empty: no split
+    int nsplit = 0, best_nsplit = 0;
+    for (int level = 0; level < 64; ++level) {
+        // the largest cost among unsplit pieces that can be cut
+        double top = -1.0;
+        for (const Piece &p : cur)
+            if (p.code < 0 && p.it.nblocks >= 16) top = std::max(top, cost_of(p.it));
+        if (top < 0.0) break;
+        std::vector<Piece> trial;
+        trial.reserve(cur.size() * 2);
+        int ns = nsplit;
+        for (const Piece &p : cur) {
+            if (p.code < 0 && p.it.nblocks >= 16 && cost_of(p.it) == top) {
+                const Table *t = c->tables[p.it.table];
+                const int tile = p.it.kind - t->kind0;
+                const uint32_t b0 = p.it.nblocks / 2;
+                Piece a = p, b = p;
+                a.it.nblocks = b0;
+                a.code = 2 * ns;
+                b.it.desc_off = p.it.desc_off + b0;
+                b.it.wofs = p.it.wofs + (uint64_t)b0 * t->cpad[tile];
+                b.it.nblocks = p.it.nblocks - b0;
+                b.code = 2 * ns + 1;
+                ++ns;
+                trial.push_back(a);
+                trial.push_back(b);
+            } else {
+                trial.push_back(p);
+            }
+        }
+        order(trial);
+        const double m = makespan(trial);
+        cur.swap(trial);
+        nsplit = ns;
+        if (m < best * 0.999) {
+            best = m;
+            best_state = cur;
+            best_nsplit = nsplit;
+        }
+    }
+    if (best_nsplit == 0) return;
+    out.resize(best_state.size());
+    code.resize(best_state.size());
+    for (size_t i = 0; i < best_state.size(); ++i) {
+        out[i] = best_state[i].it;
+        code[i] = best_state[i].code;
+    }
+}
+
 // Build (or fetch) the batch for an instance layout.
 bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch **out) {
     if (c->tables.empty()) return fail(c, BTE_ESTATE, "no weight tables: call bte_init_weights first");
@@ -266,14 +384,23 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
     std::vector<ConvItem> sorted(items.size());
     for (size_t i = 0; i < items.size(); ++i) sorted[i] = items[order[i]];
     B->nitems = (int)sorted.size();
+    std::vector<ConvItem> split_items;
+    std::vector<int> split_code;
+    plan_splits(c, sorted, split_items, split_code);
+    B->nitems_split = (int)split_items.size();
+    B->nsplit = 0;
+    for (int v : split_code) B->nsplit = std::max(B->nsplit, v / 2 + 1);
     cudaError_t e = cudaMalloc(&B->d_slot_off, sizeof(int64_t) * slot_off.size());
     if (e == cudaSuccess) e = cudaMalloc(&B->d_slot_out, sizeof(int64_t) * slot_out.size());
     if (e == cudaSuccess) e = cudaMalloc(&B->d_items, sizeof(ConvItem) * std::max<size_t>(sorted.size(), 1));
+    if (e == cudaSuccess && B->nsplit > 0) {
+        e = cudaMalloc(&B->d_items_split, sizeof(ConvItem) * split_items.size());
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_split, sizeof(int) * split_code.size());
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_part, sizeof(float) * kSplitFloats * 2 * (size_t)B->nsplit);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counters, sizeof(unsigned) * (1 + (size_t)B->nsplit));
     if (e != cudaSuccess) {
-        cudaFree(B->d_slot_off);
-        cudaFree(B->d_slot_out);
-        cudaFree(B->d_items);
-        delete B;
+        free_batch(B);
         return fail(c, BTE_ENOMEM, std::string("batch allocation: ") + cudaGetErrorString(e));
     }
     e = cudaMemcpy(B->d_slot_off, slot_off.data(), sizeof(int64_t) * slot_off.size(), cudaMemcpyHostToDevice);
@@ -281,8 +408,14 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
         e = cudaMemcpy(B->d_slot_out, slot_out.data(), sizeof(int64_t) * slot_out.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !sorted.empty())
         e = cudaMemcpy(B->d_items, sorted.data(), sizeof(ConvItem) * sorted.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && B->nsplit > 0) {
+        e = cudaMemcpy(B->d_items_split, split_items.data(), sizeof(ConvItem) * split_items.size(),
+                       cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_split, split_code.data(), sizeof(int) * split_code.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
-        delete B;
+        free_batch(B);
         return cuda_fail(c, e, "batch upload");
     }
     c->batches[key] = B;
@@ -304,6 +437,7 @@ ConvCfg cfg_of(const bte_ctx *c, const Batch *B) {
     g.warps = c->conv_warps;
     g.stages = c->conv_stages;
     g.merge = c->conv_merge;
+    g.csplit = c->conv_split;
     g.split = c->dft_split;
     return g;
 }
@@ -400,9 +534,15 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, cfg.warps, cfg.stages, cfg.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
         ConvParams p{};
-        p.items = B->d_items;
-        p.nitems = B->nitems;
-        p.counter = c->d_counter;
+        const bool split = cfg.impl == 4 && cfg.csplit && B->nsplit > 0;
+        p.items = split ? B->d_items_split : B->d_items;
+        p.nitems = split ? B->nitems_split : B->nitems;
+        p.counter = B->d_counters;
+        if (split) {
+            p.split = B->d_split;
+            p.part = B->d_part;
+            p.split_cnt = B->d_counters + 1;
+        }
         p.F = (const float2 *)c->scratch[SC_F];
         p.Qh = (float2 *)c->scratch[SC_QH];
         for (size_t i = 0; i < c->tables.size() && i < (size_t)kMaxTables; ++i) {
@@ -412,7 +552,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         p.status = c->d_status;
         p.merge = cfg.merge;
         p.stall = c->debug_conv_stall;
-        e = cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned), st);
+        e = cudaMemsetAsync(B->d_counters, 0, sizeof(unsigned) * (1 + (split ? (size_t)B->nsplit : 0)), st);
         if (e != cudaSuccess) return cuda_fail(c, e, "queue reset");
         const int on = prof_begin(c, PK_CONV32, st, &pe_conv);
         e = cudaGetLastError();
@@ -624,10 +764,7 @@ void bte_destroy(bte_ctx *c) {
         cudaEventDestroy(ab.second);
     }
     for (auto &kv : c->batches) {
-        cudaFree(kv.second->d_slot_off);
-        cudaFree(kv.second->d_slot_out);
-        cudaFree(kv.second->d_items);
-        delete kv.second;
+        free_batch(kv.second);
     }
     for (Table *t : c->tables) {
         free_table(*t);
@@ -892,6 +1029,7 @@ static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
     if (!std::strcmp(name, "conv_stages")) { *lo = 0; *hi = 4; return &c->conv_stages; }
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
+    if (!std::strcmp(name, "conv_split")) { *lo = 0; *hi = 1; return &c->conv_split; }
     if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
     return nullptr;
 }
@@ -977,14 +1115,17 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
         for (int warps : {4, 3})
             for (int stages : {1, 2})
                 for (int merge : {16, 32})
-                    for (int split : {4, 1}) {
+                    for (int split : {4, 1})
+                        for (int csplit : {1, 0}) {
                         if (!small_n && split != 4) continue;
+                        if (csplit && (impl != 4 || B->nsplit == 0)) continue;
                         ConvCfg g;
                         g.impl = impl;
                         g.warps = warps;
                         g.stages = stages;
                         g.merge = merge;
                         g.split = split;
+                        g.csplit = csplit;
                         c->tuned[key] = g;
                         if ((err = prepare(c, B, BTE_FP32, false, false)) != BTE_OK) break;
                         if ((err = enqueue_collide(c, B, f, Qtmp, BTE_FP32, POST_PROJECT, nullptr, nullptr, nullptr,
@@ -1023,6 +1164,7 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
         out_cfg[2] = best.stages;
         out_cfg[3] = best.merge;
         out_cfg[4] = best.split;
+        out_cfg[5] = best.csplit;
     }
     if (out_ms) *out_ms = best.ms;
     return BTE_OK;
@@ -1121,8 +1263,8 @@ bte_status bte_tune_save(const bte_ctx *c, const char *path) {
     for (const auto &kv : c->tuned) {
         const ConvCfg &g = kv.second;
         std::fprintf(fp, "{\"key\": \"%s\", \"impl\": %d, \"warps\": %d, \"stages\": %d, \"merge\": %d, "
-                         "\"split\": %d, \"ms\": %.6f}%s\n",
-                     kv.first.c_str(), g.impl, g.warps, g.stages, g.merge, g.split, g.ms,
+                         "\"split\": %d, \"csplit\": %d, \"ms\": %.6f}%s\n",
+                     kv.first.c_str(), g.impl, g.warps, g.stages, g.merge, g.split, g.csplit, g.ms,
                      ++i < c->tuned.size() ? "," : "");
     }
     std::fprintf(fp, "]\n}\n");
@@ -1156,10 +1298,11 @@ bte_status bte_tune_load(bte_ctx *c, const char *path, int *loaded) {
         ConvCfg g;
         if (std::sscanf(line.c_str(),
                         "{\"key\": \"%127[^\"]\", \"impl\": %d, \"warps\": %d, \"stages\": %d, \"merge\": %d, "
-                        "\"split\": %d, \"ms\": %lf}",
-                        key, &g.impl, &g.warps, &g.stages, &g.merge, &g.split, &g.ms) != 7)
+                        "\"split\": %d, \"csplit\": %d, \"ms\": %lf}",
+                        key, &g.impl, &g.warps, &g.stages, &g.merge, &g.split, &g.csplit, &g.ms) != 8)
             return fail(c, BTE_EINVAL, "bte_tune_load: malformed entry: " + line);
         if (g.impl < 0 || g.impl > 4 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
+            g.csplit < 0 || g.csplit > 1 ||
             (g.split != 1 && g.split != 2 && g.split != 4))
             return fail(c, BTE_EINVAL, "bte_tune_load: out-of-range entry: " + line);
         got[key] = g;

@@ -90,6 +90,7 @@ struct GraphKey {
 // compensated-merge interval, CTAs per cell of the fused transforms).
 struct ConvCfg {
     int impl = 4, warps = 4, stages = 0, merge = 16, split = 4;
+    int csplit = 1;   // variant 4: run the batch's split item list (the costliest pencils in two halves)
     double ms = 0.0;  // measured time of one collide of the batch when tuned
 };
 
@@ -144,6 +145,7 @@ struct bte_ctx {
     int conv_impl = 4;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2,
                                // 3 as 2 at 2 CTAs/SM, 4 as 2 with the compensated sums in shared memory
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
+    int conv_split = 1;        // variant 4: split the costliest pencil items in two
     int debug_conv_stall = 0;  // testing only: make the convolution's waits run out
     std::string gpu_name;      // device name (key of saved tuning caches)
     std::map<std::string, bte::ConvCfg> tuned;  // autotuned configuration per batch shape

@@ -546,17 +546,64 @@ __device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &
     return ok;
 }
 
+// Half `sp & 1` of split item sp >> 1: the warps' sums reduced in the fixed
+// warp order into part[], then the CTA that finishes second (an atomic count,
+// no waiting) adds half 0 and half 1 in that order and stores Q.
+template <class K>
+__device__ __forceinline__ void coop_reduce_split(const ConvItem &it, const ConvParams &p, int lane, int warp,
+                                                  int nwarps, const char *ring0, int warp_smem, int sums_off,
+                                                  int sp, int *s_last) {
+    constexpr int T = K::T;
+    const int sid = sp >> 1, half = sp & 1;
+    float *mine = p.part + ((size_t)sid * 2 + half) * kSplitFloats;
+    for (int t = warp; t < T; t += nwarps) {
+        float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+        for (int w = 0; w < nwarps; ++w) {
+            const float *red = reinterpret_cast<const float *>(ring0 + (size_t)w * warp_smem + sums_off);
+            two_sum(sr, lr, red[(2 * t) * kLanes + lane]);
+            lr += red[(2 * T + 2 * t) * kLanes + lane];
+            two_sum(si, li, red[(2 * t + 1) * kLanes + lane]);
+            li += red[(2 * T + 2 * t + 1) * kLanes + lane];
+        }
+        float *o = mine + (size_t)t * 4 * kLanes + lane;
+        o[0] = sr;
+        o[kLanes] = lr;
+        o[2 * kLanes] = si;
+        o[3 * kLanes] = li;
+    }
+    __threadfence();  // this half's sums before the count
+    __syncthreads();
+    if (threadIdx.x == 0) *s_last = atomicAdd(p.split_cnt + sid, 1u) == 1u;
+    __syncthreads();
+    if (!*s_last) return;
+    __threadfence();  // the other half's sums after the count
+    const float *h0 = p.part + (size_t)sid * 2 * kSplitFloats, *h1 = h0 + kSplitFloats;
+    float2 *Q = p.Qh + it.fofs + ((size_t)(it.k1 * K::N + it.k2) * K::N + K::K0) * kLanes + lane;
+    for (int t = warp; t < T; t += nwarps) {
+        const float *a = h0 + (size_t)t * 4 * kLanes + lane, *b = h1 + (size_t)t * 4 * kLanes + lane;
+        float sr = __ldcg(a), lr = __ldcg(a + kLanes), si = __ldcg(a + 2 * kLanes), li = __ldcg(a + 3 * kLanes);
+        two_sum(sr, lr, __ldcg(b));
+        lr += __ldcg(b + kLanes);
+        two_sum(si, li, __ldcg(b + 2 * kLanes));
+        li += __ldcg(b + 3 * kLanes);
+        Q[t * kLanes] = make_float2(sr + lr, si + li);
+    }
+}
+
 template <class K>
 __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
                                             int warp, int nwarps, char *ring0, int *abort_flag, float *sums,
-                                            int sums_off) {
+                                            int sums_off, int sp, int *s_last) {
     const bool ok = coop_item_sm<K>(r, it, p, lane, warp, nwarps, sums);
     if (!ok && lane == 0) {
         atomicOr(p.status, ST_TIMEOUT);
         *abort_flag = 1;
     }
     __syncthreads();
-    if (!*abort_flag) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off);
+    if (!*abort_flag) {
+        if (sp < 0) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off);
+        else coop_reduce_split<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off, sp, s_last);
+    }
     __syncthreads();
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     return !*abort_flag;
@@ -565,7 +612,7 @@ __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, con
 template <unsigned MASK>
 __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
     extern __shared__ __align__(128) char smem[];
-    __shared__ int s_item, s_abort;
+    __shared__ int s_item, s_abort, s_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int ring = p.warp_smem - kSumsBytes;
@@ -587,15 +634,16 @@ __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
         const int idx = s_item;
         if (idx >= p.nitems || s_abort) break;
         const ConvItem it = p.items[idx];
+        const int sp = p.split ? p.split[idx] : -1;
         bool ok = true;
         switch (it.kind) {
-            case 0: if (MASK & 1u) ok = coop_run_sm<K8>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 1: if (MASK & 2u) ok = coop_run_sm<K12>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 2: if (MASK & 4u) ok = coop_run_sm<K16>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 3: if (MASK & 8u) ok = coop_run_sm<K24a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 4: if (MASK & 16u) ok = coop_run_sm<K24b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 5: if (MASK & 32u) ok = coop_run_sm<K32a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
-            case 6: if (MASK & 64u) ok = coop_run_sm<K32b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring); break;
+            case 0: if (MASK & 1u) ok = coop_run_sm<K8>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 1: if (MASK & 2u) ok = coop_run_sm<K12>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 2: if (MASK & 4u) ok = coop_run_sm<K16>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 3: if (MASK & 8u) ok = coop_run_sm<K24a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 4: if (MASK & 16u) ok = coop_run_sm<K24b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 5: if (MASK & 32u) ok = coop_run_sm<K32a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
+            case 6: if (MASK & 64u) ok = coop_run_sm<K32b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
             default: break;
         }
         if (!ok) break;

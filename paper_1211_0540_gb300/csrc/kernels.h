@@ -44,7 +44,16 @@ struct ConvParams {
     int merge;      // blocks per TwoSum merge
     int warp_smem;  // bytes of ring per warp
     int stall;      // testing the timeout path: each warp never issues its first block
+    // Items split into two block ranges (conv_impl 4 only; null: no splits).
+    // split[i] = -1, or 2 sid + half: the two halves write their reduced sums to
+    // part[(2 sid + half) * kSplitFloats ...]; the CTA that finishes second
+    // (split_cnt[sid], zeroed before the launch) adds half 0 and half 1 in that
+    // order and writes Q.
+    const int *split;
+    float *part;
+    unsigned *split_cnt;
 };
+constexpr int kSplitFloats = 16 * 4 * 32;  // per half: T <= 16 outputs x (hi, lo) x (re, im) x 32 lanes
 int conv_stage_bytes(int kind);
 struct ConvLaunch {
     void (*fn)(ConvParams);

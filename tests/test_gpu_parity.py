@@ -88,6 +88,32 @@ def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
     assert np.all(np.abs(mom) <= 1e-12 * abs_moment_scale(N, Qg))
 
 
+@pytest.mark.parametrize("N,ncells,lam", [(8, 1, 1.0), (16, 33, 1.0), (24, 40, 0.0)])
+def test_fp32_split_items_match_oracle_and_repeat_bitwise(bte, N, ncells, lam):
+    """Variant 4 with the costliest pencil items cut into two block ranges (the
+    half that finishes second adds both in a fixed order) and without: both
+    within the FP32 bar of the oracle, the split run bit-identical on repeat."""
+    f = inputs.homogeneous_cells(N, L, ncells, seed=400 + N + ncells)
+    c = ctx_for(bte, ((N, L, lam),))
+    saved = {k: c.get_option(k) for k in ("conv_impl", "conv_split")}
+    c.set_option("conv_impl", 4)
+    out = {}
+    try:
+        for split in (1, 0):
+            c.set_option("conv_split", split)
+            out[split] = run_collide(bte, N, lam, f, bte.FP32)
+        c.set_option("conv_split", 1)
+        again = run_collide(bte, N, lam, f, bte.FP32)
+    finally:
+        for k, v in saved.items():
+            c.set_option(k, v)
+    Qo = oracle.collide(N, L, lam, f)
+    for split, Qg in out.items():
+        err = np.linalg.norm(Qg - Qo, axis=1) / loss_norm(N, lam, f)
+        assert err.max() <= TOL32, (split, err.max())
+    assert np.array_equal(out[1], again)
+
+
 @pytest.mark.parametrize("N,ncells,lam", [(8, 3, 1.0), (12, 33, 0.0)])
 def test_fp64_plain_collide_matches_oracle(bte, N, ncells, lam):
     f = inputs.homogeneous_cells(N, L, ncells, seed=200 + N)
@@ -389,6 +415,7 @@ def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
     cfg = c.autotune(ft, reps=2)
     assert cfg["conv_impl"] in (1, 2, 3, 4) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
     assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 4) and cfg["ms"] > 0.0
+    assert cfg["conv_split"] in (0, 1) and (cfg["conv_split"] == 0 or cfg["conv_impl"] == 4)
     Q = c.collide(ft)
     c.sync_status()
     Qo = oracle.collide(N, L, lam, f)
