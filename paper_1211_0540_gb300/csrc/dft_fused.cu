@@ -26,6 +26,7 @@
 #include <map>
 
 #include "fft_reg.cuh"
+#include "fpconv.cuh"
 #include "project.cuh"
 
 namespace cg = cooperative_groups;
@@ -132,8 +133,8 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const double d = fp[j];
-            bad |= !isfinite(d);
-            x[j] = (float)d;
+            bad |= !fpc::finite64(d);
+            x[j] = fpc::narrow(d);  // integer pipes: a conversion instruction would issue on the FP64 unit
         }
         float2 y[N];
         pencil_rc<N>(x, y, rt);
@@ -193,8 +194,8 @@ dft_fwd_pencils_kernel(const double *__restrict__ f, const int64_t *__restrict__
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             const double d = fp[j];
-            bad |= !isfinite(d);
-            x[j] = (float)d;
+            bad |= !fpc::finite64(d);
+            x[j] = fpc::narrow(d);  // integer pipes: a conversion instruction would issue on the FP64 unit
         }
         float2 y[N];
         pencil_rc<N>(x, y, rt);
@@ -391,7 +392,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
     // coalesced output of the own slab: local value e = (pencil p, j3)
     double *qo = q + off + (int64_t)r * MS;
     if (mode == 0) {
-        for (int e = t; e < MS; e += S::NT) qo[e] = (double)R[(e / N) * P + e % N];
+        for (int e = t; e < MS; e += S::NT) qo[e] = fpc::widen(R[(e / N) * P + e % N]);
         return;
     }
     if constexpr (PF) {
@@ -400,7 +401,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
             const int e = t + i * S::NT;
             if (e < MS) {
                 const int p = e / N, j3 = e % N;
-                const double v = (double)R[p * P + j3] - (base[p] + sg[j3]);
+                const double v = fpc::widen(R[p * P + j3]) - (base[p] + sg[j3]);
                 qo[e] = v;
                 if (mode == 2) yo[e] = fma(a, v, u[i]);
                 else if (mode == 3) yo[e] = fma(a, w[i] + v, u[i]);
@@ -410,7 +411,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
 #pragma unroll 4
         for (int e = t; e < MS; e += S::NT) {
             const int p = e / N, j3 = e % N;
-            const double v = (double)R[p * P + j3] - (base[p] + sg[j3]);
+            const double v = fpc::widen(R[p * P + j3]) - (base[p] + sg[j3]);
             qo[e] = v;
             if (mode == 2) yo[e] = fma(a, v, xo[e]);
             else if (mode == 3) yo[e] = fma(a, qpo[e] + v, yo[e]);

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "learned.h"
+#include "fpconv.cuh"
 #include "project.cuh"
 
 namespace bte {
@@ -202,7 +203,7 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
         base[t] = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
     }
     __syncthreads();
-    for (int e = t; e < M; e += NT) q[e] = fma(c, (double)y[e], -(base[e / N] + sg[e % N]));
+    for (int e = t; e < M; e += NT) q[e] = fma(c, fpc::widen(y[e]), -(base[e / N] + sg[e % N]));
 }
 
 }  // namespace

@@ -21,6 +21,7 @@
 
 #include "gemm_tc.h"
 #include "mlp.h"
+#include "fpconv.cuh"
 #include "project.cuh"
 
 namespace bte {
@@ -52,7 +53,7 @@ __global__ void __launch_bounds__(kT) prep_kernel(const double *__restrict__ f, 
     __shared__ double rho_s;
     Df s{0.f, 0.f};
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const float v = (float)fr[j];
+        const float v = fpc::narrow(fr[j]);  // integer pipes, not the FP64 unit
         xs[j] = v;
         df_add(s, v);
     }
