@@ -101,6 +101,43 @@ __device__ __forceinline__ void cluster_barrier_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
+// Barrier over the CTAs of a cell: a block barrier when the cell is one CTA
+// (a cluster barrier would add a memory fence for nothing).
+template <int C>
+__device__ __forceinline__ void cell_sync(cg::cluster_group &cl) {
+    if constexpr (C == 1) __syncthreads();
+    else cl.sync();
+}
+template <int C, class T>
+__device__ __forceinline__ T *cell_smem(cg::cluster_group &cl, T *p, int rank) {
+    if constexpr (C == 1) return p;
+    else return cl.map_shared_rank(p, rank);
+}
+
+// The N consecutive FP64 values of a pencil, narrowed to FP32 (integer pipes),
+// with 16-byte loads when the pencil is 16-byte aligned; `bad` collects
+// non-finite inputs.
+template <int N>
+__device__ __forceinline__ void load_pencil_f64(const double *__restrict__ fp, float (&x)[N], bool &bad) {
+    if ((reinterpret_cast<uintptr_t>(fp) & 15u) == 0) {
+        const double2 *f2 = reinterpret_cast<const double2 *>(fp);
+#pragma unroll
+        for (int j = 0; j < N / 2; ++j) {
+            const double2 d = f2[j];
+            bad |= !fpc::finite64(d.x) || !fpc::finite64(d.y);
+            x[2 * j] = fpc::narrow(d.x);
+            x[2 * j + 1] = fpc::narrow(d.y);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const double d = fp[j];
+            bad |= !fpc::finite64(d);
+            x[j] = fpc::narrow(d);
+        }
+    }
+}
+
 }  // namespace
 
 // Cell = cluster of C CTAs; CTA r owns the slab j1 in [r JR, (r+1) JR) of the
@@ -129,13 +166,7 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
     if (act) {  // along j3, pencil (j1, j2), real input
         const int jl = t / N, j2 = t % N;
         float x[N];
-        const double *fp = f + off + (int64_t)((r * JR + jl) * N + j2) * N;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const double d = fp[j];
-            bad |= !fpc::finite64(d);
-            x[j] = fpc::narrow(d);  // integer pipes: a conversion instruction would issue on the FP64 unit
-        }
+        load_pencil_f64<N>(f + off + (int64_t)((r * JR + jl) * N + j2) * N, x, bad);
         float2 y[N];
         pencil_rc<N>(x, y, rt);
 #pragma unroll
@@ -152,12 +183,12 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
 #pragma unroll
         for (int k = 0; k < N; ++k) B[(jl * N + k) * N + k3] = y[k];
     }
-    cl.sync();
+    cell_sync<C>(cl);
     if (act) {  // along j1, pencil (k2, k3), rows from every CTA of the cluster, into the group layout
         const int k2 = r * JR + t / N, k3 = t % N;
         const float2 *src[C];
 #pragma unroll
-        for (int o = 0; o < C; ++o) src[o] = cl.map_shared_rank(B, o);
+        for (int o = 0; o < C; ++o) src[o] = cell_smem<C>(cl, B, o);
         float2 x[N], y[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) x[j] = src[j / JR][((j % JR) * N + k2) * N + k3];
@@ -166,7 +197,7 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
 #pragma unroll
         for (int k = 0; k < N; ++k) g[(int64_t)(k * NN + pk) * kLanes] = make_float2(scale * y[k].x, scale * y[k].y);
     }
-    cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
+    if constexpr (C > 1) cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
 }
 
 // Forward transform of a cell at the modes of a few zeta pencils only (the
@@ -190,13 +221,7 @@ dft_fwd_pencils_kernel(const double *__restrict__ f, const int64_t *__restrict__
     bool bad = false;
     if (t < NN) {  // along j3, pencil (j1, j2) = t, real input
         float x[N];
-        const double *fp = f + off + (int64_t)t * N;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const double d = fp[j];
-            bad |= !fpc::finite64(d);
-            x[j] = fpc::narrow(d);  // integer pipes: a conversion instruction would issue on the FP64 unit
-        }
+        load_pencil_f64<N>(f + off + (int64_t)t * N, x, bad);
         float2 y[N];
         pencil_rc<N>(x, y, rt);
 #pragma unroll
@@ -284,12 +309,12 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
 #pragma unroll
         for (int j = 0; j < N; ++j) A[(kl * N + j) * N + k3] = yy[j];
     }
-    cl.sync();
+    cell_sync<C>(cl);
     if (act) {  // along k2, pencil (j1, k3), rows from every CTA of the cluster
         const int j1 = r * JR + t / N, k3 = t % N;
         const float2 *src[C];
 #pragma unroll
-        for (int o = 0; o < C; ++o) src[o] = cl.map_shared_rank(A, o);
+        for (int o = 0; o < C; ++o) src[o] = cell_smem<C>(cl, A, o);
         float2 xx[N], yy[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) xx[k] = src[k / JR][((k % JR) * N + j1) * N + k3];
@@ -298,7 +323,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
 #pragma unroll
         for (int j = 0; j < N; ++j) B[(jl * N + j) * P + k3] = yy[j];
     }
-    cl.sync();  // all remote reads of A are done (no CTA may leave earlier)
+    cell_sync<C>(cl);  // all remote reads of A are done (no CTA may leave earlier)
     // along k3, real part, pencil (j1, j2); per-pencil moment sums in double-float
     Df mom[5];
     if (act) {
@@ -352,14 +377,14 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
                 part[2 * i] = mom[i].hi;
                 part[2 * i + 1] = mom[i].lo;
             }
-        cl.sync();
+        cell_sync<C>(cl);
         if (warp == 0) {
             double mu = 0.0;
             if (lane < 5) {
                 Df m{0.f, 0.f};
 #pragma unroll
                 for (int o = 0; o < C; ++o) {
-                    const float *po = cl.map_shared_rank(part, o);
+                    const float *po = cell_smem<C>(cl, part, o);
                     m = df_add(m, Df{po[2 * lane], po[2 * lane + 1]});
                 }
                 // mu = (sum q, dv sum w_d q (d = 1..3), dv^2 sum |w|^2 q), w = j - N/2
@@ -376,7 +401,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
                 lam[lane] = l;
             }
         }
-        cl.sync();  // every CTA has read the partials before any leaves; lambda is visible
+        cell_sync<C>(cl);  // every CTA has read the partials before any leaves; lambda is visible
         // correction C^T lambda = base(j1, j2) + g(j3)
         const double dv = pa.dv;
         if (t < N) {
