@@ -25,7 +25,7 @@ namespace bte {
 
 namespace {
 constexpr int kTThreads = 128;  // consecutive velocities of one cell chunk
-constexpr int kTChunk = 8;      // cells per thread (sliding stencil window)
+constexpr int kTChunk = 4;      // cells per thread: 1024 CTAs at 128 cells x N = 16 (6.7 per SM)
 
 // minmod(a, b) = 0 if a b <= 0, else the argument of smaller magnitude.
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -104,10 +104,14 @@ __global__ void __launch_bounds__(kTThreads) transport_stage_kernel(const double
                                                                      const __grid_constant__ TransportArgs a) {
     const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
     const int c0 = blockIdx.y * kTChunk, c1 = min(c0 + kTChunk, a.nx);
-    // walls: only the chunks whose stencil reaches a diffuse ghost need sigma_w
+    // walls: sigma_w only where a diffuse ghost is read for an incoming
+    // velocity (i > N/2 at the left wall, i < N/2 at the right), i.e. the
+    // chunks next to a wall and CTAs whose velocity range has such an i
+    const int ilo = (int)(blockIdx.x * blockDim.x) / NN;
+    const int ihi = min((int)((blockIdx.x + 1) * blockDim.x) - 1, M - 1) / NN;
     double sig_l = 0.0, sig_r = 0.0;
-    if (c0 < 2 && a.bc_left == BTE_BC_DIFFUSE) sig_l = wall_sigma(src, a, 0);
-    if (c1 > a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE) sig_r = wall_sigma(src, a, 1);
+    if (c0 < 2 && a.bc_left == BTE_BC_DIFFUSE && ihi > h) sig_l = wall_sigma(src, a, 0);
+    if (c1 > a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE && ilo < h) sig_r = wall_sigma(src, a, 1);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     const int i = j / NN;
