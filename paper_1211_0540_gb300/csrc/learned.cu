@@ -130,7 +130,7 @@ __global__ void indicator_reduce_kernel(const float *__restrict__ err2, const fl
 // cell, one thread per pencil (j1, j2): the moments of Y are accumulated in
 // double-float FP32 (the values are FP32), mu(Q) = c mu(Y) and lambda are
 // formed in FP64, and Q_j = c Y_j - C_j^T lambda is written in FP64 on a
-// coalesced mapping (about four FP64 operations per value).
+// coalesced mapping (one FP64 operation per value).
 template <int N>
 __global__ void __launch_bounds__((N * N + 31) / 32 * 32)
 post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho, float s_out, ProjArgs pa,
@@ -140,7 +140,8 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
     const float *y = Y + (size_t)r * M;
     double *q = Q + (size_t)r * M;
     __shared__ float red[NW][10];
-    __shared__ double base[NN], sg[N], lam[5];
+    __shared__ float2 base[NN], sg[N];
+    __shared__ double lam[5];
     const double c = rho[r] * rho[r] / (double)s_out;
     Df mom[5];
     if (t < NN) {
@@ -193,17 +194,35 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
         }
     }
     __syncthreads();
+    // The correction C^T lambda = base(j1, j2) + g(j3) is formed in FP64 per
+    // pencil and per j3, then kept as double-float pairs (hi, lo): per value
+    // Q = c Y - base - g is then FP32 work (an exact TwoProduct for c Y and
+    // two double-float additions, relative error ~2^-48) and one FP64
+    // addition hi + lo, instead of three FP64-unit operations.
     const double dv = pa.dv;
     if (t < N) {
         const double v = dv * (double)(t - H);
-        sg[t] = fma(lam[3], v, lam[4] * v * v);
+        const double g = fma(lam[3], v, lam[4] * v * v);
+        const float hi = fpc::narrow(g);
+        sg[t] = make_float2(hi, fpc::narrow(g - fpc::widen(hi)));
     }
     if (t < NN) {
         const double v1 = dv * (double)(t / N - H), v2 = dv * (double)(t % N - H);
-        base[t] = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
+        const double b = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
+        const float hi = fpc::narrow(b);
+        base[t] = make_float2(hi, fpc::narrow(b - fpc::widen(hi)));
     }
+    const float c_hi = fpc::narrow(c), c_lo = fpc::narrow(c - fpc::widen(c_hi));
     __syncthreads();
-    for (int e = t; e < M; e += NT) q[e] = fma(c, fpc::widen(y[e]), -(base[e / N] + sg[e % N]));
+    for (int e = t; e < M; e += NT) {
+        const float yv = y[e];
+        const float p = c_hi * yv;
+        Df prod{p, fmaf(c_lo, yv, fmaf(c_hi, yv, -p))};
+        const float2 b = base[e / N], g = sg[e % N];
+        const Df corr = df_add(Df{b.x, b.y}, Df{g.x, g.y});
+        const Df v = df_add(prod, Df{-corr.hi, -corr.lo});
+        q[e] = fpc::widen(v.hi) + fpc::widen(v.lo);
+    }
 }
 
 }  // namespace

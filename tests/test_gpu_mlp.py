@@ -118,7 +118,8 @@ def test_learned_mode_projection_and_fallback():
     c.project(raw)
     c.sync_status()
     assert st["fallbacks"] == 0 and st["max_indicator"] > 0.0
-    assert torch.allclose(q1, raw, rtol=0, atol=1e-15)
+    # the fused epilogue evaluates Q = c Y - C^T lambda in double-float FP32 (48-bit significands)
+    assert (q1 - raw).abs().max().item() <= 2.0 ** -44 * raw.abs().max().item()
     Q1 = q1.cpu().numpy().reshape(40, -1)
     m = oracle.moments(N, L, Q1)
     v1, v2, v3 = inputs.velocity_nodes(N, L)
