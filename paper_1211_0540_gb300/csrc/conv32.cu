@@ -486,15 +486,17 @@ constexpr int kSumsBytes = 4 * 16 * kLanes * 4;
 
 // One item by all warps of the CTA, sums in shared memory at r.base + ring
 // bytes. Returns false if this warp timed out.
+// pre: the copies of this warp's first block were issued before (during the
+// previous item's reduction).
 template <class K>
 __device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane, int warp,
-                             int nwarps, float *sums) {
+                             int nwarps, float *sums, bool pre) {
     constexpr int T = K::T;
     const int nb = (int)it.nblocks;
     const int S = p.stages;
     const int mine = nb > warp ? (nb - warp + nwarps - 1) / nwarps : 0;
     if (lane == 0)
-        for (int s = 0; s < S && s < mine; ++s)
+        for (int s = pre ? 1 : 0; s < S && s < mine; ++s)
             if (!(p.stall && s == 0)) issue_block<K>(r, s, it, p, warp + s * nwarps);
 #pragma unroll
     for (int q = 0; q < 4 * T; ++q) sums[q * kLanes + lane] = 0.f;
@@ -590,16 +592,46 @@ __device__ __forceinline__ void coop_reduce_split(const ConvItem &it, const Conv
     }
 }
 
-template <class K>
+// Copies of this warp's first block of item it into stage 0 (lane 0 only),
+// for any kind compiled into the kernel.
+template <unsigned MASK>
+__device__ __forceinline__ void issue_first_any(const WarpRing &r, const ConvItem &it, const ConvParams &p,
+                                                int warp) {
+    if ((int)it.nblocks <= warp || p.stall) return;
+    switch (it.kind) {
+        case 0: if (MASK & 1u) issue_block<K8>(r, 0, it, p, warp); break;
+        case 1: if (MASK & 2u) issue_block<K12>(r, 0, it, p, warp); break;
+        case 2: if (MASK & 4u) issue_block<K16>(r, 0, it, p, warp); break;
+        case 3: if (MASK & 8u) issue_block<K24a>(r, 0, it, p, warp); break;
+        case 4: if (MASK & 16u) issue_block<K24b>(r, 0, it, p, warp); break;
+        case 5: if (MASK & 32u) issue_block<K32a>(r, 0, it, p, warp); break;
+        case 6: if (MASK & 64u) issue_block<K32b>(r, 0, it, p, warp); break;
+        default: break;
+    }
+}
+
+// One item, then the next: once every warp has consumed its blocks, the next
+// item is taken from the queue (into *s_next) and each warp issues the copies
+// of its first block into its now idle ring before the CTA reduces this item's
+// sums, which live outside the rings.
+template <class K, unsigned MASK>
 __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
                                             int warp, int nwarps, char *ring0, int *abort_flag, float *sums,
-                                            int sums_off, int sp, int *s_last) {
-    const bool ok = coop_item_sm<K>(r, it, p, lane, warp, nwarps, sums);
+                                            int sums_off, int sp, int *s_last, bool pre, int *s_next) {
+    const bool ok = coop_item_sm<K>(r, it, p, lane, warp, nwarps, sums, pre);
     if (!ok && lane == 0) {
         atomicOr(p.status, ST_TIMEOUT);
         *abort_flag = 1;
     }
     __syncthreads();
+    if (threadIdx.x == 0) *s_next = *abort_flag ? p.nitems : (int)atomicAdd(p.counter, 1u);
+    __syncthreads();
+    const int nx = *s_next;
+    if (nx < p.nitems && lane == 0) {
+        // the ring was last read by generic loads; order them before the copies
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue_first_any<MASK>(r, p.items[nx], p, warp);
+    }
     if (!*abort_flag) {
         if (sp < 0) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off);
         else coop_reduce_split<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off, sp, s_last);
@@ -626,27 +658,40 @@ __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
         for (int s = 0; s < p.stages; ++s) mbar_init(r.bars + 8u * s, 1);
         fence_mbar_init();
     }
-    if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        s_item = (int)atomicAdd(p.counter, 1u);
+    }
     __syncthreads();
+    bool pre = false;  // the first block of item s_item is already in flight
     for (;;) {
-        if (threadIdx.x == 0) s_item = (int)atomicAdd(p.counter, 1u);
-        __syncthreads();
         const int idx = s_item;
         if (idx >= p.nitems || s_abort) break;
         const ConvItem it = p.items[idx];
         const int sp = p.split ? p.split[idx] : -1;
-        bool ok = true;
+        bool ok = true, ran = true;
         switch (it.kind) {
-            case 0: if (MASK & 1u) ok = coop_run_sm<K8>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 1: if (MASK & 2u) ok = coop_run_sm<K12>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 2: if (MASK & 4u) ok = coop_run_sm<K16>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 3: if (MASK & 8u) ok = coop_run_sm<K24a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 4: if (MASK & 16u) ok = coop_run_sm<K24b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 5: if (MASK & 32u) ok = coop_run_sm<K32a>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            case 6: if (MASK & 64u) ok = coop_run_sm<K32b>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last); break;
-            default: break;
+            case 0: if (MASK & 1u) ok = coop_run_sm<K8, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 1: if (MASK & 2u) ok = coop_run_sm<K12, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 2: if (MASK & 4u) ok = coop_run_sm<K16, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 3: if (MASK & 8u) ok = coop_run_sm<K24a, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 4: if (MASK & 16u) ok = coop_run_sm<K24b, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 5: if (MASK & 32u) ok = coop_run_sm<K32a, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 6: if (MASK & 64u) ok = coop_run_sm<K32b, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            default: ran = false; break;
         }
         if (!ok) break;
+        if (!ran) {  // a kind this kernel was not built for: flag it, take the next item
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                atomicOr(p.status, ST_BADDESC);
+                s_item = (int)atomicAdd(p.counter, 1u);
+            }
+            __syncthreads();
+            pre = false;
+            continue;
+        }
+        pre = true;  // coop_run_sm took the next item and issued its first copies
     }
 }
 
