@@ -677,6 +677,38 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "gpu_launches": launches, "clocks": clocks})
 
 
+def _surrogate_gemm_rates(torch, ctx, rows, info, stream, reps=10):
+    """The surrogate's three layer GEMMs at the inference shape (rows = cells in
+    the batch), each timed alone on the tensor-core kernel (bf16 in, FP32
+    accumulate) with CUDA events: TFLOP/s against the measured bf16 peak."""
+    width, ndim = int(info["width"]), int(info["ndim"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, basis = float(json.load(fh)["bf16_tflops"]), "of measured (cuBLAS bf16 burst)"
+    except (OSError, ValueError, KeyError):
+        peak, basis = 1900.0, "of fallback"
+    g = torch.Generator(device="cuda").manual_seed(0)
+    out = []
+    for name, (M, N, K) in (("W1", (rows, width, ndim)), ("W2", (rows, width, width)), ("W3", (rows, ndim, width))):
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ctx.tc_gemm(A, B, stream=stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                ctx.tc_gemm(A, B, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+        out.append({"layer": name, "M": M, "N": N, "K": K, "us": ms * 1e3, "tflops": tf, "frac": tf / peak})
+    ctx.sync_status(stream)
+    return {"peak_tflops": peak, "peak_basis": basis, "layers": out,
+            "note": "each GEMM alone, FP32 output (the surrogate fuses bias, GELU and the bf16 store instead)"}
+
+
 def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     """Surrogate trained on seeded pairs (f, Q_FP32(f)) at N = 16, evaluated with the
     fallback indicator on 1024 cells of the wall-heating slab after 200 steps."""
@@ -749,6 +781,7 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     v_l = nx * args.steps / (sum(ms_l) * 1e-3)
     v_f = nx * args.steps / (sum(ms_f) * 1e-3)
     v_64 = nx / (ms_64[0] * 1e-3)
+    gemms = _surrogate_gemm_rates(torch, ctx, nx, info, stream)
     wl = ("learned surrogate (residual MLP, width 1024, BF16 tensor cores) + P_N + fallback indicator "
           "(64 zeta points, tolerance 1e-2) on 1024 cells of the wall-heating slab (N=16, L=6, lambda=1, "
           "Kn=0.1) after 200 FP32 Strang steps; trained on %d seeded pairs, %d epochs" % (args.train_states,
@@ -762,6 +795,7 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "surrogate_indicator": {"value": nx * args.steps / (sum(ms_ind) * 1e-3), "unit": UNIT,
                                 "note": "surrogate + projection + indicator, threshold set so that no cell "
                                         "falls back"},
+        "surrogate_gemms": gemms,
         "fallback": {"cells": st["cells"], "fallbacks": st["fallbacks"],
                      "rate": st["fallbacks"] / max(st["cells"], 1), "max_indicator": st["max_indicator"]},
         "accuracy": {"norm": "||Q - Q_oracle|| / ||Q_loss_oracle|| on %d sampled cells" % len(pick),

@@ -3,9 +3,10 @@
 // followed by a fused epilogue (bias, GELU, residual, FP32 / BF16 / transposed BF16 stores).
 // Used by the learned surrogate (forward and backward passes of its MLP).
 //
-// Structure of one CTA (4 warps, one 128 x BN output tile):
+// Structure of one CTA (4 warps, one 128 x BN output tile, BN = 64, 128 or 256):
 // - thread 0 (producer) streams 128 x 64 tiles of A and BN x 64 tiles of B with
-//   TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) into a STAGES-deep ring,
+//   TMA (cp.async.bulk.tensor.2d, 128-byte swizzle) into a STAGES-deep ring
+//   (4, or 6-8 when the grid fits in one wave),
 //   signalling a "full" mbarrier with the transaction byte count;
 // - thread 32 (MMA issuer) waits for a full stage, issues four
 //   tcgen05.mma.kind::f16 (K = 16 each) into the TMEM accumulator (128 lanes x
@@ -30,7 +31,6 @@ namespace bte {
 namespace {
 
 constexpr int BM = 128, BK = 64;
-constexpr int STAGES = 4;
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -88,7 +88,10 @@ __device__ __forceinline__ float gelu_f(float x) {
     return 0.5f * x * (1.0f + tanhf(k0 * (x + k1 * x * x * x)));
 }
 
-template <int BN>
+// STAGES: depth of the TMA ring. With one CTA per SM the ring is what keeps
+// the copies in flight against the L2 latency, so a grid that fits in one
+// wave takes the deepest ring that fits (192 KB).
+template <int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmEpi g,
                     int M, int N, int K, int *status) {
@@ -279,19 +282,37 @@ bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int STAGES>
 size_t smem_bytes() {
     return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
+}
+
+template <int BN, int STAGES>
+cudaError_t set_smem() {
+    return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<BN, STAGES>());
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            n = 1;
+    }
+    return n;
 }
 
 }  // namespace
 
 cudaError_t gemm_bf16_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes<128>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gemm_bf16_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<64>());
+    cudaError_t e = set_smem<256, 4>();
+    if (e == cudaSuccess) e = set_smem<128, 4>();
+    if (e == cudaSuccess) e = set_smem<128, 6>();
+    if (e == cudaSuccess) e = set_smem<64, 4>();
+    if (e == cudaSuccess) e = set_smem<64, 8>();
+    sm_count();
     return e;
 }
 
@@ -300,14 +321,26 @@ cudaError_t gemm_bf16_prepare() {
 // fills rows beyond M with zeros; the epilogue skips them).
 int gemm_bf16(const void *A, const void *B, int M, int N, int K, const GemmEpi &g, int *status, cudaStream_t st) {
     if (M <= 0 || N <= 0 || K <= 0 || K % BK != 0 || N % 64 != 0) return -1;
-    const int BN = (N % 128 == 0 && (long)((M + BM - 1) / BM) * (N / 128) >= 148) ? 128 : 64;
+    // tile width: 256 when a 256-wide grid still fills about two thirds of the
+    // SMs in one wave (fewer re-reads of A), else 128 with at least a wave of
+    // tiles, else 64
+    const long mt = (M + BM - 1) / BM;
+    const int BN = (N % 256 == 0 && mt * (N / 256) >= 2 * sm_count() / 3 && mt * (N / 256) <= sm_count()) ? 256
+                   : (N % 128 == 0 && mt * (N / 128) >= 148) ? 128
+                                                              : 64;
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, M, K, BM) || !make_map(&mb, B, N, K, BN)) return -2;
     dim3 grid(N / BN, (M + BM - 1) / BM);
-    if (BN == 128)
-        gemm_bf16_tc_kernel<128><<<grid, 128, smem_bytes<128>(), st>>>(ma, mb, g, M, N, K, status);
-    else
-        gemm_bf16_tc_kernel<64><<<grid, 128, smem_bytes<64>(), st>>>(ma, mb, g, M, N, K, status);
+    const bool deep = (long)grid.x * grid.y <= sm_count() && K / BK > 4;  // one wave: the deep ring
+    if (BN == 256) {
+        gemm_bf16_tc_kernel<256, 4><<<grid, 128, smem_bytes<256, 4>(), st>>>(ma, mb, g, M, N, K, status);
+    } else if (BN == 128) {
+        if (deep) gemm_bf16_tc_kernel<128, 6><<<grid, 128, smem_bytes<128, 6>(), st>>>(ma, mb, g, M, N, K, status);
+        else gemm_bf16_tc_kernel<128, 4><<<grid, 128, smem_bytes<128, 4>(), st>>>(ma, mb, g, M, N, K, status);
+    } else {
+        if (deep) gemm_bf16_tc_kernel<64, 8><<<grid, 128, smem_bytes<64, 8>(), st>>>(ma, mb, g, M, N, K, status);
+        else gemm_bf16_tc_kernel<64, 4><<<grid, 128, smem_bytes<64, 4>(), st>>>(ma, mb, g, M, N, K, status);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

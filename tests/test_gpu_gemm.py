@@ -31,7 +31,7 @@ def bf16(rng, shape, scale=1.0):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 256, 512), (77, 64, 128), (1024, 1024, 4096),
-                                   (256, 4096, 1024)])
+                                   (256, 4096, 1024), (1024, 4096, 1024), (896, 4096, 512)])
 def test_gemm_matches_fp64(ctx, M, N, K):
     rng = np.random.default_rng(M + N + K)
     A, An = bf16(rng, (M, K))
