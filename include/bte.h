@@ -238,8 +238,8 @@ bte_status bte_state_load(bte_ctx *ctx, const char *path, double *f, int64_t n, 
  * bte_collide) it runs one projected FP32 collide of f per candidate
  * configuration -- convolution variant 1, 2, 3 or 4, 3 or 4 warps per CTA, 1 or 2
  * blocks in flight per warp, compensated merge every 16 or 32 blocks, for
- * variant 4 with and without split pencil items, and for N <= 16 one or four
- * CTAs per cell in the fused transforms -- times reps
+ * variant 4 with and without split pencil items, and for N <= 16 one, two or
+ * four CTAs per cell in the fused transforms -- times reps
  * repetitions with CUDA events on `stream`, and keeps the fastest as this
  * context's configuration for batches of the same shape (the same set of
  * grid sizes and number of 32-cell slots); it takes precedence over the

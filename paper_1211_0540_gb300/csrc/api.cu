@@ -1115,7 +1115,7 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
         for (int warps : {4, 3})
             for (int stages : {1, 2})
                 for (int merge : {16, 32})
-                    for (int split : {4, 1})
+                    for (int split : {4, 2, 1})
                         for (int csplit : {1, 0}) {
                         if (!small_n && split != 4) continue;
                         if (csplit && (impl != 4 || B->nsplit == 0)) continue;

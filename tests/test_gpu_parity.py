@@ -123,6 +123,29 @@ def test_fp64_plain_collide_matches_oracle(bte, N, ncells, lam):
     assert err.max() <= TOL64, err.max()
 
 
+@pytest.mark.parametrize("N", [8, 16])
+def test_zero_distribution_gives_zero_operator(bte, N):
+    """f = 0: fhat = 0, Qhat = 0, every moment 0, so Q is exactly 0 in both paths."""
+    f = np.zeros((40, N ** 3))
+    for mode in (bte.FP32, bte.FP64_PLAIN):
+        Q = run_collide(bte, N, 1.0, f, mode)
+        assert np.all(Q == 0.0), (mode, np.abs(Q).max())
+
+
+@pytest.mark.parametrize("N,ncells", [(8, 70), (16, 40)])
+def test_identical_cells_give_identical_results(bte, N, ncells):
+    """One cell copied into every slot (all 32 lanes of a group, several groups,
+    a ragged last group): every slot runs the same arithmetic in the same
+    order, so all outputs are bit-identical, and they match the oracle."""
+    one = inputs.homogeneous_cells(N, L, 1, seed=500 + N)
+    f = np.repeat(one, ncells, axis=0)
+    Q = run_collide(bte, N, 1.0, f, bte.FP32)
+    assert np.all(Q == Q[0]), np.abs(Q - Q[0]).max()
+    Qo = oracle.collide(N, L, 1.0, one)
+    err = np.linalg.norm(Q[:1] - Qo, axis=1) / loss_norm(N, 1.0, one)
+    assert err.max() <= TOL32, err.max()
+
+
 def test_raw_operator_matches_oracle_raw(bte):
     N, lam = 12, 1.0
     f = inputs.homogeneous_cells(N, L, 3, seed=7)
@@ -414,7 +437,7 @@ def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
     c.init_weights([(N, L, lam)])
     cfg = c.autotune(ft, reps=2)
     assert cfg["conv_impl"] in (1, 2, 3, 4) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
-    assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 4) and cfg["ms"] > 0.0
+    assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 2, 4) and cfg["ms"] > 0.0
     assert cfg["conv_split"] in (0, 1) and (cfg["conv_split"] == 0 or cfg["conv_impl"] == 4)
     Q = c.collide(ft)
     c.sync_status()
