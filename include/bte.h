@@ -180,6 +180,14 @@ bte_status bte_profile_read(bte_ctx *ctx, const char *kernel, int64_t *launches,
                             void *stream);
 bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
 
+/* Number of instance layouts (batches) the context keeps: each distinct
+ * (inst, ninst) given to bte_collide / bte_step / bte_autotune builds a batch
+ * (slot map, work items; device memory) that later calls reuse. The cache
+ * holds at most the "batch_cache" option (default 64); a new layout beyond it
+ * evicts the least recently used one, which synchronizes the device and drops
+ * captured step graphs. count (HOST) receives the number. */
+bte_status bte_batch_count(const bte_ctx *ctx, int64_t *count);
+
 /* Tuning options of the FP32 convolution (read by the autotuner and tests).
  * name: "conv_impl"   0 = one warp per work item, 1 = all warps of a CTA share
  *                      an item (reduced in shared memory), 2 = as 1 with packed
@@ -194,6 +202,8 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  *                      resident CTAs per SM of a one-block ring);
  *       "conv_merge"  blocks accumulated in plain FP32 between compensated
  *                      (TwoSum) merges (>= 1, default 16);
+ *       "batch_cache" instance layouts kept (2..2^20, default 64; see
+ *                      bte_batch_count);
  *       "conv_split"  variant 4: 1 (default) runs the batch's plan in which
  *                      the costliest pencil items are cut into two block
  *                      ranges (chosen when the batch is built, by simulating

@@ -25,7 +25,7 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 # Every symbol include/bte.h declares (checked by the ABI tests).
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
-           "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count",
+           "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count", "bte_batch_count",
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
            "bte_mlp_set_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
            "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_autotune", "bte_tune_save",
@@ -86,6 +86,7 @@ def load(path=None):
         "bte_profile_read": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_i64),
                                      ctypes.POINTER(c_d), vp]),
         "bte_launch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
+        "bte_batch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
         "bte_set_option": (c_int, [vp, ctypes.c_char_p, c_int]),
         "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
         "bte_collide_noalloc": (c_int, [vp, vp, vp, c_i64, vp]),
@@ -242,6 +243,11 @@ class Context:
     def launch_count(self):
         n = ctypes.c_int64()
         self._rc(self._lib.bte_launch_count(self._h, ctypes.byref(n)), "bte_launch_count")
+        return n.value
+
+    def batch_count(self):
+        n = ctypes.c_int64()
+        self._rc(self._lib.bte_batch_count(self._h, ctypes.byref(n)), "bte_batch_count")
         return n.value
 
     def set_option(self, name, value):

@@ -45,6 +45,7 @@ struct Batch {
     int *d_split = nullptr;
     float *d_part = nullptr;
     unsigned *d_counters = nullptr;
+    uint64_t last_use = 0;  // context tick of the latest lookup (least recently used is evicted first)
     unsigned kinds_mask = 0;
     bool uniform = false;
     int uniform_table = 0;
@@ -294,8 +295,21 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
     }
     auto it = c->batches.find(key);
     if (it != c->batches.end()) {
+        it->second->last_use = ++c->batch_tick;
         *out = it->second;
         return BTE_OK;
+    }
+    // bounded cache: a new layout evicts the least recently used one (an
+    // earlier batch of the same API call was looked up later, so it stays)
+    while ((int)c->batches.size() >= c->batch_cache_max && !c->batches.empty()) {
+        auto lru = c->batches.begin();
+        for (auto b = c->batches.begin(); b != c->batches.end(); ++b)
+            if (b->second->last_use < lru->second->last_use) lru = b;
+        cudaError_t e = cudaDeviceSynchronize();  // kernels in flight may still read it
+        if (e != cudaSuccess) return cuda_fail(c, e, "batch eviction");
+        drop_graphs(c);  // captured steps hold its device arrays
+        free_batch(lru->second);
+        c->batches.erase(lru);
     }
     // instance -> (table, offset)
     std::vector<int> tab(ninst);
@@ -418,6 +432,7 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
         free_batch(B);
         return cuda_fail(c, e, "batch upload");
     }
+    B->last_use = ++c->batch_tick;
     c->batches[key] = B;
     *out = B;
     return BTE_OK;
@@ -730,6 +745,12 @@ extern "C" {
 
 const char *bte_version(void) { return "libbte 0.1 (sm_103a)"; }
 
+bte_status bte_batch_count(const bte_ctx *c, int64_t *count) {
+    if (!c || !count) return BTE_EINVAL;
+    *count = (int64_t)c->batches.size();
+    return BTE_OK;
+}
+
 bte_status bte_create(bte_ctx **ctx, int device) {
     if (!ctx) return BTE_EINVAL;
     *ctx = nullptr;
@@ -1030,6 +1051,7 @@ static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_stages")) { *lo = 0; *hi = 4; return &c->conv_stages; }
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
     if (!std::strcmp(name, "conv_split")) { *lo = 0; *hi = 1; return &c->conv_split; }
+    if (!std::strcmp(name, "batch_cache")) { *lo = 2; *hi = 1 << 20; return &c->batch_cache_max; }
     if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
     return nullptr;
 }

@@ -127,7 +127,9 @@ struct bte_ctx {
     static constexpr int kScratch = 16;
     void *scratch[kScratch] = {nullptr};
     size_t scratch_bytes[kScratch] = {0};
-    std::map<std::string, bte::Batch *> batches;
+    std::map<std::string, bte::Batch *> batches;  // per instance layout, at most batch_cache_max
+    int batch_cache_max = 64;
+    uint64_t batch_tick = 0;
     std::map<bte::GraphKey, bte::GraphRec> graphs;
     // profiling / launch accounting
     bool prof = false;

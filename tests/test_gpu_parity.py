@@ -209,6 +209,32 @@ def test_uneven_batch_matches_oracle(bte):
     assert np.all(Qg[mask] == 7.0)
 
 
+def test_batch_cache_evicts_least_recently_used(bte):
+    """At most "batch_cache" instance layouts are kept; a layout beyond that
+    evicts the least recently used one, and an evicted layout used again is
+    rebuilt with correct results (here: 6 layouts through a cache of 3)."""
+    N, lam = 8, 1.0
+    c = bte.Context(0)
+    c.init_weights([(N, L, lam)])
+    c.set_option("batch_cache", 3)
+    M = N ** 3
+    f = inputs.homogeneous_cells(N, L, 12, seed=77)
+    ft = torch.from_numpy(f.reshape(-1).copy()).cuda()
+    Qo = oracle.collide(N, L, lam, f)
+    scale = loss_norm(N, lam, f)
+    layouts = [list(range(k, 12, 2 + k % 3)) for k in range(6)] + [list(range(0, 12, 2))]
+    for cells in layouts:
+        inst = [(0, i * M) for i in cells]
+        Qt = torch.zeros_like(ft)
+        c.collide(ft, Qt, inst=inst, mode=bte.FP32)
+        c.sync_status()
+        assert c.batch_count() <= 3
+        Q = Qt.cpu().numpy().reshape(12, M)
+        err = np.linalg.norm(Q[cells] - Qo[cells], axis=1) / scale[cells]
+        assert err.max() <= TOL32, (cells, err.max())
+    c.close()
+
+
 def test_rk2_step_matches_oracle(bte):
     N, lam = 12, 1.0
     f = inputs.homogeneous_cells(N, L, 33, seed=9)
