@@ -689,7 +689,8 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
             return fail(c, BTE_ENOMEM, "learned mode: indicator table");
     }
     bte_status s;
-    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * (size_t)B->nslots * (2 * c->ind->S + 1))) != BTE_OK)
+    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * indicator_scratch_floats(*c->ind, t->N, B->nslots))) !=
+        BTE_OK)
         return s;
     // 1. surrogate in chunks of up to 8192 cells, 2. its output projected (fused)
     const int64_t chunk = 8192;

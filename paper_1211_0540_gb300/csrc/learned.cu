@@ -32,21 +32,26 @@ namespace {
 // projected surrogate output.
 constexpr int kIndWarps = 8;
 
+// The pencil's blocks are split between two CTAs (blockIdx.z = half) so that
+// the S x groups items fill the GPU; each half reduces its warps in a fixed
+// order into part[], and the half that finishes second (an atomic count, no
+// waiting) adds half 0 and half 1 in that order and forms the errors.
 template <int N>
 __global__ void __launch_bounds__(32 * kIndWarps)
 indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, const float *__restrict__ Wfull,
                  const float *__restrict__ Wloss, const uint32_t *__restrict__ desc, const IndPencil *__restrict__ pens,
-                 int cpad, int64_t eoff, int nslots, float *err2, float *den2) {
+                 int cpad, int64_t eoff, int nslots, float *err2, float *den2, float *part, unsigned *cnt) {
     constexpr int M = N * N * N, H = N / 2;
     extern __shared__ __align__(16) float red[];  // [kIndWarps][4 N][32]
-    const int p = blockIdx.x, g = blockIdx.y, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p = blockIdx.x, g = blockIdx.y, half = blockIdx.z, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const IndPencil pen = pens[p];
     const int k1 = pen.kk / N, k2 = pen.kk % N;
     const float2 *Fg = F + eoff + (int64_t)g * M * kLanes + lane;
     float acc[4 * N];  // full (re, im) per k3, then loss (re, im) per k3
 #pragma unroll
     for (int i = 0; i < 4 * N; ++i) acc[i] = 0.f;
-    for (int b = warp; b < pen.nblocks; b += kIndWarps) {
+    const int bmid = pen.nblocks / 2, bend = half ? pen.nblocks : bmid;
+    for (int b = (half ? bmid : 0) + warp; b < bend; b += kIndWarps) {
         const uint32_t d = desc[pen.desc_off + b];
         const int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16), n1 = k1 - m1 + H, n2 = k2 - m2 + H;
         float2 av[N], bv[N];
@@ -85,27 +90,37 @@ indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, co
 #pragma unroll
     for (int i = 0; i < 4 * N; ++i) red[(warp * 4 * N + i) * kLanes + lane] = acc[i];
     __syncthreads();
-    if (warp == 0) {
-        float e = 0.f, dn = 0.f;
-        const float2 *qn = QN + eoff + (int64_t)g * M * kLanes + (int64_t)pen.kk * N * kLanes + lane;
-        for (int j = 0; j < N; ++j) {
-            float fr = 0.f, fi = 0.f, lr = 0.f, li = 0.f;
-            for (int w = 0; w < kIndWarps; ++w) {
-                const float *rw = red + (size_t)w * 4 * N * kLanes + lane;
-                fr += rw[(2 * j) * kLanes];
-                fi += rw[(2 * j + 1) * kLanes];
-                lr += rw[(2 * N + 2 * j) * kLanes];
-                li += rw[(2 * N + 2 * j + 1) * kLanes];
-            }
-            const float2 q = qn[(int64_t)j * kLanes];
-            const float dr = q.x - fr, di = q.y - fi;
-            e += dr * dr + di * di;
-            dn += lr * lr + li * li;
-        }
-        const int slot = g * kLanes + lane;
-        err2[(size_t)p * nslots + slot] = e;
-        den2[(size_t)p * nslots + slot] = dn;
+    if (warp != 0) return;
+    const size_t item = (size_t)p * gridDim.y + g;
+    float *mine = part + (item * 2 + half) * (4 * N * kLanes) + lane;
+    for (int i = 0; i < 4 * N; ++i) {
+        float v = 0.f;
+        for (int w = 0; w < kIndWarps; ++w) v += red[((size_t)w * 4 * N + i) * kLanes + lane];
+        mine[i * kLanes] = v;
     }
+    __threadfence();  // this half's sums before the count
+    __syncwarp();
+    unsigned old = 0;
+    if (lane == 0) old = atomicAdd(cnt + item, 1u);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != 1u) return;
+    __threadfence();  // the other half's sums after the count
+    const float *h0 = part + item * 2 * (4 * N * kLanes) + lane, *h1 = h0 + 4 * N * kLanes;
+    float e = 0.f, dn = 0.f;
+    const float2 *qn = QN + eoff + (int64_t)g * M * kLanes + (int64_t)pen.kk * N * kLanes + lane;
+    for (int j = 0; j < N; ++j) {
+        const float fr = __ldcg(h0 + (2 * j) * kLanes) + __ldcg(h1 + (2 * j) * kLanes);
+        const float fi = __ldcg(h0 + (2 * j + 1) * kLanes) + __ldcg(h1 + (2 * j + 1) * kLanes);
+        const float lr = __ldcg(h0 + (2 * N + 2 * j) * kLanes) + __ldcg(h1 + (2 * N + 2 * j) * kLanes);
+        const float li = __ldcg(h0 + (2 * N + 2 * j + 1) * kLanes) + __ldcg(h1 + (2 * N + 2 * j + 1) * kLanes);
+        const float2 q = qn[(int64_t)j * kLanes];
+        const float dr = q.x - fr, di = q.y - fi;
+        e += dr * dr + di * di;
+        dn += lr * lr + li * li;
+    }
+    const int slot = g * kLanes + lane;
+    err2[(size_t)p * nslots + slot] = e;
+    den2[(size_t)p * nslots + slot] = dn;
 }
 
 template <int N>
@@ -315,23 +330,33 @@ void launch_post_project(const float *Y, const double *rho, int B, int N, float 
     }
 }
 
+size_t indicator_scratch_floats(const IndicatorTable &it, int N, int nslots) {
+    const size_t items = (size_t)it.S * (nslots / kLanes);
+    return 2 * (size_t)it.S * nslots + nslots + items * 2 * 4 * N * kLanes + items;
+}
+
 void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
                       int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st) {
-    dim3 grid(it.S, nslots / kLanes);
+    dim3 grid(it.S, nslots / kLanes, 2);
+    // after err2, den2 and ind: the halves' partial sums, then the per-item counts
+    const size_t items = (size_t)it.S * (nslots / kLanes);
+    float *part = ind + nslots;
+    unsigned *cnt = reinterpret_cast<unsigned *>(part + items * 2 * 4 * t.N * kLanes);
+    cudaMemsetAsync(cnt, 0, sizeof(unsigned) * items, st);
     switch (t.N) {
         case 8:
             indicator_kernel<8><<<grid, 32 * kIndWarps, ind_smem<8>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
-                                                                           it.d_pen, t.cpad[0], eoff, nslots, err2, den2);
+                                                                           it.d_pen, t.cpad[0], eoff, nslots, err2, den2, part, cnt);
             break;
         case 12:
             indicator_kernel<12><<<grid, 32 * kIndWarps, ind_smem<12>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
                                                                              it.d_pen, t.cpad[0], eoff, nslots, err2,
-                                                                             den2);
+                                                                             den2, part, cnt);
             break;
         default:
             indicator_kernel<16><<<grid, 32 * kIndWarps, ind_smem<16>(), st>>>(F, QN, t.d_w32, it.d_wloss, t.d_desc,
                                                                              it.d_pen, t.cpad[0], eoff, nslots, err2,
-                                                                             den2);
+                                                                             den2, part, cnt);
             break;
     }
     indicator_reduce_kernel<<<(nslots + 255) / 256, 256, 0, st>>>(err2, den2, it.S, nslots, nvalid, ind);

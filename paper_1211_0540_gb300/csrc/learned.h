@@ -29,7 +29,9 @@ void free_indicator_table(IndicatorTable &t);
 void launch_post_project(const float *Y, const double *rho, int B, int N, float s_out, const ProjArgs &pa, double *Q,
                          cudaStream_t st);
 // ind[slot] for the slots of one segment (eoff: its offset in the group buffers);
-// err2, den2: S * nslots floats of scratch.
+// err2, den2: S * nslots floats of scratch each, ind: nslots floats followed by
+// the kernel's own scratch (indicator_scratch_floats counts all of it).
+size_t indicator_scratch_floats(const IndicatorTable &it, int N, int nslots);
 void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
                       int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st);
 
