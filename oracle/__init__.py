@@ -39,8 +39,11 @@ PINS = {
                 "symmetry; Qhat(0) = 0; weak-form brute force (different discretisation)",
     "project": "CQ=0, P^2=P, minimal-norm (projection onto null(C)) via numpy lstsq",
     "collide": "Q(Maxwellian) -> 0 and BKW closed form, both converging in N",
-    "rk2_homogeneous": "conservation over steps; Heun order on a linear test via Ghat lookups",
+    "rk2_homogeneous": "explicit Heun stages; conservation over 20 steps; second order in dt "
+                       "(successive differences shrink by ~4 per halving)",
     "transport": "constant state, exact mass balance at the walls, second-order convergence",
+    "learned.indicator_pencils": "SplitMix64 published test vector; range and distinctness",
+    "learned.learned_indicator": "numpy FFT + dense-weight gather evaluation; scale invariance",
 }
 
 _lib = None

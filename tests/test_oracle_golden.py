@@ -1,6 +1,6 @@
-"""The oracle against its stored regression fixture (tests/golden/README.md
-says why the fixture is the oracle's own output: the paper prints no solution
-values)."""
+"""The oracle against its stored regression fixture, written by
+tests/golden/make_fixtures.py from the oracle itself: the paper prints no
+solution values (its figures are plots, its one table wall-clock times)."""
 import json
 import os
 

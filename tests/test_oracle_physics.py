@@ -104,3 +104,23 @@ def test_heun_step_matches_explicit_stages():
     ref = f + 0.5 * dt / eps * (q1 + q2)
     got = oracle.rk2_homogeneous(N, L, 1.0, f, dt, eps)
     assert np.abs(got - ref).max() <= 1e-15 * np.abs(f).max() * 10
+
+
+def test_heun_step_is_second_order_in_time():
+    """Order of the RK2 reading (Sec. 3.1): differences of the state at T = 0.8
+    between runs with dt, dt/2, dt/4 and dt/8 shrink by about 4 per halving and
+    approach 4 (a first-order step would give 2, a wrong stage weight a plateau)."""
+    N = 8
+    f0 = inputs.homogeneous_cells(N, L, 1, seed=3)
+
+    def run(dt, T=0.8):
+        f = f0.copy()
+        for _ in range(int(round(T / dt))):
+            f = oracle.rk2_homogeneous(N, L, 1.0, f, dt)
+        return f
+
+    a, b, c, d = (run(dt) for dt in (0.1, 0.05, 0.025, 0.0125))
+    r1 = np.abs(a - b).max() / np.abs(b - c).max()
+    r2 = np.abs(b - c).max() / np.abs(c - d).max()
+    # measured 4.45 and 4.21
+    assert 3.6 < r2 < r1 < 5.0 and r2 < 4.4, (r1, r2)
