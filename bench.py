@@ -399,8 +399,8 @@ def main():
     flops_per_launch = 10.0 * conv_pairs * NX
     conv_avg_ms = conv_ms / max(conv_n, 1)
     achieved = flops_per_launch / (conv_avg_ms * 1e-3) / 1e12
-    clk = clocks["sm_mhz"] or 1920.0
-    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    peak, clk = _alu_peak(clocks)
+    fma = _measured_fma(ctx, stream)
     traffic = load_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -415,8 +415,8 @@ def main():
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz "
-                                   "(measured FFMA microbenchmark: 74.9 TFLOP/s)" % clk,
+                     "peak_basis": _peak_basis(clk, fma), "measured_fma": fma,
+                     "frac_of_measured_ffma2": achieved / fma["fp32_ffma2_tflops"],
                      "flops_per_launch": flops_per_launch,
                      "flop_unit": "10 flops per evaluated (zeta, {xi, zeta-xi}) pair per cell",
                      "conv_ms_per_launch": conv_avg_ms, "conv_launches_timed": conv_n},
@@ -479,8 +479,25 @@ def _moment_rel(oracle, n, q):
 
 
 def _alu_peak(clocks):
-    clk = clocks["sm_mhz"] or 1920.0
+    """FP32 ALU peak from the unit counts and the SM clock sampled during the
+    timed region; no clock samples is an error, not a guess."""
+    clk = clocks.get("sm_mhz")
+    if not clk:
+        raise RuntimeError("no SM clock samples during the timed region (nvidia-smi): the ALU peak is unknown")
     return SMS * FP32_LANES * 2 * clk * 1e6 / 1e12, clk
+
+
+def _measured_fma(ctx, stream):
+    """FMA rates measured on this GPU in this run (bte_alu_peak, untimed)."""
+    return {"fp32_ffma_tflops": ctx.alu_peak(0, stream), "fp32_ffma2_tflops": ctx.alu_peak(1, stream),
+            "fp64_dfma_tflops": ctx.alu_peak(2, stream),
+            "how": "bte_alu_peak: 2048 threads per SM of independent FMA chains, 5 launches after a warm-up"}
+
+
+def _peak_basis(clk, fma):
+    return ("152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz during the timed region; measured in "
+            "this run (bte_alu_peak): FFMA %.1f, FFMA2 %.1f TFLOP/s" % (clk, fma["fp32_ffma_tflops"],
+                                                                      fma["fp32_ffma2_tflops"]))
 
 
 def _line(args, metric, value, unit, ms_per_step, workload, extra):
@@ -589,6 +606,7 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
     relp = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qo, axis=1)
     peak, clk = _alu_peak(clocks)
+    fma = _measured_fma(ctx, stream)
     pairs = conv_pairs_per_cell(n)
     conv_ms = conv[0] / max(conv[1], 1)
     achieved = 10.0 * pairs * nc / (conv_ms * 1e-3) / 1e12
@@ -597,7 +615,7 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     return _line(args, "cell-collision evals/s at N=32 (FP32 operator)", value, UNIT, tot / args.steps, wl, {
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk,
+                     "peak_basis": _peak_basis(clk, fma), "measured_fma": fma,
                      "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
                      "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
         "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
@@ -646,6 +664,7 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     flops_step = sum(2 * 10.0 * conv_pairs_per_cell(n) for (n, _, _) in items)
     conv_ms = t / max(k, 1)
     peak, clk = _alu_peak(clocks)
+    fma = _measured_fma(ctx, stream)
     achieved = flops_step / 2 / (conv_ms * 1e-3) / 1e12
     # accuracy of one collision evaluation of the batch on sampled instances
     fb = torch.from_numpy(buf).cuda()
@@ -671,7 +690,7 @@ def run_uneven(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution, all sizes in one launch)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "conv_ms_per_launch": conv_ms,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock %.0f MHz" % clk},
+                     "peak_basis": _peak_basis(clk, fma), "measured_fma": fma},
         "flop_rate_whole_step_tflops": flops_step / (tot / args.steps * 1e-3) / 1e12,
         "accuracy": {"rel_l2_loss_norm_max_by_N": {str(k_): v for k_, v in errs.items()}},
         "gpu_launches": launches, "clocks": clocks})
@@ -774,10 +793,10 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     ctx.sync_status(stream)
     a32, al, ann = (x.cpu().numpy().reshape(nx, M) for x in (Q32, Ql, Qnn))
     fwn = fw.cpu().numpy().reshape(nx, M)
-    # errors normalised by the loss term (Q itself is near 0 in the equilibrated interior)
-    pick = np.unique(np.concatenate([np.arange(8), np.linspace(0, nx - 1, 56).astype(int)]))
-    qm = np.linalg.norm(oracle.collide(n, L, lam, fwn[pick], part=1, project=False), axis=1)
-    qo = oracle.collide(n, L, lam, fwn[pick])
+    # errors normalised by the loss term (Q itself is near 0 in the equilibrated interior), every cell
+    pick = np.arange(nx)
+    qm = np.linalg.norm(oracle.collide(n, L, lam, fwn, part=1, project=False), axis=1)
+    qo = oracle.collide(n, L, lam, fwn)
     e_l = np.linalg.norm(al[pick] - qo, axis=1) / qm
     e_nn = np.linalg.norm(ann[pick] - qo, axis=1) / qm
     e_32 = np.linalg.norm(a32[pick] - qo, axis=1) / qm
@@ -802,11 +821,11 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "autotuned": tuned,
         "fallback": {"cells": st["cells"], "fallbacks": st["fallbacks"],
                      "rate": st["fallbacks"] / max(st["cells"], 1), "max_indicator": st["max_indicator"]},
-        "accuracy": {"norm": "||Q - Q_oracle|| / ||Q_loss_oracle|| on %d sampled cells" % len(pick),
+        "accuracy": {"norm": "||Q - Q_oracle|| / ||Q_loss_oracle|| on all %d cells" % len(pick),
                      "learned_with_fallback_max": float(e_l.max()),
                      "learned_with_fallback_median": float(np.median(e_l)),
                      "surrogate_only_max": float(e_nn.max()), "surrogate_only_median": float(np.median(e_nn)),
-                     "fp32_max": float(e_32.max()), "cells_checked": pick.tolist()},
+                     "fp32_max": float(e_32.max()), "cells_checked": int(len(pick))},
         "training": {"states": args.train_states, "epochs": args.epochs, "final_loss": float(loss),
                      "data_s": t_data, "train_s": t_train,
                      "samples_per_s": args.train_states * args.epochs / t_train, "params": info},

@@ -21,7 +21,9 @@
  *   bte_sync_status.
  * - Every call returns a bte_status; on failure bte_last_error() describes it.
  *   No call traps the GPU on bad input: shapes are checked on the host.
- * - A context is not thread-safe; use one context per host thread.
+ * - A context is not thread-safe; use one context per host thread. Contexts
+ *   on different host threads are independent (the library's process-wide
+ *   caches of kernel configurations are locked).
  *
  * Instances (uneven batches)
  * --------------------------
@@ -122,8 +124,8 @@ bte_status bte_collide(bte_ctx *ctx, const double *f, double *Q, const bte_insta
 /* bte_collide with flags (BTE_FLAG_RAW returns the unprojected Qt).
  * Mode BTE_LEARNED (uniform cells of table 0, surrogate built with
  * bte_mlp_init): Q = P_N(Q_nn) from the surrogate, then a residual indicator
- * per cell: the exact operator is evaluated at 64 sampled Fourier modes
- * (seeded, |k'|_inf <= N/4, zeta != 0) and
+ * per cell: the exact operator is evaluated at about 64 sampled Fourier modes
+ * (bte_learned_sample: whole pencils with |k1'|, |k2'| <= N/4) and
  *   ind = ||F[Q](zeta_s) - Qhat(zeta_s)|| / ||Qhat_loss(zeta_s)||
  * (Qhat_loss: the same sum with the loss term of Ghat only). Cells with ind
  * above the option "learned_tol_ppm" * 1e-6 (default 1e-2) are recomputed with
@@ -184,9 +186,16 @@ bte_status bte_launch_count(const bte_ctx *ctx, int64_t *count);
  * (inst, ninst) given to bte_collide / bte_step / bte_autotune builds a batch
  * (slot map, work items; device memory) that later calls reuse. The cache
  * holds at most the "batch_cache" option (default 64); a new layout beyond it
- * evicts the least recently used one, which synchronizes the device and drops
- * captured step graphs. count (HOST) receives the number. */
+ * evicts the least recently used one, which waits for the kernels this context
+ * has enqueued and drops captured step graphs. count (HOST) receives the number. */
 bte_status bte_batch_count(const bte_ctx *ctx, int64_t *count);
+
+/* Number of captured step graphs the context keeps (bte_step on a non-default
+ * stream captures one per (instance list, mode, transport, dt, eps, f,
+ * stream)). The cache holds at most the "graph_cache" option (default 32); a
+ * new graph beyond it destroys the least recently replayed one (a replay
+ * still in flight completes first). count (HOST) receives the number. */
+bte_status bte_graph_count(const bte_ctx *ctx, int64_t *count);
 
 /* Tuning options of the FP32 convolution (read by the autotuner and tests).
  * name: "conv_impl"   0 = one warp per work item, 1 = all warps of a CTA share
@@ -204,6 +213,8 @@ bte_status bte_batch_count(const bte_ctx *ctx, int64_t *count);
  *                      (TwoSum) merges (>= 1, default 16);
  *       "batch_cache" instance layouts kept (2..2^20, default 64; see
  *                      bte_batch_count);
+ *       "graph_cache" captured step graphs kept (1..2^20, default 32; see
+ *                      bte_graph_count);
  *       "conv_split"  variant 4: 1 (default) runs the batch's plan in which
  *                      the costliest pencil items are cut into two block
  *                      ranges (chosen when the batch is built, by simulating
@@ -302,6 +313,12 @@ bte_status bte_tc_gemm(bte_ctx *ctx, const void *A, const void *B, float *D, int
 bte_status bte_mlp_init(bte_ctx *ctx, int table, int width, uint64_t seed);
 bte_status bte_mlp_info(const bte_ctx *ctx, int64_t *nparams, int *width, int *ndim, double *s_in, double *s_out);
 bte_status bte_mlp_set_scales(bte_ctx *ctx, double s_in, double s_out);
+/* bte_mlp_fit_scales: s_in as given, and s_out making the training targets
+ *   s_out Q / rho^2 of the n pairs (f[i], Q[i]) (DEVICE, FP64, back to back)
+ *   unit-RMS: s_out = 1 / sqrt(mean_i,j (Q_ij / rho_i^2)^2), rho_i = sum f_i dv^3.
+ *   FP64, summed in a fixed order. *s_out (HOST, optional) receives it. Synchronous. */
+bte_status bte_mlp_fit_scales(bte_ctx *ctx, const double *f, const double *Q, int64_t n, double s_in, double *s_out,
+                              void *stream);
 bte_status bte_mlp_get_params(bte_ctx *ctx, float *host, int64_t n);
 bte_status bte_mlp_set_params(bte_ctx *ctx, const float *host, int64_t n);
 bte_status bte_mlp_train(bte_ctx *ctx, const double *f, const double *Q, int64_t nsamples, int epochs, int batch,
@@ -314,10 +331,31 @@ bte_status bte_mlp_infer(bte_ctx *ctx, const double *f, double *Q, int64_t n, vo
  * the largest indicator seen. */
 bte_status bte_learned_stats(bte_ctx *ctx, int64_t *cells, int64_t *fallbacks, double *max_indicator, int reset);
 
+/* The fallback indicator of the learned mode (no counterpart in the paper).
+ * Sampled modes: S = max(1, 64 / N) distinct zeta pencils (k1, k2) of table 0,
+ * each with all N values of k3; the offsets k1' = k1 - N/2 and k2' lie in
+ * [-N/4, N/4] and are drawn from SplitMix64 (Steele, Lea and Flood, OOPSLA
+ * 2014) seeded with 12345: offset = (next mod (N/2 + 1)) - N/4, k1' first,
+ * repeated pencils skipped (integer arithmetic, the same on every platform).
+ * bte_learned_sample: *S (HOST) receives the pencil count and kk (HOST,
+ *   optional, cap ints) the pencils as k1 N + k2 in drawing order.
+ * bte_learned_indicator: for ncells uniform cells of table 0 (N <= 16) with
+ *   distributions f and candidate operator values Q (DEVICE, FP64, ncells N^3
+ *   each), writes per cell (DEVICE, ncells doubles)
+ *     ind = ||F[Q](zeta_s) - Qhat(zeta_s)|| / ||Qhat_loss(zeta_s)||
+ *   over the sampled modes: F is the forward transform of Sec. 3.2 in FP32,
+ *   Qhat the weighted convolution of Sec. 3.2 at those modes (FP32, the fast
+ *   path's pair-symmetrised weights) and Qhat_loss the same sum with the loss
+ *   term of Ghat only. This is the quantity BTE_LEARNED compares with the
+ *   threshold. Asynchronous. Errors: BTE_EINVAL, BTE_ESTATE, BTE_ENOMEM, BTE_ECUDA. */
+bte_status bte_learned_sample(bte_ctx *ctx, int *kk, int cap, int *S);
+bte_status bte_learned_indicator(bte_ctx *ctx, const double *f, const double *Q, int64_t ncells, double *ind,
+                                 void *stream);
+
 /* Size of the static device work area used by bte_collide_noalloc (16 MiB). */
 #define BTE_NOALLOC_SCRATCH_BYTES (16u << 20)
 
-/* bte_collide_noalloc — the FP32 collision operator (as bte_collide with
+/* bte_collide_noalloc -- the FP32 collision operator (as bte_collide with
  * mode BTE_FP32, inst == NULL: ncells uniform cells of table 0, projected Q)
  * for callers that cannot allocate GPU memory while they run: code that works
  * inside a fixed memory budget handed out up front (an embedding application's
@@ -326,22 +364,38 @@ bte_status bte_learned_stats(bte_ctx *ctx, int64_t *cells, int64_t *fallbacks, d
  * synchronised by, cudaMalloc/cudaFree. The paper has no counterpart; this is
  * a service of the library.
  * The call allocates nothing: no cudaMalloc, no cudaFree, no allocating
- * library routine, no host heap. Its work area (queue counter, per-cell
- * offsets, work list, fhat and Qhat) is one file-scope device array of
- * BTE_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds until
- * the process exits. The caller passes f and Q (device, ncells * N^3 doubles);
- * the weight tables must have been built before (bte_init_weights, set-up).
+ * library routine, and on success no host heap either. Its work area (queue
+ * counter, per-cell offsets, work list, fhat and Qhat) is one file-scope
+ * device array of BTE_NOALLOC_SCRATCH_BYTES, which every GPU that loads the
+ * library holds until the process exits. A small kernel fills the work list
+ * from a template built with the weight tables, so the call copies nothing
+ * from the host and does not wait for `stream`. The caller passes f and Q
+ * (device, ncells * N^3 doubles); the weight tables must have been built
+ * before (bte_init_weights, at set-up), which also prepares the kernel
+ * configurations the call looks up (as do bte_set_option and bte_autotune).
+ * It runs the configuration autotuned for this batch shape if there is one
+ * (without split work items), else the context's options.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Every call shares the array and leaves its contents
- * behind; each call resets what must start at zero. Calls that overlap on the
- * GPU (two streams, or two threads) race on the array: serialise them. The
- * call uploads its work list and synchronises `stream` once before launching.
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. The caller's current device is left as it was.
+ * Every call shares the array and leaves its contents behind; each call resets
+ * what must start at zero. Calls that overlap on the GPU (two streams, or two
+ * threads) race on the array: serialise them.
  * Limits: table 0 must have N = 8, 12 or 16; the cells must fit the array
  * (2 * ceil(ncells/32) * 32 * N^3 * 8 bytes of work arrays plus the work list):
- * up to 224 cells at N = 16, 576 at N = 12, 2016 at N = 8. Larger requests fail with BTE_EINVAL and a message
- * naming the bytes needed. Errors: BTE_EINVAL, BTE_ESTATE, BTE_ECUDA. */
+ * up to 224 cells at N = 16, 576 at N = 12, 2016 at N = 8. Larger requests fail
+ * with BTE_EINVAL and a message naming the bytes needed. Errors: BTE_EINVAL,
+ * BTE_ESTATE, BTE_ECUDA. */
 bte_status bte_collide_noalloc(bte_ctx *ctx, const double *f, double *Q, int64_t ncells, void *stream);
+
+/* Arithmetic-rate probe of this GPU (no counterpart in the paper; the
+ * denominators of the kernels' rooflines). kind 0: FP32 FMA (fma.rn.f32),
+ * 1: packed FP32 FMA (fma.rn.f32x2), 2: FP64 FMA. Every SM runs 2048 threads of
+ * independent FMA chains; *tflops (HOST) receives 2 flops per FMA over the
+ * CUDA-event time of 5 launches after one warm-up, *ms (HOST, optional) the
+ * time of one launch. Synchronous (on `stream`). Errors: BTE_EINVAL, BTE_ENOMEM,
+ * BTE_ECUDA. */
+bte_status bte_alu_peak(bte_ctx *ctx, int kind, double *tflops, double *ms, void *stream);
 
 /* Library build identification (static string). */
 const char *bte_version(void);

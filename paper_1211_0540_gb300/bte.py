@@ -25,11 +25,12 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 # Every symbol include/bte.h declares (checked by the ABI tests).
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
-           "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count", "bte_batch_count",
+           "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count", "bte_batch_count", "bte_graph_count",
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
-           "bte_mlp_set_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
-           "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_autotune", "bte_tune_save",
-           "bte_tune_load", "bte_state_save", "bte_state_load"]
+           "bte_mlp_set_scales", "bte_mlp_fit_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
+           "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_learned_sample",
+           "bte_learned_indicator", "bte_autotune", "bte_tune_save",
+           "bte_tune_load", "bte_state_save", "bte_state_load", "bte_alu_peak"]
 
 
 class Grid(ctypes.Structure):
@@ -87,6 +88,7 @@ def load(path=None):
                                      ctypes.POINTER(c_d), vp]),
         "bte_launch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
         "bte_batch_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
+        "bte_graph_count": (c_int, [vp, ctypes.POINTER(c_i64)]),
         "bte_set_option": (c_int, [vp, ctypes.c_char_p, c_int]),
         "bte_get_option": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
         "bte_collide_noalloc": (c_int, [vp, vp, vp, c_i64, vp]),
@@ -95,6 +97,7 @@ def load(path=None):
         "bte_mlp_info": (c_int, [vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_d), ctypes.POINTER(c_d)]),
         "bte_mlp_set_scales": (c_int, [vp, c_d, c_d]),
+        "bte_mlp_fit_scales": (c_int, [vp, vp, vp, c_i64, c_d, ctypes.POINTER(c_d), vp]),
         "bte_mlp_get_params": (c_int, [vp, vp, c_i64]),
         "bte_mlp_set_params": (c_int, [vp, vp, c_i64]),
         "bte_mlp_train": (c_int, [vp, vp, vp, c_i64, c_int, c_int, c_d, c_d, ctypes.c_uint64,
@@ -103,11 +106,14 @@ def load(path=None):
         "bte_mlp_infer": (c_int, [vp, vp, vp, c_i64, vp]),
         "bte_learned_stats": (c_int, [vp, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64), ctypes.POINTER(c_d),
                                       c_int]),
+        "bte_learned_sample": (c_int, [vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int)]),
+        "bte_learned_indicator": (c_int, [vp, vp, vp, c_i64, vp, vp]),
         "bte_autotune": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_int, ctypes.POINTER(c_int),
                                  ctypes.POINTER(c_d), vp]),
         "bte_tune_save": (c_int, [vp, ctypes.c_char_p]),
         "bte_tune_load": (c_int, [vp, ctypes.c_char_p, ctypes.POINTER(c_int)]),
         "bte_state_save": (c_int, [vp, ctypes.c_char_p, vp, c_i64, c_d, c_i64, vp]),
+        "bte_alu_peak": (c_int, [vp, c_int, ctypes.POINTER(c_d), ctypes.POINTER(c_d), vp]),
         "bte_state_load": (c_int, [vp, ctypes.c_char_p, vp, c_i64, ctypes.POINTER(c_d), ctypes.POINTER(c_i64), vp]),
     }
     for name, (res, args) in sig.items():
@@ -199,6 +205,24 @@ class Context:
                                              int(bool(reset))), "bte_learned_stats")
         return dict(cells=a.value, fallbacks=b.value, max_indicator=d.value)
 
+    def learned_sample(self):
+        """The indicator's sampled pencils (k1 N + k2), in drawing order."""
+        S = ctypes.c_int()
+        buf = (ctypes.c_int * 1024)()
+        self._rc(self._lib.bte_learned_sample(self._h, buf, 1024, ctypes.byref(S)), "bte_learned_sample")
+        return list(buf[:S.value])
+
+    def learned_indicator(self, f, Q, stream=None):
+        """Indicator of the learned mode for caller-given (f, Q) pairs (uniform cells of table 0)."""
+        import torch
+        _check_f64(f, "f")
+        _check_f64(Q, "Q")
+        _, n = self._inst(None, f)
+        out = torch.empty(n, dtype=torch.float64, device=f.device)
+        self._rc(self._lib.bte_learned_indicator(self._h, _ptr(f), _ptr(Q), n, _ptr(out), _stream(stream)),
+                 "bte_learned_indicator")
+        return out
+
     def project(self, Q, inst=None, stream=None):
         _check_f64(Q, "Q")
         arr, n = self._inst(inst, Q)
@@ -250,6 +274,11 @@ class Context:
         self._rc(self._lib.bte_batch_count(self._h, ctypes.byref(n)), "bte_batch_count")
         return n.value
 
+    def graph_count(self):
+        n = ctypes.c_int64()
+        self._rc(self._lib.bte_graph_count(self._h, ctypes.byref(n)), "bte_graph_count")
+        return n.value
+
     def set_option(self, name, value):
         self._rc(self._lib.bte_set_option(self._h, name.encode(), int(value)), "bte_set_option")
 
@@ -290,6 +319,16 @@ class Context:
 
     def mlp_set_scales(self, s_in, s_out):
         self._rc(self._lib.bte_mlp_set_scales(self._h, float(s_in), float(s_out)), "bte_mlp_set_scales")
+
+    def mlp_fit_scales(self, f, Q, s_in=10.0, stream=None):
+        """Set s_in and the s_out that makes the targets s_out Q / rho^2 of (f, Q) unit-RMS."""
+        _check_f64(f, "f")
+        _check_f64(Q, "Q")
+        n = f.numel() // self.mlp_info()["ndim"]
+        so = ctypes.c_double()
+        self._rc(self._lib.bte_mlp_fit_scales(self._h, _ptr(f), _ptr(Q), n, float(s_in), ctypes.byref(so),
+                                              _stream(stream)), "bte_mlp_fit_scales")
+        return so.value
 
     def mlp_get_params(self):
         import numpy as np
@@ -370,6 +409,13 @@ class Context:
         self._rc(self._lib.bte_state_load(self._h, str(path).encode(), _ptr(f), f.numel(), ctypes.byref(t),
                                           ctypes.byref(step), _stream(stream)), "bte_state_load")
         return t.value, step.value
+
+    def alu_peak(self, kind=0, stream=None):
+        """Measured FMA rate of this GPU in TFLOP/s: kind 0 FP32, 1 packed FP32x2, 2 FP64."""
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        self._rc(self._lib.bte_alu_peak(self._h, int(kind), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)),
+                 "bte_alu_peak")
+        return tf.value
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

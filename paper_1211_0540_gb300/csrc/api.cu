@@ -19,6 +19,7 @@
 namespace bte {
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr uint64_t kIndicatorSeed = 12345;  // SplitMix64 seed of the indicator's pencil sample
 
 // A batch: the instance layout of one (inst, ninst) argument, mapped onto
 // slots. Instances are grouped by weight table into segments; a segment's
@@ -93,10 +94,57 @@ bool owned_by_graph(const bte_ctx *c, cudaEvent_t ev) {
     return false;
 }
 
+// Record the context's fence on `st` after the work a call enqueued there.
+void fence_record(bte_ctx *c, cudaStream_t st) {
+    if (c->capturing) return;
+    auto it = c->fence.find(st);
+    if (it == c->fence.end()) {
+        if (c->fence.size() >= 64) {  // many streams: wait for all and start over
+            for (auto &kv : c->fence) {
+                cudaEventSynchronize(kv.second);
+                cudaEventDestroy(kv.second);
+            }
+            c->fence.clear();
+        }
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(st);  // no event: this call's work is finished instead
+            cudaGetLastError();
+            return;
+        }
+        it = c->fence.emplace(st, ev).first;
+    }
+    cudaEventRecord(it->second, st);
+}
+
+// Wait until every kernel this context has enqueued has finished (other
+// users of the device are not waited for).
+cudaError_t quiesce(bte_ctx *c) {
+    cudaError_t r = cudaSuccess;
+    for (auto &kv : c->fence) {
+        cudaError_t e = cudaEventSynchronize(kv.second);
+        if (e != cudaSuccess) r = e;
+    }
+    return r;
+}
+
+// Events of a graph that is being destroyed: those no pending profile entry
+// names go back to the pool; pending ones return when they are read.
+void release_graph_events(bte_ctx *c, const GraphRec &g) {
+    for (const ProfEntry &pe : g.prof) {
+        bool named = false;
+        for (const ProfEntry &q : c->pending)
+            if (q.a == pe.a) named = true;
+        if (!named) c->ev_free.push_back({pe.a, pe.b});
+    }
+}
+
 // Forget every captured step graph (they bake in scratch pointers, options and
-// profiling events); the next bte_step captures again. Waits for the device.
+// profiling events); the next bte_step captures again. Waits for the
+// context's own work.
 void drop_graphs(bte_ctx *c) {
-    cudaDeviceSynchronize();
+    quiesce(c);
     for (const ProfEntry &pe : c->pending)
         if (!owned_by_graph(c, pe.a)) c->ev_free.push_back({pe.a, pe.b});
     c->pending.clear();
@@ -305,7 +353,7 @@ bte_status get_batch(bte_ctx *c, const bte_instance *inst, int64_t ninst, Batch 
         auto lru = c->batches.begin();
         for (auto b = c->batches.begin(); b != c->batches.end(); ++b)
             if (b->second->last_use < lru->second->last_use) lru = b;
-        cudaError_t e = cudaDeviceSynchronize();  // kernels in flight may still read it
+        cudaError_t e = quiesce(c);  // this context's kernels in flight may still read it
         if (e != cudaSuccess) return cuda_fail(c, e, "batch eviction");
         drop_graphs(c);  // captured steps hold its device arrays
         free_batch(lru->second);
@@ -662,6 +710,20 @@ bte_status wall_table(bte_ctx *c, const Table *t, double Tw, int side, const dou
     return BTE_OK;
 }
 
+// Set-up-time configuration of what a uniform batch of table 0 runs with the
+// context's options (shared-memory attributes, launch shapes, DFT roots), so
+// that later calls -- bte_collide_noalloc in particular -- only look it up.
+bte_status prime_configs(bte_ctx *c) {
+    if (c->tables.empty()) return BTE_OK;
+    for (const Table *t : c->tables)
+        if (fused_dft_supported(t->N)) fused_dft_prepare(t->N);
+    const Table *t = c->tables[0];
+    const unsigned mask = 1u << t->kind0 | (t->ntiles > 1 ? 1u << (t->kind0 + 1) : 0u);
+    ConvLaunch L;
+    cudaError_t e = conv32_configure(mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "convolution kernel configuration");
+}
+
 bte_status check_mode(bte_ctx *c, int mode) {
     if (mode == BTE_FP64_PLAIN || mode == BTE_FP32) return BTE_OK;
     if (mode == BTE_LEARNED) {
@@ -669,6 +731,48 @@ bte_status check_mode(bte_ctx *c, int mode) {
         return BTE_OK;
     }
     return fail(c, BTE_EINVAL, "unknown mode");
+}
+
+// The indicator's sampled pencils for table 0 (built on first use).
+bte_status ensure_indicator(bte_ctx *c) {
+    if (c->ind) return BTE_OK;
+    const Table *t = c->tables[0];
+    if (t->N > 16) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
+    IndicatorTable *it = new IndicatorTable();
+    if (build_indicator_table(*t, c->learned_samples, kIndicatorSeed, *it) != 0) {
+        free_indicator_table(*it);
+        delete it;
+        return fail(c, BTE_ENOMEM, "learned mode: indicator table");
+    }
+    c->ind = it;
+    return BTE_OK;
+}
+
+// Indicator of the uniform batch B (cells of table 0): transform of f at every
+// mode, of Q at the sampled pencils, the exact sums there and the per-slot
+// ratio. *ind receives the device array (one float per slot, in SC_MISC).
+bte_status enqueue_indicator(bte_ctx *c, Batch *B, const double *f, const double *Q, float **ind, cudaStream_t st) {
+    const Segment &sg = B->segs[0];
+    const Table *t = c->tables[0];
+    bte_status s;
+    if ((s = ensure_indicator(c)) != BTE_OK) return s;
+    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * indicator_scratch_floats(*c->ind, t->N, B->nslots))) !=
+        BTE_OK)
+        return s;
+    DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
+    const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+    launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
+                             cfg_of(c, B).split);  // the batch's tuned split, else the option
+    launch_dft_forward_pencils(Q, B->d_slot_off, ds, sf, c->ind->d_kk, c->ind->S, (float2 *)c->scratch[SC_QH],
+                               c->d_status, st);  // only the sampled pencils are compared
+    float *e2 = (float *)c->scratch[SC_MISC];
+    float *d2 = e2 + (size_t)B->nslots * c->ind->S;
+    *ind = d2 + (size_t)B->nslots * c->ind->S;
+    launch_indicator(*c->ind, *t, (const float2 *)c->scratch[SC_F], (const float2 *)c->scratch[SC_QH], sg.eoff,
+                     sg.nslots, sg.nvalid, e2, d2, *ind, st);
+    count_launches(c, 4);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "indicator launch");
 }
 
 // Learned path on a uniform batch of table `mlp->table`: surrogate, projection,
@@ -680,18 +784,9 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
     Mlp *m = c->mlp;
     if (!B->uniform || B->segs.size() != 1 || m->table != 0)
         return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
-    const Segment &sg = B->segs[0];
     const Table *t = c->tables[0];
     if (t->N > 16) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
-    if (!c->ind) {
-        c->ind = new IndicatorTable();
-        if (build_indicator_table(*t, c->learned_samples, 12345, *c->ind) != 0)
-            return fail(c, BTE_ENOMEM, "learned mode: indicator table");
-    }
     bte_status s;
-    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * indicator_scratch_floats(*c->ind, t->N, B->nslots))) !=
-        BTE_OK)
-        return s;
     // 1. surrogate in chunks of up to 8192 cells, 2. its output projected (fused)
     const int64_t chunk = 8192;
     for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
@@ -708,18 +803,8 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned mode: launch");
     }
     // 3. indicator at the sampled modes
-    DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
-    const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
-    launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
-                             cfg_of(c, B).split);  // the batch's tuned split, else the option
-    launch_dft_forward_pencils(Q, B->d_slot_off, ds, sf, c->ind->d_kk, c->ind->S, (float2 *)c->scratch[SC_QH],
-                               c->d_status, st);  // only the sampled pencils are compared
-    float *e2 = (float *)c->scratch[SC_MISC];
-    float *d2 = e2 + (size_t)B->nslots * c->ind->S;
-    float *ind = d2 + (size_t)B->nslots * c->ind->S;
-    launch_indicator(*c->ind, *t, (const float2 *)c->scratch[SC_F], (const float2 *)c->scratch[SC_QH], sg.eoff,
-                     sg.nslots, sg.nvalid, e2, d2, ind, st);
-    count_launches(c, 4);
+    float *ind = nullptr;
+    if ((s = enqueue_indicator(c, B, f, Q, &ind, st)) != BTE_OK) return s;
     std::vector<float> h(B->nslots);
     cudaError_t e = cudaMemcpyAsync(h.data(), ind, sizeof(float) * B->nslots, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -780,7 +865,9 @@ bte_status bte_create(bte_ctx **ctx, int device) {
 void bte_destroy(bte_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
     drop_graphs(c);  // graph-owned events move to the free pool once, pending entries too
+    for (auto &kv : c->fence) cudaEventDestroy(kv.second);
     for (auto &ab : c->ev_free) {
         cudaEventDestroy(ab.first);
         cudaEventDestroy(ab.second);
@@ -826,7 +913,7 @@ bte_status bte_init_weights(bte_ctx *c, const bte_grid *grids, int ngrids, int *
         c->tables.push_back(t);
         // batches built before this call stay valid (they name tables by id)
     }
-    return BTE_OK;
+    return prime_configs(c);
 }
 
 bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_instance *inst, int64_t ninst,
@@ -840,9 +927,12 @@ bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_inst
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
     if ((s = prepare(c, B, mode == BTE_LEARNED ? BTE_FP32 : mode, false, false)) != BTE_OK) return s;
-    if (mode == BTE_LEARNED) return learned_collide(c, B, f, Q, ninst, flags, (cudaStream_t)stream);
-    return enqueue_collide(c, B, f, Q, mode, (flags & BTE_FLAG_RAW) ? POST_RAW : POST_PROJECT, nullptr, nullptr,
-                           nullptr, 0.0, (cudaStream_t)stream);
+    if (mode == BTE_LEARNED) s = learned_collide(c, B, f, Q, ninst, flags, (cudaStream_t)stream);
+    else
+        s = enqueue_collide(c, B, f, Q, mode, (flags & BTE_FLAG_RAW) ? POST_RAW : POST_PROJECT, nullptr, nullptr,
+                            nullptr, 0.0, (cudaStream_t)stream);
+    fence_record(c, (cudaStream_t)stream);
+    return s;
 }
 
 bte_status bte_collide(bte_ctx *c, const double *f, double *Q, const bte_instance *inst, int64_t ninst, int mode,
@@ -860,6 +950,7 @@ bte_status bte_project(bte_ctx *c, double *Q, const bte_instance *inst, int64_t 
     for (const Segment &sg : B->segs)
         launch_project(Q, B->d_slot_off, sg.s0, sg.nslots, proj_args(c->tables[sg.table]), 0, nullptr, nullptr,
                        nullptr, 0.0, (cudaStream_t)stream);
+    fence_record(c, (cudaStream_t)stream);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "projection launch");
 }
@@ -876,6 +967,7 @@ bte_status bte_moments(bte_ctx *c, const double *f, double *out, const bte_insta
         const Table *t = c->tables[sg.table];
         launch_moments(f, B->d_slot_off, sg.s0, sg.nslots, t->N, t->dv, B->d_slot_out, out, (cudaStream_t)stream);
     }
+    fence_record(c, (cudaStream_t)stream);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "moments launch");
 }
@@ -940,7 +1032,11 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "kernel launch");
     };
-    if (st == nullptr) return body();  // the legacy stream cannot be captured
+    if (st == nullptr) {  // the legacy stream cannot be captured
+        bte_status r = body();
+        fence_record(c, st);
+        return r;
+    }
     if (mode == BTE_LEARNED) return fail(c, BTE_EINVAL, "bte_step: use bte_collide for the learned mode");
     GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
                  tr ? 1 : 0, dt, eps, f, stream};
@@ -950,13 +1046,23 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
          std::memcmp(it->second.inst.data(), inst, sizeof(bte_instance) * ninst) != 0)) {
         // another instance list with the same count and hash: capture anew. A
         // replay of the old graph may still be in flight, which the driver lets
-        // finish before it frees the executable; its events stay allocated
-        // because pending profile entries may still name them.
+        // finish before it frees the executable.
         cudaGraphExecDestroy(it->second.exec);
+        release_graph_events(c, it->second);
         c->graphs.erase(it);
         it = c->graphs.end();
     }
     if (it == c->graphs.end()) {
+        // bounded cache (its key holds f and dt, which a caller may vary):
+        // the least recently replayed graph goes first
+        while ((int)c->graphs.size() >= c->graph_cache_max && !c->graphs.empty()) {
+            auto lru = c->graphs.begin();
+            for (auto g = c->graphs.begin(); g != c->graphs.end(); ++g)
+                if (g->second.last_use < lru->second.last_use) lru = g;
+            cudaGraphExecDestroy(lru->second.exec);  // an in-flight replay completes first
+            release_graph_events(c, lru->second);
+            c->graphs.erase(lru);
+        }
         prof_reserve(c, 16);
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
@@ -987,8 +1093,16 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
     }
     cudaError_t e = cudaGraphLaunch(it->second.exec, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    it->second.last_use = ++c->graph_tick;
     c->launches += it->second.launches;
     for (const ProfEntry &pe : it->second.prof) c->pending.push_back(pe);
+    fence_record(c, st);
+    return BTE_OK;
+}
+
+bte_status bte_graph_count(const bte_ctx *c, int64_t *count) {
+    if (!c || !count) return BTE_EINVAL;
+    *count = (int64_t)c->graphs.size();
     return BTE_OK;
 }
 
@@ -1053,6 +1167,7 @@ static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_merge")) { *lo = 1; *hi = 1 << 20; return &c->conv_merge; }
     if (!std::strcmp(name, "conv_split")) { *lo = 0; *hi = 1; return &c->conv_split; }
     if (!std::strcmp(name, "batch_cache")) { *lo = 2; *hi = 1 << 20; return &c->batch_cache_max; }
+    if (!std::strcmp(name, "graph_cache")) { *lo = 1; *hi = 1 << 20; return &c->graph_cache_max; }
     if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
     return nullptr;
 }
@@ -1068,7 +1183,11 @@ bte_status bte_set_option(bte_ctx *c, const char *name, int value) {
         *slot = value;
     }
     // an explicit choice of the FP32 path's configuration replaces the tuned ones
-    if (!std::strncmp(name, "conv_", 5) || !std::strcmp(name, "dft_split")) c->tuned.clear();
+    if (!std::strncmp(name, "conv_", 5) || !std::strcmp(name, "dft_split")) {
+        c->tuned.clear();
+        cudaSetDevice(c->device);
+        return prime_configs(c);
+    }
     return BTE_OK;
 }
 
@@ -1091,6 +1210,39 @@ bte_status bte_learned_stats(bte_ctx *c, int64_t *cells, int64_t *fallbacks, dou
         c->learned_max_ind = 0.0;
     }
     return BTE_OK;
+}
+
+bte_status bte_learned_sample(bte_ctx *c, int *kk, int cap, int *S) {
+    if (!c || !S) return BTE_EINVAL;
+    if (c->tables.empty()) return fail(c, BTE_ESTATE, "bte_learned_sample: no weight tables");
+    cudaSetDevice(c->device);
+    bte_status s = ensure_indicator(c);
+    if (s != BTE_OK) return s;
+    *S = c->ind->S;
+    if (kk)
+        for (int i = 0; i < c->ind->S && i < cap; ++i) kk[i] = c->ind->kks[i];
+    return BTE_OK;
+}
+
+bte_status bte_learned_indicator(bte_ctx *c, const double *f, const double *Q, int64_t ncells, double *ind,
+                                 void *stream) {
+    if (!c) return BTE_EINVAL;
+    if (!f || !Q || !ind) return fail(c, BTE_EINVAL, "bte_learned_indicator: null pointer");
+    if (c->tables.empty()) return fail(c, BTE_ESTATE, "bte_learned_indicator: no weight tables");
+    if (c->tables[0]->N > 16) return fail(c, BTE_EINVAL, "bte_learned_indicator: table 0 must have N <= 16");
+    cudaSetDevice(c->device);
+    Batch *B = nullptr;
+    bte_status s;
+    if ((s = get_batch(c, nullptr, ncells, &B)) != BTE_OK) return s;
+    if ((s = prepare(c, B, BTE_FP32, false, false)) != BTE_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *d_ind = nullptr;
+    if ((s = enqueue_indicator(c, B, f, Q, &d_ind, st)) != BTE_OK) return s;
+    launch_widen(d_ind, ind, (int)ncells, st);
+    count_launches(c, 1);
+    fence_record(c, st);
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "bte_learned_indicator: launch");
 }
 
 bte_status bte_sync_status(bte_ctx *c, void *stream) {

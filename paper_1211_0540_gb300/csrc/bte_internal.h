@@ -66,6 +66,11 @@ struct Table {
     double *d_w64 = nullptr;
     uint64_t *d_w64_off = nullptr;       // per k (M + 1 entries)
     size_t n_w64 = 0;
+    // Work items of one 32-cell group (fofs 0, table 0), every k3 tile and
+    // pencil with kept blocks, costliest first: the set-up-time template from
+    // which bte_collide_noalloc expands its work list on the device.
+    ConvItem *d_tmpl = nullptr;
+    int n_tmpl = 0;
     // DFT roots exp(2 pi i t / N), t in [0, N)
     float2 *d_root32 = nullptr;
     double2 *d_root64 = nullptr;
@@ -109,6 +114,7 @@ struct WallTable {
 };
 struct GraphRec {
     cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;        // context tick of the latest replay (least recently used is evicted first)
     std::vector<ProfEntry> prof;  // events baked into the graph
     int64_t launches = 0;         // kernels per replay
     std::vector<bte_instance> inst;  // the instance list the graph was captured for (the key holds a hash)
@@ -130,7 +136,13 @@ struct bte_ctx {
     std::map<std::string, bte::Batch *> batches;  // per instance layout, at most batch_cache_max
     int batch_cache_max = 64;
     uint64_t batch_tick = 0;
-    std::map<bte::GraphKey, bte::GraphRec> graphs;
+    std::map<bte::GraphKey, bte::GraphRec> graphs;  // at most graph_cache_max
+    int graph_cache_max = 32;
+    uint64_t graph_tick = 0;
+    // Per stream the context has enqueued work on: an event recorded after that
+    // work. Waiting on these (instead of the whole device) lets the context free
+    // or rebuild what its own kernels may still read.
+    std::map<cudaStream_t, cudaEvent_t> fence;
     // profiling / launch accounting
     bool prof = false;
     int prof_mask = 63;        // bit k: record events around ProfKernel k

@@ -24,6 +24,7 @@
 //   expiry the warp records BTE_ETIMEOUT in the status word, waits (bounded)
 //   for its own copies in flight and leaves.
 #include <map>
+#include <mutex>
 #include <tuple>
 
 #include "kernels.h"
@@ -751,10 +752,18 @@ int conv_stage_bytes(int kind) {
     }
 }
 
+namespace {
+std::recursive_mutex g_conv_cfg_mu;  // guards the caches below (contexts on several host threads)
+}  // namespace
+
 cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages, int impl,
                              ConvLaunch *out) {
-    static std::map<std::tuple<unsigned, int, int, int, int>, ConvLaunch> cache;
-    auto key = std::make_tuple(kinds_mask, num_sms, warps_per_cta, stages, impl);
+    std::lock_guard<std::recursive_mutex> lock(g_conv_cfg_mu);
+    // keyed by device too: the shared-memory attribute is set per device
+    static std::map<std::tuple<int, unsigned, int, int, int, int>, ConvLaunch> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto key = std::make_tuple(dev, kinds_mask, num_sms, warps_per_cta, stages, impl);
     auto itc = cache.find(key);
     if (itc != cache.end()) {
         *out = itc->second;
@@ -813,8 +822,8 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     }
     // the attribute belongs to the function and is shared by every cached
     // configuration of it: only ever raise it
-    static std::map<void *, size_t> fn_smem;
-    size_t &cur = fn_smem[(void *)L.fn];
+    static std::map<std::pair<int, void *>, size_t> fn_smem;
+    size_t &cur = fn_smem[std::make_pair(dev, (void *)L.fn)];
     if (L.smem > cur) {
         cudaError_t e0 = cudaFuncSetAttribute(L.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
         if (e0 != cudaSuccess) return e0;

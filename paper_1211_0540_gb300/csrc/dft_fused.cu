@@ -24,6 +24,7 @@
 
 #include <cmath>
 #include <map>
+#include <mutex>
 
 #include "fft_reg.cuh"
 #include "fpconv.cuh"
@@ -491,6 +492,8 @@ void fused_dft_prepare(int N) {
     // roots of unity (constant memory is per device) and shared-memory
     // attributes; must happen outside stream capture
     static std::map<int, unsigned> done;  // device -> bit N of the uploaded root tables
+    static std::mutex mu;                   // contexts on several host threads share the map
+    std::lock_guard<std::mutex> lock(mu);
     int dev = 0;
     cudaGetDevice(&dev);
     if (N < 0 || N > 32 || (done[dev] >> N) & 1u) return;

@@ -12,12 +12,12 @@
 // N^2 pencils of the convolution (4 / 256 = 1.6 % at N = 16).
 #include <algorithm>
 #include <cmath>
-#include <random>
 #include <vector>
 
 #include "learned.h"
 #include "fpconv.cuh"
 #include "project.cuh"
+#include "rng.h"
 
 namespace bte {
 
@@ -240,18 +240,33 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
     }
 }
 
+// ind (one float per slot of a uniform batch, slot = cell) to the caller's doubles.
+__global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)in[i];
+}
+
 }  // namespace
+
+void launch_widen(const float *in, double *out, int n, cudaStream_t st) {
+    if (n > 0) widen_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+}
 
 int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTable &out) {
     const int N = t.N, h = N / 2, q = N / 4;
     const int S = std::max(1, modes / N);
     const double dz3 = t.dz * t.dz * t.dz;
     const double c = std::sqrt(2.0 / 3.14159265358979323846);
-    std::mt19937_64 rng(seed);
-    std::uniform_int_distribution<int> d(-q, q);
+    // SplitMix64 from `seed`; each pencil offset is (next mod (2q + 1)) - q,
+    // k1' first; repeated pencils are skipped. Integer arithmetic only, so
+    // every platform draws the same sample.
+    SplitMix64 rng(seed);
+    const uint64_t span = (uint64_t)(2 * q + 1);
     std::vector<int> kks;
     while ((int)kks.size() < S) {
-        const int kk = (d(rng) + h) * N + (d(rng) + h);
+        const int k1 = (int)(rng.next() % span) - q;
+        const int k2 = (int)(rng.next() % span) - q;
+        const int kk = (k1 + h) * N + (k2 + h);
         if (std::find(kks.begin(), kks.end(), kk) == kks.end()) kks.push_back(kk);
     }
     // loss weights of the sampled pencils in the FP32 table's block layout (one k3 tile, N <= 16)
@@ -294,6 +309,7 @@ int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTab
         pens.push_back(pn);
     }
     out.S = S;
+    out.kks = kks;
     cudaError_t e = cudaMalloc(&out.d_wloss, sizeof(float) * std::max<size_t>(wl.size(), 4));
     if (e == cudaSuccess) e = cudaMalloc(&out.d_pen, sizeof(IndPencil) * S);
     if (e == cudaSuccess) e = cudaMemcpy(out.d_wloss, wl.data(), sizeof(float) * wl.size(), cudaMemcpyHostToDevice);

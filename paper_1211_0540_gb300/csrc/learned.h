@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 
 #include "kernels.h"
 
@@ -17,6 +18,7 @@ struct IndPencil {
 
 struct IndicatorTable {
     int S = 0;                     // sampled pencils (S x N sampled modes)
+    std::vector<int> kks;          // host copy of the sampled pencils (k1 N + k2), drawing order
     float *d_wloss = nullptr;      // loss weights of the sampled pencils (pair-symmetrised, times dz^3)
     IndPencil *d_pen = nullptr;
     int *d_kk = nullptr;           // the sampled pencils' k1 N + k2
@@ -32,6 +34,8 @@ void launch_post_project(const float *Y, const double *rho, int B, int N, float 
 // err2, den2: S * nslots floats of scratch each, ind: nslots floats followed by
 // the kernel's own scratch (indicator_scratch_floats counts all of it).
 size_t indicator_scratch_floats(const IndicatorTable &it, int N, int nslots);
+// out[i] = (double) in[i], i < n
+void launch_widen(const float *in, double *out, int n, cudaStream_t st);
 void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
                       int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st);
 

@@ -14,7 +14,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <random>
 #include <string>
 #include <utility>
 #include <vector>
@@ -23,6 +22,7 @@
 #include "mlp.h"
 #include "fpconv.cuh"
 #include "project.cuh"
+#include "rng.h"
 
 namespace bte {
 
@@ -83,6 +83,34 @@ __global__ void __launch_bounds__(kT) prep_kernel(const double *__restrict__ f, 
         const double c = (double)s_out / (rho * rho);
         const double *qr = Q + off[r];
         for (int j = threadIdx.x; j < M; j += blockDim.x) T[(size_t)r * M + j] = (float)(qr[j] * c);
+    }
+}
+
+// Per cell of a uniform array: rho = sum f dv^3 and sum_j Q_j^2 / rho^4 (the
+// squared norm of the cell's unscaled target Q / rho^2), FP64 in a fixed order.
+__global__ void __launch_bounds__(kT) target_norm_kernel(const double *__restrict__ f, const double *__restrict__ Q,
+                                                         int64_t M, double dv3, double *out) {
+    const int64_t r = blockIdx.x;
+    const double *fr = f + r * M, *qr = Q + r * M;
+    __shared__ double sf[kT], sq[kT];
+    double a = 0.0, b = 0.0;
+    for (int64_t j = threadIdx.x; j < M; j += kT) {
+        a += fr[j];
+        b = fma(qr[j], qr[j], b);
+    }
+    sf[threadIdx.x] = a;
+    sq[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sf[threadIdx.x] += sf[threadIdx.x + w];
+            sq[threadIdx.x] += sq[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double rho = sf[0] * dv3;
+        out[r] = sq[0] / (rho * rho * rho * rho);
     }
 }
 
@@ -392,10 +420,9 @@ bte_status bte_mlp_init(bte_ctx *c, int table, int width, uint64_t seed) {
     }
     // He-style initialisation (host, seeded), zero biases, zero Adam state
     std::vector<float> h(P, 0.0f);
-    std::mt19937_64 rng(seed);
+    SplitMix64 rng(seed);
     auto fill = [&](size_t off, int rows, int cols, float sd) {
-        std::normal_distribution<float> nd(0.0f, sd);
-        for (size_t i = 0; i < (size_t)rows * cols; ++i) h[off + i] = nd(rng);
+        for (size_t i = 0; i < (size_t)rows * cols; ++i) h[off + i] = (float)(sd * rng.normal());
     };
     fill(m->off_W1(), m->H, m->M, std::sqrt(2.0f / m->M));
     fill(m->off_W2(), m->H, m->H, std::sqrt(1.0f / m->H));
@@ -431,6 +458,33 @@ bte_status bte_mlp_set_scales(bte_ctx *c, double s_in, double s_out) {
     if (!(s_in > 0) || !(s_out > 0)) return mlp_fail(c, BTE_EINVAL, "bte_mlp_set_scales: scales must be > 0");
     c->mlp->s_in = (float)s_in;
     c->mlp->s_out = (float)s_out;
+    return BTE_OK;
+}
+
+bte_status bte_mlp_fit_scales(bte_ctx *c, const double *f, const double *Q, int64_t n, double s_in, double *s_out,
+                              void *stream) {
+    bte_status s = need_mlp(c);
+    if (s != BTE_OK) return s;
+    if (!f || !Q || n < 1 || n > (1 << 30) || !(s_in > 0))
+        return mlp_fail(c, BTE_EINVAL, "bte_mlp_fit_scales: bad arguments");
+    cudaSetDevice(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *d = nullptr;
+    if (cudaMalloc(&d, sizeof(double) * (size_t)n) != cudaSuccess)
+        return mlp_fail(c, BTE_ENOMEM, "bte_mlp_fit_scales: scratch");
+    target_norm_kernel<<<(unsigned)n, kT, 0, st>>>(f, Q, c->mlp->M, c->mlp->dv3, d);
+    std::vector<double> h((size_t)n);
+    cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return mlp_fail(c, BTE_ECUDA, "bte_mlp_fit_scales: reduction");
+    double sum = 0.0;
+    for (double v : h) sum += v;  // fixed order: the same scale on every run
+    const double ms = sum / ((double)n * c->mlp->M);
+    if (!(ms > 0.0) || !std::isfinite(ms)) return mlp_fail(c, BTE_EINVAL, "bte_mlp_fit_scales: targets are zero or not finite");
+    c->mlp->s_in = (float)s_in;
+    c->mlp->s_out = (float)(1.0 / std::sqrt(ms));
+    if (s_out) *s_out = c->mlp->s_out;
     return BTE_OK;
 }
 
@@ -491,7 +545,7 @@ bte_status bte_mlp_train(bte_ctx *c, const double *f, const double *Q, int64_t n
     cudaSetDevice(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (!m->ensure_batch(batch)) return mlp_fail(c, BTE_ENOMEM, "bte_mlp_train: activations");
-    std::mt19937_64 rng(seed);
+    SplitMix64 rng(seed);
     std::vector<int64_t> perm(nsamples), rows(nsamples);
     for (int64_t i = 0; i < nsamples; ++i) perm[i] = i;
     const int64_t steps_per_epoch = nsamples / batch;
@@ -507,7 +561,7 @@ bte_status bte_mlp_train(bte_ctx *c, const double *f, const double *Q, int64_t n
         ~Free() { cudaFree(p); }
     } free_rows{d_rows};
     for (int e = 0; e < epochs; ++e) {
-        std::shuffle(perm.begin(), perm.end(), rng);
+        rng.shuffle(perm);
         for (int64_t i = 0; i < nsamples; ++i) rows[i] = perm[i] * m->M;
         // one upload per epoch; the stream orders it after the previous epoch's steps
         if (cudaMemcpyAsync(d_rows, rows.data(), sizeof(int64_t) * nsamples, cudaMemcpyHostToDevice, st) !=

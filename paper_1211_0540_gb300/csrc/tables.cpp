@@ -229,9 +229,38 @@ int build_table(Table &t, std::string &err) {
         r64[s] = make_double2(c, sn);
     }
 
+    // one group's work items, costliest first (stable, so ties keep (tile, k1, k2) order)
+    std::vector<ConvItem> tmpl;
+    std::vector<uint64_t> tcost;
+    for (int tile = 0; tile < t.ntiles; ++tile)
+        for (int kk = 0; kk < N * N; ++kk) {
+            if (t.nblocks[kk] == 0) continue;
+            ConvItem ci{};
+            ci.fofs = 0;
+            ci.wofs = t.wofs[(size_t)tile * N * N + kk];
+            ci.desc_off = t.desc_off[kk];
+            ci.nblocks = t.nblocks[kk];
+            ci.k1 = (uint16_t)(kk / N);
+            ci.k2 = (uint16_t)(kk % N);
+            ci.kind = (uint16_t)(t.kind0 + tile);
+            ci.table = 0;
+            tmpl.push_back(ci);
+            tcost.push_back((uint64_t)ci.nblocks * t.cpad[tile]);
+        }
+    {
+        std::vector<size_t> ord(tmpl.size());
+        for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return tcost[a] > tcost[b]; });
+        std::vector<ConvItem> sorted(tmpl.size());
+        for (size_t i = 0; i < ord.size(); ++i) sorted[i] = tmpl[ord[i]];
+        tmpl.swap(sorted);
+    }
+    t.n_tmpl = (int)tmpl.size();
+
     // upload
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&t.d_w32, sizeof(float) * std::max<size_t>(total, 4));
+    if (e == cudaSuccess) e = cudaMalloc(&t.d_tmpl, sizeof(ConvItem) * std::max<size_t>(tmpl.size(), 1));
     if (e == cudaSuccess) e = cudaMalloc(&t.d_desc, sizeof(uint32_t) * std::max<size_t>(t.n_desc, 1));
     if (e == cudaSuccess) e = cudaMalloc(&t.d_root32, sizeof(float2) * N);
     if (e == cudaSuccess) e = cudaMalloc(&t.d_root64, sizeof(double2) * N);
@@ -241,6 +270,8 @@ int build_table(Table &t, std::string &err) {
         return BTE_ENOMEM;
     }
     e = cudaMemcpy(t.d_w32, w32.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tmpl.empty())
+        e = cudaMemcpy(t.d_tmpl, tmpl.data(), sizeof(ConvItem) * tmpl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(t.d_desc, desc.data(), sizeof(uint32_t) * t.n_desc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t.d_root32, r32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
@@ -298,6 +329,8 @@ int build_table_fp64(Table &t, std::string &err) {
 
 void free_table(Table &t) {
     cudaFree(t.d_w32);
+    cudaFree(t.d_tmpl);
+    t.d_tmpl = nullptr;
     cudaFree(t.d_desc);
     cudaFree(t.d_w64);
     cudaFree(t.d_w64_off);

@@ -45,18 +45,9 @@ def make_training_set(ctx, N, L, n_states, seed, relax_fraction=0.4, dt=0.05, ma
     return f, Q
 
 
-def target_scale(f, Q, N, L):
-    """s_out making the training targets s_out Q / rho^2 unit-RMS."""
-    import torch
-    M = N ** 3
-    dv3 = (2.0 * L / N) ** 3
-    rho = f.view(-1, M).sum(dim=1) * dv3
-    t = Q.view(-1, M) / (rho ** 2)[:, None]
-    return float(1.0 / torch.sqrt(torch.mean(t * t)))
-
-
 def train(ctx, f, Q, N, L, epochs=20, batch=1024, lr=1e-3, weight_decay=0.0, seed=0, s_in=10.0):
-    ctx.mlp_set_scales(s_in, target_scale(f, Q, N, L))
+    """Scales fitted by the library (unit-RMS targets), then AdamW training."""
+    ctx.mlp_fit_scales(f, Q, s_in)
     return ctx.mlp_train(f, Q, epochs=epochs, batch=batch, lr=lr, weight_decay=weight_decay, seed=seed)
 
 

@@ -127,3 +127,24 @@ def test_learned_mode_projection_and_fallback():
     C = dv3 * np.stack([np.ones(N ** 3), v1.ravel(), v2.ravel(), v3.ravel(), (v1 ** 2 + v2 ** 2 + v3 ** 2).ravel()])
     assert np.all(np.abs(m) <= 1e-12 * (np.abs(Q1) @ np.abs(C).T))
     c.close()
+
+
+def test_fit_scales_matches_numpy():
+    """bte_mlp_fit_scales: s_out = 1 / sqrt(mean (Q / rho^2)^2), rho = sum f dv^3."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_0540_gb300 import bte
+    N = 8
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.mlp_init(0, 128, seed=1)
+    f = inputs.training_states(N, L, 300, seed=9)
+    Q = oracle.collide(N, L, 1.0, f)
+    s_out = c.mlp_fit_scales(torch.from_numpy(f).cuda(), torch.from_numpy(Q).cuda(), s_in=7.0)
+    dv3 = (2 * L / N) ** 3
+    rho = f.sum(axis=1) * dv3
+    ref = 1.0 / np.sqrt(np.mean((Q / (rho ** 2)[:, None]) ** 2))
+    info = c.mlp_info()
+    assert abs(s_out - ref) <= 1e-6 * ref and abs(info["s_out"] - ref) <= 1e-6 * ref
+    assert info["s_in"] == 7.0
+    c.close()

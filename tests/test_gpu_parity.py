@@ -123,6 +123,22 @@ def test_fp64_plain_collide_matches_oracle(bte, N, ncells, lam):
     assert err.max() <= TOL64, err.max()
 
 
+@pytest.mark.parametrize("N,ncells,nsample,lam", [(16, 40, 4, 1.0), (24, 33, 2, 0.0), (32, 33, 2, 1.0)])
+def test_fp64_plain_collide_matches_oracle_at_full_grid_sizes(bte, N, ncells, nsample, lam):
+    """The plain FP64 operator at N = 16, 24, 32 on sampled cells (the last cell of
+    the ragged second group included): its weights come from the library's host
+    closed forms (Eq. GHat_calc integrated analytically) and the oracle's from
+    Gauss-Legendre quadrature, so agreement at 1e-12 checks the tabulated
+    weights over every (zeta, xi) pair that the sampled cells use."""
+    f = inputs.precision_sweep_cells(N, L, ncells, seed=250 + N)
+    Qg = run_collide(bte, N, lam, f, bte.FP64_PLAIN)
+    rng = np.random.default_rng(N)
+    pick = np.sort(rng.choice(ncells - 1, size=nsample - 1, replace=False)).tolist() + [ncells - 1]
+    Qo = oracle.collide(N, L, lam, f[pick])
+    err = np.linalg.norm(Qg[pick] - Qo, axis=1) / loss_norm(N, lam, f[pick])
+    assert err.max() <= TOL64, err.max()
+
+
 @pytest.mark.parametrize("N", [8, 16])
 def test_zero_distribution_gives_zero_operator(bte, N):
     """f = 0: fhat = 0, Qhat = 0, every moment 0, so Q is exactly 0 in both paths."""
@@ -209,6 +225,44 @@ def test_uneven_batch_matches_oracle(bte):
     assert np.all(Qg[mask] == 7.0)
 
 
+def test_uneven_batch_with_all_grid_sizes_matches_oracle(bte):
+    """One launch over instances of N = 12, 16, 24 and 32 (both k3 tiles of the
+    two larger grids, lambda 0 and 1), in shuffled order with gaps."""
+    grids = ((12, L, 0.0), (16, L, 1.0), (24, L, 1.0), (32, L, 0.0))
+    c = ctx_for(bte, grids)
+    kinds = [0, 1, 2, 3, 0, 1, 2, 3, 0, 1, 2]
+    rng = np.random.default_rng(17)
+    rng.shuffle(kinds)
+    inst, chunks = [], []
+    off = 0
+    for i, t in enumerate(kinds):
+        N = grids[t][0]
+        f = inputs.precision_sweep_cells(N, L, 1, seed=1100 + i)[0]
+        off += int(rng.integers(0, 3)) * 16
+        inst.append((t, off))
+        chunks.append((off, f))
+        off += N ** 3
+    buf = np.zeros(off)
+    for o, f in chunks:
+        buf[o:o + f.size] = f
+    Qt = torch.full_like(torch.from_numpy(buf), 3.0).cuda()
+    c.collide(torch.from_numpy(buf).cuda(), Qt, inst=inst, mode=bte.FP32)
+    c.sync_status()
+    Qg = Qt.cpu().numpy()
+    for t in range(4):
+        N, _, lam = grids[t]
+        idx = [k for k in range(len(inst)) if kinds[k] == t]
+        f = np.stack([chunks[k][1] for k in idx])
+        got = np.stack([Qg[inst[k][1]:inst[k][1] + N ** 3] for k in idx])
+        err = np.linalg.norm(got - oracle.collide(N, L, lam, f), axis=1) / loss_norm(N, lam, f)
+        assert err.max() <= TOL32, (N, err.max())
+        assert np.all(np.abs(oracle.moments(N, L, got)) <= 1e-12 * abs_moment_scale(N, got))
+    mask = np.ones(off, bool)
+    for o, f in chunks:
+        mask[o:o + f.size] = False
+    assert np.all(Qg[mask] == 3.0)
+
+
 def test_batch_cache_evicts_least_recently_used(bte):
     """At most "batch_cache" instance layouts are kept; a layout beyond that
     evicts the least recently used one, and an evicted layout used again is
@@ -278,6 +332,33 @@ def test_strang_step_with_walls_matches_oracle(bte):
         assert d <= tol, (mode, d)
         dv3 = (2 * L / N) ** 3
         assert abs(ft.cpu().numpy().sum() - f.sum()) * dv3 <= 1e-12 * f.sum() * dv3
+
+
+def test_strang_steps_at_the_benchmark_shape_match_oracle(bte):
+    """Three Strang steps of the wall-heating slab as the benchmark runs it:
+    N = 16, 128 cells, diffuse wall at T = 2 on the left, specular on the right,
+    Kn = 0.1, dt = CFL 0.5; both paths against the oracle's trajectory."""
+    N, nx, lam = 16, 128, 1.0
+    f = inputs.wall_heating_initial(N, L, nx)
+    dt, eps = 0.5 * (1.0 / nx) / L, 0.1
+    kw = dict(x0=0.0, x1=1.0, bc_left=oracle.BC_DIFFUSE, bc_right=oracle.BC_SPECULAR, Tw_left=2.0, Tw_right=1.0)
+    ref = f.copy()
+    for _ in range(3):
+        ref = oracle.strang_step(N, L, lam, ref, dt, eps, **kw)
+    c = ctx_for(bte, ((N, L, lam),))
+    s = torch.cuda.Stream()
+    for mode, tol in ((bte.FP64_PLAIN, 1e-13), (bte.FP32, 1e-7)):
+        ft = torch.from_numpy(f.copy()).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                c.step(ft, dt, eps, transport=dict(nx=nx, **kw), mode=mode, stream=s)
+        c.sync_status(s)
+        got = ft.cpu().numpy()
+        d = np.abs(got - ref).max() / np.abs(f).max()
+        assert d <= tol, (mode, d)
+        dv3 = (2 * L / N) ** 3
+        assert abs(got.sum() - f.sum()) * dv3 <= 1e-12 * f.sum() * dv3
 
 
 def test_nonfinite_input_is_reported(bte):
@@ -545,3 +626,62 @@ def test_checkpoint_resume_is_bitwise(bte, tmp_path):
     assert err.value.code == -6
     for x in (a, c, d):
         x.close()
+
+
+def test_step_graph_cache_is_bounded(bte):
+    """bte_step captures one graph per (dt, f, stream, ...); with "graph_cache" 3
+    a run whose dt changes every step keeps at most 3, and every step still
+    matches the oracle's Heun step."""
+    N, lam = 8, 1.0
+    c = bte.Context(0)
+    c.init_weights([(N, L, lam)])
+    c.set_option("graph_cache", 3)
+    f = inputs.homogeneous_cells(N, L, 33, seed=81)
+    ft = torch.from_numpy(f.copy()).cuda()
+    ref = f.copy()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for k, dt in enumerate((0.01, 0.011, 0.012, 0.013, 0.014, 0.01, 0.015)):
+        with torch.cuda.stream(s):
+            c.step(ft, dt, 1.0, mode=bte.FP64_PLAIN, stream=s)
+        ref = oracle.rk2_homogeneous(N, L, lam, ref, dt, 1.0)
+        assert c.graph_count() <= 3
+    c.sync_status(s)
+    assert np.abs(ft.cpu().numpy() - ref).max() <= 1e-13 * np.abs(f).max()
+    c.close()
+
+
+def test_contexts_on_two_host_threads(bte):
+    """Two contexts used at the same time from two host threads (the library's
+    process-wide configuration caches are locked): both match the oracle."""
+    import threading
+    N, lam = 12, 1.0
+    f = inputs.homogeneous_cells(N, L, 40, seed=91)
+    Qo = oracle.collide(N, L, lam, f)
+    norm = loss_norm(N, lam, f)
+    errs = [None, None]
+
+    def work(i):
+        try:
+            c = bte.Context(0)
+            c.init_weights([(N, L, lam)])
+            c.set_option("conv_warps", 3 + i)
+            s = torch.cuda.Stream()
+            ft = torch.from_numpy(f).cuda()
+            out = None
+            for _ in range(5):
+                out = c.collide(ft, mode=bte.FP32, stream=s)
+            c.sync_status(s)
+            errs[i] = (np.linalg.norm(out.cpu().numpy() - Qo, axis=1) / norm).max()
+            c.close()
+        except Exception as e:  # reported below
+            errs[i] = e
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for e in errs:
+        assert not isinstance(e, Exception), e
+        assert e is not None and e <= TOL32, e
