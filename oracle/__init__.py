@@ -21,7 +21,7 @@ __all__ = [
     "lib", "gauss_legendre", "sinc", "radial_I", "radial_J", "ghat_pair", "weights",
     "ghat_dense", "dft_forward_direct", "dft_forward", "dft_inverse", "convolve",
     "convolve_dense", "moments", "project", "collide", "rk2_homogeneous", "transport",
-    "strang_step", "BC_DIFFUSE", "BC_SPECULAR", "set_threads", "get_threads",
+    "strang_step", "BC_DIFFUSE", "BC_SPECULAR", "set_threads", "get_threads", "weights_beta",
 ]
 
 BC_DIFFUSE = 0
@@ -42,6 +42,10 @@ PINS = {
     "rk2_homogeneous": "explicit Heun stages; conservation over 20 steps; second order in dt "
                        "(successive differences shrink by ~4 per halving)",
     "transport": "constant state, exact mass balance at the walls, second-order convergence",
+    "weights_beta / collide(beta)": "beta = 1 reproduces the elastic tables; weak-form brute force with the "
+                                    "inelastic rule; energy dissipation -beta(1-beta)(rho E - |P|^2) for "
+                                    "Maxwell molecules and its hard-sphere Maxwellian value, converging in N",
+    "project(rows=4)": "CQ = 0 on the kept rows, idempotence, numpy lstsq on the 4 rows",
     "learned.indicator_pencils": "SplitMix64 published test vector; range and distinctness",
     "learned.learned_indicator": "numpy FFT + dense-weight gather evaluation; scale invariance",
 }
@@ -81,6 +85,12 @@ def lib():
         "ora_rk2_homogeneous": (None, [i, d, i, p, p, d, d, p]),
         "ora_transport": (None, [i, d, i, d, d, i, i, d, d, d, p]),
         "ora_strang_step": (None, [i, d, i, d, d, i, i, d, d, p, p, d, d, p]),
+        "ora_project_rows": (None, [i, d, i, i, p]),
+        "ora_weights_sizes_beta": (None, [i, p, p]),
+        "ora_weights_build_beta": (i, [i, d, d, d, p, p]),
+        "ora_convolve_beta": (None, [i, d, i, p, p, i, p, p]),
+        "ora_collide_beta": (None, [i, d, i, p, p, i, i, i, p, p, p, p]),
+        "ora_rk2_homogeneous_beta": (None, [i, d, i, p, p, i, d, d, p]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -148,7 +158,30 @@ class Weights:
             raise ValueError("oracle: bad grid (N must be even and >= 2, L > 0)")
 
 
+class WeightsBeta:
+    """Inelastic weights (restitution parameter beta, Sec. 2.2): gain integrals on
+    the invariants (|k'|^2, |m'|^2, k'.m'), loss integrals on |m'|^2 (N <= 16)."""
+
+    def __init__(self, N, L, lam, beta):
+        np_, nt = ctypes.c_int(), ctypes.c_int()
+        lib().ora_weights_sizes_beta(int(N), ctypes.byref(np_), ctypes.byref(nt))
+        self.N, self.L, self.lam, self.beta = int(N), float(L), float(lam), float(beta)
+        self.I3 = np.zeros(np_.value * np_.value * nt.value)
+        self.J = np.zeros(np_.value)
+        rc = lib().ora_weights_build_beta(self.N, self.L, self.lam, self.beta, _p(self.I3), _p(self.J))
+        if rc != 0:
+            raise ValueError("oracle: bad inelastic grid (N even, 2 <= N <= 16, L > 0, 0 < beta <= 1)")
+
+
 _weights_cache = {}
+_weights_beta_cache = {}
+
+
+def weights_beta(N, L, lam, beta):
+    key = (int(N), float(L), float(lam), float(beta))
+    if key not in _weights_beta_cache:
+        _weights_beta_cache[key] = WeightsBeta(N, L, lam, beta)
+    return _weights_beta_cache[key]
 
 
 def weights(N, L, lam):
@@ -201,11 +234,17 @@ def dft_inverse(N, L, qh):
     return out, ratio
 
 
-def convolve(N, L, lam, fh, part=0):
-    """Qhat_k = dz^3 sum_m Ghat(xi_m, zeta_k) fhat_m fhat_{k-m+N/2} (Sec. 3.2)."""
+def convolve(N, L, lam, fh, part=0, beta=1.0):
+    """Qhat_k = dz^3 sum_m Ghat(xi_m, zeta_k) fhat_m fhat_{k-m+N/2} (Sec. 3.2);
+    beta != 1: the inelastic weights (Sec. 2.2, Eq. GHat_calc with beta)."""
     fh = np.ascontiguousarray(fh, dtype=np.complex128).reshape(-1, N ** 3)
-    w = weights(N, L, lam)
     out = np.zeros(fh.shape, dtype=np.complex128)
+    if float(beta) != 1.0:
+        w = weights_beta(N, L, lam, beta)
+        lib().ora_convolve_beta(int(N), float(L), fh.shape[0], _p(w.I3), _p(w.J), int(part),
+                                _p(fh.view(np.float64)), _p(out.view(np.float64)))
+        return out
+    w = weights(N, L, lam)
     lib().ora_convolve(int(N), float(L), fh.shape[0], _p(w.I), _p(w.J), int(part),
                        _p(fh.view(np.float64)), _p(out.view(np.float64)))
     return out
@@ -228,31 +267,43 @@ def moments(N, L, f):
     return out
 
 
-def project(N, L, Q):
-    """P_N Q = Q - C^T (C C^T)^{-1} C Q per cell (Sec. 3.3; sign reading)."""
+def project(N, L, Q, rows=5):
+    """P_N Q = Q - C^T (C C^T)^{-1} C Q per cell (Sec. 3.3; sign reading), with the
+    first `rows` rows of C: 5 = mass, momentum, energy; 4 = mass and momentum."""
     q2, nc = _cells(Q, N)
     q2 = q2.copy()
-    lib().ora_project(int(N), float(L), nc, _p(q2))
+    lib().ora_project_rows(int(N), float(L), nc, int(rows), _p(q2))
     return q2
 
 
-def collide(N, L, lam, f, part=0, project=True, want_raw=False):
-    """Q = P_N Qt(f) per cell. Returns Q (and Qt, imag ratio if want_raw)."""
+def collide(N, L, lam, f, part=0, project=True, want_raw=False, beta=1.0):
+    """Q = P_N Qt(f) per cell. Returns Q (and Qt, imag ratio if want_raw).
+    beta != 1: inelastic weights, projection on mass and momentum only (Sec. 3.3)."""
     f2, nc = _cells(f, N)
-    w = weights(N, L, lam)
     Q = np.zeros_like(f2)
     raw = np.zeros_like(f2)
     ratio = np.zeros(nc)
-    lib().ora_collide(int(N), float(L), nc, _p(w.I), _p(w.J), int(part), int(bool(project)),
-                      _p(f2), _p(Q), _p(raw), _p(ratio))
+    if float(beta) != 1.0:
+        w = weights_beta(N, L, lam, beta)
+        lib().ora_collide_beta(int(N), float(L), nc, _p(w.I3), _p(w.J), int(part), 4, int(bool(project)),
+                               _p(f2), _p(Q), _p(raw), _p(ratio))
+    else:
+        w = weights(N, L, lam)
+        lib().ora_collide(int(N), float(L), nc, _p(w.I), _p(w.J), int(part), int(bool(project)),
+                          _p(f2), _p(Q), _p(raw), _p(ratio))
     if want_raw:
         return Q, raw, ratio
     return Q
 
 
-def rk2_homogeneous(N, L, lam, f, dt, eps=1.0):
+def rk2_homogeneous(N, L, lam, f, dt, eps=1.0, beta=1.0):
     f2, nc = _cells(f, N)
     f2 = f2.copy()
+    if float(beta) != 1.0:
+        w = weights_beta(N, L, lam, beta)
+        lib().ora_rk2_homogeneous_beta(int(N), float(L), nc, _p(w.I3), _p(w.J), 4, float(dt), float(eps),
+                                       _p(f2))
+        return f2
     w = weights(N, L, lam)
     lib().ora_rk2_homogeneous(int(N), float(L), nc, _p(w.I), _p(w.J), float(dt), float(eps),
                               _p(f2))

@@ -494,40 +494,44 @@ void ora_moments(int N, double L, int ncells, const double *f, double *mom) {
     }
 }
 
-/* Solve the SPD 5x5 system A x = b by Cholesky (A is overwritten). */
-static void ora_chol5(double A[5][5], double *b) {
-    for (int j = 0; j < 5; ++j) {
+/* Solve the SPD n x n system A x = b (n <= 5) by Cholesky (A is overwritten). */
+static void ora_chol(int n, double A[5][5], double *b) {
+    for (int j = 0; j < n; ++j) {
         double d = A[j][j];
         for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
         A[j][j] = sqrt(d);
-        for (int i = j + 1; i < 5; ++i) {
+        for (int i = j + 1; i < n; ++i) {
             double s = A[i][j];
             for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
             A[i][j] = s / A[j][j];
         }
     }
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < n; ++i) {
         double s = b[i];
         for (int k = 0; k < i; ++k) s -= A[i][k] * b[k];
         b[i] = s / A[i][i];
     }
-    for (int i = 4; i >= 0; --i) {
+    for (int i = n - 1; i >= 0; --i) {
         double s = b[i];
-        for (int k = i + 1; k < 5; ++k) s -= A[k][i] * b[k];
+        for (int k = i + 1; k < n; ++k) s -= A[k][i] * b[k];
         b[i] = s / A[i][i];
     }
 }
 
-/* Q <- Q - C^T (C C^T)^{-1} C Q, in place, followed by one refinement pass
- * (the same correction applied to the corrected Q). */
-void ora_project(int N, double L, int ncells, double *Q) {
+/* Q <- Q - C^T (C C^T)^{-1} C Q with the first nrows rows of C, in place,
+ * followed by one refinement pass (the same correction applied to the
+ * corrected Q). nrows = 5: mass, momentum and energy (elastic collisions);
+ * nrows = 4: mass and momentum only (inelastic collisions do not conserve
+ * energy, Sec. 3.3). */
+void ora_project_rows(int N, double L, int ncells, int nrows, double *Q) {
     int M = N * N * N;
+    if (nrows < 1 || nrows > 5) return;
     double A0[5][5] = {{0}};
     double col[5];
     for (int j = 0; j < M; ++j) {
         ora_c_column(N, L, j, col);
-        for (int a = 0; a < 5; ++a)
-            for (int b = 0; b < 5; ++b) A0[a][b] += col[a] * col[b];
+        for (int a = 0; a < nrows; ++a)
+            for (int b = 0; b < nrows; ++b) A0[a][b] += col[a] * col[b];
     }
 #pragma omp parallel for schedule(static)
     for (int cidx = 0; cidx < ncells; ++cidx) {
@@ -536,20 +540,23 @@ void ora_project(int N, double L, int ncells, double *Q) {
             double mu[5] = {0, 0, 0, 0, 0}, c5[5];
             for (int j = 0; j < M; ++j) {
                 ora_c_column(N, L, j, c5);
-                for (int i = 0; i < 5; ++i) mu[i] += c5[i] * q[j];
+                for (int i = 0; i < nrows; ++i) mu[i] += c5[i] * q[j];
             }
             double A[5][5];
             memcpy(A, A0, sizeof(A));
-            ora_chol5(A, mu);
+            ora_chol(nrows, A, mu);
             for (int j = 0; j < M; ++j) {
                 ora_c_column(N, L, j, c5);
                 double corr = 0.0;
-                for (int i = 0; i < 5; ++i) corr += c5[i] * mu[i];
+                for (int i = 0; i < nrows; ++i) corr += c5[i] * mu[i];
                 q[j] -= corr;
             }
         }
     }
 }
+
+/* The elastic projection: all five rows of C. */
+void ora_project(int N, double L, int ncells, double *Q) { ora_project_rows(N, L, ncells, 5, Q); }
 
 /* ------------------------------------------------------------------------ */
 /* Collision operator                                                       */
@@ -584,6 +591,146 @@ void ora_rk2_homogeneous(int N, double L, int ncells, const double *Itab, const 
     ora_collide(N, L, ncells, Itab, Jtab, 0, 1, f, q1, NULL, NULL);
     for (size_t i = 0; i < n; ++i) fs[i] = f[i] + dt / eps * q1[i];
     ora_collide(N, L, ncells, Itab, Jtab, 0, 1, fs, q2, NULL, NULL);
+    for (size_t i = 0; i < n; ++i) f[i] += 0.5 * dt / eps * (q1[i] + q2[i]);
+    free(q1);
+    free(q2);
+    free(fs);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inelastic collisions (beta in Eq. G_eqn and Eq. GHat_calc; Sec. 3.3)     */
+/* ------------------------------------------------------------------------ */
+/* The collision rule with restitution parameter beta is
+ * v' = v + (beta/2)(|u| sigma - u) (beta = 1: the elastic rule of
+ * Eq. velocity_interact), and Eq. GHat_calc keeps beta in the gain term:
+ *   Ghat = 4 pi/(2 pi)^{3/2} int_0^L r^{lam+2} [sinc(beta r |zeta|/2) sinc(r |xi - beta zeta/2|)
+ *                                              - sinc(r |xi|)] dr.
+ * On the grid the gain arguments are a = beta hz sqrt(p) and
+ * b = hz |2 m' - beta k'| = hz sqrt(4 s - 4 beta t + beta^2 p), hz = dz/2, with the
+ * integers p = |k'|^2, s = |m'|^2, t = k'.m'; so the gain integrals are
+ * tabulated on the triple (p, s, t) (only the triples some zero-extended pair
+ * uses are evaluated) and the loss integrals on s, as for beta = 1.
+ * I3[(p * np + s) * nt + t + 3h^2], np = 3h^2 + 1, nt = 6h^2 + 1 (N <= 16). */
+
+void ora_weights_sizes_beta(int N, int *np, int *nt) {
+    int h = N / 2;
+    *np = 3 * h * h + 1;
+    *nt = 6 * h * h + 1;
+}
+
+int ora_weights_build_beta(int N, double L, double lam, double beta, double *I3, double *Jtab) {
+    if (N < 2 || (N % 2) != 0 || N > 16 || L <= 0.0 || !(beta > 0.0 && beta <= 1.0)) return -1;
+    int np, nt, h = N / 2, M = N * N * N, T0 = 3 * h * h;
+    ora_weights_sizes_beta(N, &np, &nt);
+    size_t nI = (size_t)np * np * nt;
+    unsigned char *need = (unsigned char *)calloc(nI, 1);
+    if (!need) return -2;
+    for (int kk = 0; kk < M; ++kk) {
+        int k[3] = {kk / (N * N) - h, (kk / N) % N - h, kk % N - h};
+        for (int mm = 0; mm < M; ++mm) {
+            int m[3] = {mm / (N * N) - h, (mm / N) % N - h, mm % N - h};
+            int p = 0, sm = 0, t = 0, valid = 1;
+            for (int d = 0; d < 3; ++d) {
+                int n = k[d] - m[d] + h; /* grid index of zeta - xi (k, m here are k', m') */
+                if (n < 0 || n >= N) valid = 0;
+                p += k[d] * k[d];
+                sm += m[d] * m[d];
+                t += k[d] * m[d];
+            }
+            if (valid) need[((size_t)p * np + sm) * nt + (t + T0)] = 1;
+        }
+    }
+    double hz = 0.5 * ORA_PI / L;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (long long idx = 0; idx < (long long)nI; ++idx) {
+        if (!need[idx]) {
+            I3[idx] = NAN;
+            continue;
+        }
+        int t = (int)(idx % nt) - T0;
+        int sm = (int)((idx / nt) % np);
+        int p = (int)(idx / ((size_t)nt * np));
+        double a = beta * hz * sqrt((double)p);
+        double b2 = 4.0 * sm - 4.0 * beta * t + beta * beta * p; /* |2m' - beta k'|^2 >= 0 */
+        double b = hz * sqrt(b2 > 0.0 ? b2 : 0.0);
+        I3[idx] = ora_radial_I(lam, L, a, b);
+    }
+    for (int sm = 0; sm < np; ++sm) Jtab[sm] = ora_radial_J(lam, L, hz * sqrt((double)(4 * sm)));
+    free(need);
+    return 0;
+}
+
+static double ora_ghat_lookup_beta(int N, const double *I3, const double *Jtab, int part, const int *k,
+                                   const int *m) {
+    int np, nt, h = N / 2;
+    ora_weights_sizes_beta(N, &np, &nt);
+    int p = 0, sm = 0, t = 0;
+    for (int d = 0; d < 3; ++d) {
+        int kp = k[d] - h, mp = m[d] - h;
+        p += kp * kp;
+        sm += mp * mp;
+        t += kp * mp;
+    }
+    double pref = 4.0 * ORA_PI / pow(2.0 * ORA_PI, 1.5);
+    double gain = I3[((size_t)p * np + sm) * nt + (t + 3 * h * h)], loss = Jtab[sm];
+    if (part == 1) return -pref * loss;
+    if (part == 2) return pref * gain;
+    return pref * (gain - loss);
+}
+
+/* The weighted convolution of Sec. 3.2 with the inelastic weights. */
+void ora_convolve_beta(int N, double L, int ncells, const double *I3, const double *Jtab, int part,
+                       const double *fh, double *qh) {
+    int M = N * N * N, h = N / 2;
+    double dz = ORA_PI / L;
+    double w = dz * dz * dz;
+#pragma omp parallel for collapse(2) schedule(dynamic, 16)
+    for (int cidx = 0; cidx < ncells; ++cidx)
+        for (int kk = 0; kk < M; ++kk) {
+            const double *F = fh + (size_t)cidx * 2 * M;
+            int k[3] = {kk / (N * N), (kk / N) % N, kk % N};
+            double re = 0.0, im = 0.0;
+            for (int mm = 0; mm < M; ++mm) {
+                int m[3] = {mm / (N * N), (mm / N) % N, mm % N};
+                int n[3] = {k[0] - m[0] + h, k[1] - m[1] + h, k[2] - m[2] + h};
+                if (n[0] < 0 || n[0] >= N || n[1] < 0 || n[1] >= N || n[2] < 0 || n[2] >= N) continue;
+                int nn = (n[0] * N + n[1]) * N + n[2];
+                double g = ora_ghat_lookup_beta(N, I3, Jtab, part, k, m);
+                double ar = F[2 * mm], ai = F[2 * mm + 1], br = F[2 * nn], bi = F[2 * nn + 1];
+                re += g * (ar * br - ai * bi);
+                im += g * (ar * bi + ai * br);
+            }
+            qh[(size_t)cidx * 2 * M + 2 * kk] = w * re;
+            qh[(size_t)cidx * 2 * M + 2 * kk + 1] = w * im;
+        }
+}
+
+/* Q = P Qt(f) with the inelastic weights and the projection on the first
+ * nrows rows of C (4: mass and momentum). Arguments as ora_collide. */
+void ora_collide_beta(int N, double L, int ncells, const double *I3, const double *Jtab, int part, int nrows,
+                      int project, const double *f, double *Q, double *Qraw, double *imag_ratio) {
+    int M = N * N * N;
+    double *fh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
+    double *qh = (double *)malloc(sizeof(double) * 2 * (size_t)M * ncells);
+    ora_dft_forward(N, L, ncells, f, fh);
+    ora_convolve_beta(N, L, ncells, I3, Jtab, part, fh, qh);
+    ora_dft_inverse(N, L, ncells, qh, Q, imag_ratio);
+    if (Qraw) memcpy(Qraw, Q, sizeof(double) * (size_t)M * ncells);
+    if (project) ora_project_rows(N, L, ncells, nrows, Q);
+    free(fh);
+    free(qh);
+}
+
+/* Heun step of Sec. 3.1 with the inelastic operator (projection on nrows rows at each stage). */
+void ora_rk2_homogeneous_beta(int N, double L, int ncells, const double *I3, const double *Jtab, int nrows,
+                              double dt, double eps, double *f) {
+    size_t n = (size_t)N * N * N * ncells;
+    double *q1 = (double *)malloc(sizeof(double) * n);
+    double *q2 = (double *)malloc(sizeof(double) * n);
+    double *fs = (double *)malloc(sizeof(double) * n);
+    ora_collide_beta(N, L, ncells, I3, Jtab, 0, nrows, 1, f, q1, NULL, NULL);
+    for (size_t i = 0; i < n; ++i) fs[i] = f[i] + dt / eps * q1[i];
+    ora_collide_beta(N, L, ncells, I3, Jtab, 0, nrows, 1, fs, q2, NULL, NULL);
     for (size_t i = 0; i < n; ++i) f[i] += 0.5 * dt / eps * (q1[i] + q2[i]);
     free(q1);
     free(q2);

@@ -6,11 +6,13 @@
   The indicator is a ratio of FP32 sums at the sampled modes: agreement
   |ind_gpu - ind_oracle| <= 1e-5 ind_oracle + 1e-6 (the FP32 operator's own
   error is ~1e-7 of the loss-term norm).
-- Accuracy of the learned mode (the config-5 recipe at reduced training size):
-  a width-1024 surrogate trained on pairs the FP32 operator produces, run on
-  1024 cells of the wall-heating slab with the fallback at 1e-2: every cell is
+- Accuracy of the learned mode (the config-5 recipe): a width-1024 surrogate
+  trained on 200k pairs the FP32 operator produces (30 epochs), run on 1024
+  cells of the wall-heating slab with the fallback at 1e-2: every cell is
   within 1e-2 of the oracle (||Q - Q_oracle|| / ||Q_loss_oracle||) and
-  conserves mass, momentum and energy to 1e-12.
+  conserves mass, momentum and energy to 1e-12. Measured on GB300: 27 cells
+  fall back, max error 8.4e-3; the surrogate alone reaches 0.11, and its full
+  error over its indicator has median 1.08 and max 2.3.
 - Gain: on the same 1024 cells the learned mode evaluates more cells per
   second than the FP32 operator, each at its stated accuracy.
 """
@@ -100,15 +102,20 @@ def test_learned_mode_thresholds_the_indicator(bte):
 
 @pytest.fixture(scope="module")
 def trained(bte):
-    """Width-1024 surrogate at N = 16 trained on 24k operator pairs, and the
-    wall-heating slab of 1024 cells after 100 Strang steps."""
+    """Width-1024 surrogate at N = 16 trained as config 5 prescribes (200k pairs
+    the FP32 operator produces, 30 epochs), and the wall-heating slab of 1024
+    cells after 100 Strang steps."""
     from paper_1211_0540_gb300 import surrogate
     N, lam, nx = 16, 1.0, 1024
     c = bte.Context(0)
     c.init_weights([(N, L, lam)])
     c.mlp_init(0, 1024, seed=1)
-    f_tr, Q_tr = surrogate.make_training_set(c, N, L, 24576, seed=5)
-    surrogate.train(c, f_tr, Q_tr, N, L, epochs=20, batch=1024, lr=1e-3, seed=0)
+    t0 = time.perf_counter()
+    f_tr, Q_tr = surrogate.make_training_set(c, N, L, 200000, seed=5)
+    t1 = time.perf_counter()
+    loss = surrogate.train(c, f_tr, Q_tr, N, L, epochs=30, batch=1024, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    print("training set %.1f s, training %.1f s, final loss %.3e" % (t1 - t0, time.perf_counter() - t1, loss))
     del f_tr, Q_tr
     fw = torch.from_numpy(inputs.wall_heating_initial(N, L, nx)).cuda().reshape(-1)
     tr = dict(nx=nx, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=2.0, Tw_right=1.0)
@@ -127,6 +134,14 @@ def trained(bte):
 
 def test_learned_mode_is_within_1e2_of_the_oracle_on_every_cell(bte, trained):
     c, fw, f, Qo, norm = trained
+    # the surrogate alone and its indicator on every cell (how well the sample tracks the full error)
+    Qnn = c.collide(fw, mode=bte.LEARNED, fallback=False)
+    ind = c.learned_indicator(fw, Qnn).cpu().numpy()
+    e_nn = np.linalg.norm(Qnn.cpu().numpy().reshape(f.shape) - Qo, axis=1) / norm
+    r = e_nn / ind
+    print("surrogate alone: max err %.3e, median %.3e; err/indicator: max %.2f, median %.2f, "
+          "cells with err > 1e-2 and indicator <= 1e-2: %d"
+          % (e_nn.max(), np.median(e_nn), r.max(), np.median(r), int(np.sum((e_nn > 1e-2) & (ind <= 1e-2)))))
     c.set_option("learned_tol_ppm", 10000)
     c.learned_stats(reset=True)
     Q = c.collide(fw, mode=bte.LEARNED)
