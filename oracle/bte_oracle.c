@@ -118,23 +118,43 @@ double ora_sinc(double x) {
 }
 
 #define ORA_GL_PER_PANEL 16
+#define ORA_GRADE_LEVELS 12
+#define ORA_GRADE_RATIO 0.15
 
 /* Composite Gauss-Legendre rule on [0, L] whose panel count resolves the
  * highest angular frequency omega: at least 16 nodes per half period. The
- * caller frees *r and *w. Returns the node count. */
+ * first panel [0, h] is graded geometrically towards r = 0 (sub-panels
+ * [h s^(j+1), h s^j], j < 12, s = 0.15, and [0, h s^12]): for non-integer
+ * lambda the factor r^(lambda+2) is not smooth at 0, and one 16-point panel
+ * there leaves errors of ~1e-9 relative; graded, the rule reaches FP64
+ * accuracy (checked against 30-digit quadrature in the tests). The caller
+ * frees *r and *w. Returns the node count. */
 static int ora_radial_rule(double L, double omega, double **r, double **w) {
     int panels = (int)ceil(omega * L / ORA_PI) + 4;
-    int n = panels * ORA_GL_PER_PANEL;
+    int nseg = panels - 1 + ORA_GRADE_LEVELS + 1;
+    int n = nseg * ORA_GL_PER_PANEL;
     double gx[ORA_GL_PER_PANEL], gw[ORA_GL_PER_PANEL];
     ora_gauss_legendre(ORA_GL_PER_PANEL, gx, gw);
     *r = (double *)malloc(sizeof(double) * n);
     *w = (double *)malloc(sizeof(double) * n);
     double h = L / panels;
-    for (int p = 0; p < panels; ++p) {
-        double a = p * h;
-        for (int q = 0; q < ORA_GL_PER_PANEL; ++q) {
-            (*r)[p * ORA_GL_PER_PANEL + q] = a + 0.5 * h * (gx[q] + 1.0);
-            (*w)[p * ORA_GL_PER_PANEL + q] = 0.5 * h * gw[q];
+    int k = 0;
+    for (int seg = 0; seg < nseg; ++seg) {
+        double a, b;
+        if (seg < panels - 1) { /* the uniform panels [p h, (p + 1) h], p >= 1 */
+            a = (seg + 1) * h;
+            b = (seg + 2) * h;
+        } else if (seg < panels - 1 + ORA_GRADE_LEVELS) { /* graded sub-panels of [0, h] */
+            int j = seg - (panels - 1);
+            b = h * pow(ORA_GRADE_RATIO, j);
+            a = b * ORA_GRADE_RATIO;
+        } else {
+            a = 0.0;
+            b = h * pow(ORA_GRADE_RATIO, ORA_GRADE_LEVELS);
+        }
+        for (int q = 0; q < ORA_GL_PER_PANEL; ++q, ++k) {
+            (*r)[k] = a + 0.5 * (b - a) * (gx[q] + 1.0);
+            (*w)[k] = 0.5 * (b - a) * gw[q];
         }
     }
     return n;

@@ -138,3 +138,20 @@ def test_weight_table_symmetries():
         assert G[tuple(kp[perm] + h) + tuple(mp[perm] + h)] == base
         s = rng.choice([-1, 1], size=3)
         assert abs(G[tuple(s * kp + h) + tuple(s * mp + h)] - base) <= 1e-15 * abs(base) + 1e-300
+
+
+@pytest.mark.parametrize("lam", [0.1, 0.3, 0.5, 0.75])
+def test_radial_integrals_for_non_integer_lambda_match_high_precision_quadrature(lam):
+    """Sec. 2.2: for non-integer lambda the weights are a 1-D integral evaluated by
+    quadrature. Reference: mpmath's adaptive quadrature at 30 digits (64 panels);
+    the oracle's graded composite Gauss-Legendre rule must agree to FP64 level."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 30
+    for a, b in ((0.0, 0.0), (0.26, 0.26), (1.3, 4.1), (7.2, 13.9), (0.0, 5.0), (3.3, 0.2)):
+        def f(r):
+            return r ** (lam + 2) * (mpmath.sinc(a * r) if a else 1) * (mpmath.sinc(b * r) if b else 1)
+        ref = float(mpmath.quad(f, [0] + [L * i / 64 for i in range(1, 65)]))
+        got = oracle.radial_I(lam, L, a, b)
+        assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-16, (a, b, got, ref)
+        if a == 0.0:
+            assert abs(oracle.radial_J(lam, L, b) - ref) <= 1e-13 * abs(ref) + 1e-16
