@@ -72,6 +72,18 @@ typedef struct {
     double lambda;
 } bte_grid;
 
+/* A weight table's grid and collision model, with the restitution parameter
+ * beta of the collision rule v' = v + (beta/2)(|u| sigma - u) (Sec. 2.2,
+ * Eq. G_eqn / GHat_calc): beta = 1 elastic; 0 < beta < 1 inelastic (beta =
+ * (1 + e)/2 for a restitution coefficient e), whose projection conserves mass
+ * and momentum only (Sec. 3.3). */
+typedef struct {
+    int N;
+    double L;
+    double lambda;
+    double beta;
+} bte_grid_ex;
+
 typedef struct {
     int32_t table;   /* id returned by bte_init_weights                        */
     int32_t pad_;
@@ -100,15 +112,20 @@ void bte_destroy(bte_ctx *ctx);
 const char *bte_last_error(const bte_ctx *ctx);
 
 /* Tabulate the convolution weights Ghat(xi_m, zeta_k) of Sec. 2.2,
- * Eq. GHat_calc (beta = 1, isotropic b, radial integral cut off at r0 = L,
- * Sec. 3.1) in FP64 on the host for each grid, and store them on the device:
- * the FP32 pair-symmetrised table of the fast path and the moment/projection
- * constants of Sec. 3.3. The FP64 table of the plain operator is built on the
- * first BTE_FP64_PLAIN call that needs it. table_ids[i] (host array of
- * ngrids ints) receives the id of grid i. Synchronous.
- * Errors: BTE_EINVAL (N unsupported, L <= 0, lambda not in [0, 1] with a closed
- * form or quadrature), BTE_ENOMEM. */
+ * Eq. GHat_calc (isotropic b, radial integral cut off at r0 = L, Sec. 3.1) in
+ * FP64 on the host for each grid, and store them on the device: the FP32
+ * pair-symmetrised table of the fast path and the moment/projection constants
+ * of Sec. 3.3. lambda = 0, 1: closed forms of the radial integrals; 0 < lambda
+ * < 1: the same integrals by composite Clenshaw-Curtis quadrature (the first
+ * panel substituted r = h u^2), as Sec. 2.2 prescribes for other lambda.
+ * The FP64 table of the plain operator is built on the first BTE_FP64_PLAIN
+ * call that needs it. table_ids[i] (host array of ngrids ints) receives the id
+ * of grid i. Synchronous. bte_init_weights: elastic grids (beta = 1).
+ * bte_init_weights_ex: any beta in (0, 1]; beta < 1 needs lambda = 0 or 1.
+ * Errors: BTE_EINVAL (N unsupported, L <= 0, lambda outside [0, 1], beta
+ * outside (0, 1]), BTE_ENOMEM. */
 bte_status bte_init_weights(bte_ctx *ctx, const bte_grid *grids, int ngrids, int *table_ids);
+bte_status bte_init_weights_ex(bte_ctx *ctx, const bte_grid_ex *grids, int ngrids, int *table_ids);
 
 /* Collision operator Q = P_N Qt(f) of Sec. 3.2-3.3 for a batch of cells:
  * forward transform of f, weighted convolution
@@ -136,7 +153,8 @@ bte_status bte_collide_ex(bte_ctx *ctx, const double *f, double *Q, const bte_in
 
 /* Conservation projection of Sec. 3.3 in place on device array Q:
  * Q <- Q - C^T (C C^T)^{-1} C Q, C = dv^3 (1, v1, v2, v3, |v|^2) per grid
- * point, FP64. (The paper prints "+ C"; the Lagrange solution of the stated
+ * point, FP64 (for inelastic tables, beta < 1, C keeps the mass and momentum
+ * rows only). (The paper prints "+ C"; the Lagrange solution of the stated
  * minimisation has "- C^T".) Asynchronous. Errors: BTE_EINVAL, BTE_ESTATE. */
 bte_status bte_project(bte_ctx *ctx, double *Q, const bte_instance *inst, int64_t ninst,
                        void *stream);

@@ -23,7 +23,7 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
           -5: "BTE_ENONFINITE", -6: "BTE_ESTATE"}
 
 # Every symbol include/bte.h declares (checked by the ABI tests).
-EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_collide",
+EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_init_weights_ex", "bte_collide",
            "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count", "bte_batch_count", "bte_graph_count",
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
@@ -35,6 +35,11 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "b
 
 class Grid(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("lambda_", ctypes.c_double)]
+
+
+class GridEx(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("beta", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -75,6 +80,7 @@ def load(path=None):
         "bte_destroy": (None, [vp]),
         "bte_last_error": (ctypes.c_char_p, [vp]),
         "bte_init_weights": (c_int, [vp, ctypes.POINTER(Grid), c_int, ctypes.POINTER(c_int)]),
+        "bte_init_weights_ex": (c_int, [vp, ctypes.POINTER(GridEx), c_int, ctypes.POINTER(c_int)]),
         "bte_collide": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, c_int, vp]),
         "bte_collide_ex": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, c_int, c_u, vp]),
         "bte_project": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
@@ -170,11 +176,14 @@ class Context:
             raise BteError(rc, "%s: %s" % (what, msg.decode() if msg else ""))
 
     def init_weights(self, grids):
-        """grids: list of (N, L, lambda). Returns the table ids."""
-        arr = (Grid * len(grids))(*[Grid(int(N), float(L), float(lam)) for (N, L, lam) in grids])
-        ids = (ctypes.c_int * len(grids))()
-        self._rc(self._lib.bte_init_weights(self._h, arr, len(grids), ids), "bte_init_weights")
-        self.grids += list(grids)
+        """grids: list of (N, L, lambda) or (N, L, lambda, beta) (beta = 1: elastic).
+        Returns the table ids."""
+        full = [tuple(g) + (1.0,) if len(g) == 3 else tuple(g) for g in grids]
+        arr = (GridEx * len(full))(*[GridEx(int(N), float(L), float(lam), float(beta))
+                                      for (N, L, lam, beta) in full])
+        ids = (ctypes.c_int * len(full))()
+        self._rc(self._lib.bte_init_weights_ex(self._h, arr, len(full), ids), "bte_init_weights")
+        self.grids += [g[:3] for g in full]
         return list(ids)
 
     def _inst(self, inst, f):

@@ -896,6 +896,13 @@ const char *bte_last_error(const bte_ctx *c) { return c ? c->err.c_str() : "null
 
 bte_status bte_init_weights(bte_ctx *c, const bte_grid *grids, int ngrids, int *table_ids) {
     if (!c || !grids || !table_ids || ngrids <= 0) return fail(c, BTE_EINVAL, "bte_init_weights: bad arguments");
+    std::vector<bte_grid_ex> ex(ngrids);
+    for (int i = 0; i < ngrids; ++i) ex[i] = bte_grid_ex{grids[i].N, grids[i].L, grids[i].lambda, 1.0};
+    return bte_init_weights_ex(c, ex.data(), ngrids, table_ids);
+}
+
+bte_status bte_init_weights_ex(bte_ctx *c, const bte_grid_ex *grids, int ngrids, int *table_ids) {
+    if (!c || !grids || !table_ids || ngrids <= 0) return fail(c, BTE_EINVAL, "bte_init_weights: bad arguments");
     if ((int)c->tables.size() + ngrids > kMaxTables)
         return fail(c, BTE_EINVAL, "too many weight tables (max " + std::to_string(kMaxTables) + ")");
     cudaSetDevice(c->device);
@@ -904,6 +911,7 @@ bte_status bte_init_weights(bte_ctx *c, const bte_grid *grids, int ngrids, int *
         t->N = grids[i].N;
         t->L = grids[i].L;
         t->lam = grids[i].lambda;
+        t->beta = grids[i].beta;
         int r = build_table(*t, c->err);
         if (r != BTE_OK) {
             delete t;
@@ -1362,6 +1370,7 @@ uint64_t grids_hash(const bte_ctx *c) {
     for (const Table *t : c->tables) {
         const double v[3] = {(double)t->N, t->L, t->lam};
         h = fnv1a(v, sizeof v, h);
+        if (t->beta != 1.0) h = fnv1a(&t->beta, sizeof t->beta, h);  // elastic grids hash as before
     }
     return h;
 }

@@ -51,6 +51,7 @@ static_assert(sizeof(ConvItem) == 32, "ConvItem layout");
 struct Table {
     int N = 0;
     double L = 0, lam = 0;
+    double beta = 1.0;  // restitution parameter of the collision rule (1: elastic)
     int ntiles = 0;
     int kind0 = 0;
     double dv = 0, dz = 0;
@@ -80,6 +81,7 @@ struct Table {
     std::vector<double> I, J;            // I[p * nq + q], J[s]
     int np = 0, nq = 0, ns = 0;
     double ghat(int k1, int k2, int k3, int m1, int m2, int m3) const;  // FP64, no dz^3
+    double gain_inelastic(double a, double b) const;                    // I(a, b) off the lattice
 };
 
 struct GraphKey {

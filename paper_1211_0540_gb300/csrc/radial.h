@@ -1,0 +1,100 @@
+// Radial integrals of the convolution weights (internal, host only).
+//
+//   I(a, b) = int_0^L r^(lam+2) sinc(ar) sinc(br) dr,  J(c) = int_0^L r^(lam+2) sinc(cr) dr
+// (Sec. 2.2, Eq. GHat_calc, cut off at r0 = L). For lambda = 0, 1 they have
+// closed forms (Radial); for other lambda a composite Clenshaw-Curtis rule
+// (RadialRule). Kept in a header of its own so that a host program can check
+// both against high-precision quadrature.
+#pragma once
+
+#include <cmath>
+#include <vector>
+
+namespace bte {
+namespace radial {
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct Radial {
+    double L, lam;
+    double C(double k) const {
+        if (k == 0.0) return lam == 0.0 ? L : 0.5 * L * L;
+        double sk = std::sin(k * L) / k;
+        if (lam == 0.0) return sk;
+        double h = std::sin(0.5 * k * L);
+        return L * sk - 2.0 * h * h / (k * k);
+    }
+    double J(double c) const {
+        if (c == 0.0) return std::pow(L, lam + 3.0) / (lam + 3.0);
+        double x = c * L, s = std::sin(x), co = std::cos(x);
+        if (lam == 0.0) return (s - x * co) / (c * c * c);
+        return (2.0 * x * s - (x * x - 2.0) * co - 2.0) / (c * c * c * c);
+    }
+    double I(double a, double b) const {
+        if (a == 0.0) return J(b);
+        if (b == 0.0) return J(a);
+        return (C(a - b) - C(a + b)) / (2.0 * a * b);
+    }
+};
+
+// Radial quadrature for non-integer lambda (Sec. 2.2: the weights are then a
+// 1-D integral precomputed by quadrature). Composite Clenshaw-Curtis rule on
+// [0, L]: uniform panels of at most half a period of the highest frequency
+// omega of the table (25 points each); on the first panel [0, h] the
+// substitution r = h u^2 (dr = 2 h u du) turns the factor r^(lambda+2), which
+// is not smooth at 0, into u^(2 lambda + 5) (33 points). Clenshaw-Curtis
+// weights on [-1, 1] for n intervals (n even), nodes cos(j pi / n):
+//   w_j = (c_j / n) [1 - sum_{k=1}^{n/2} b_k cos(2 pi j k / n) / (4k^2 - 1)],
+//   c_0 = c_n = 1, c_j = 2 otherwise, b_{n/2} = 1, b_k = 2 otherwise.
+struct RadialRule {
+    std::vector<double> r, w;  // nodes on [0, L] and weights of int_0^L g(r) dr
+};
+
+inline void cc_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n + 1, 0.0);
+    w.assign(n + 1, 0.0);
+    for (int j = 0; j <= n; ++j) {
+        x[j] = std::cos(j * kPi / n);
+        double s = 0.0;
+        for (int k = 1; k <= n / 2; ++k) {
+            const double b = (2 * k == n) ? 1.0 : 2.0;
+            s += b * std::cos(2.0 * kPi * j * k / n) / (4.0 * k * k - 1.0);
+        }
+        const double c = (j == 0 || j == n) ? 1.0 : 2.0;
+        w[j] = c / n * (1.0 - s);
+    }
+}
+
+inline RadialRule radial_rule(double L, double omega) {
+    const int panels = (int)std::ceil(omega * L / kPi) + 4;
+    const double h = L / panels;
+    RadialRule R;
+    std::vector<double> x, w;
+    cc_rule(32, x, w);  // first panel, u in [0, 1]: u = (x + 1) / 2
+    for (size_t j = 0; j < x.size(); ++j) {
+        const double u = 0.5 * (x[j] + 1.0);
+        R.r.push_back(h * u * u);
+        R.w.push_back(0.5 * w[j] * 2.0 * h * u);
+    }
+    cc_rule(24, x, w);
+    for (int p = 1; p < panels; ++p)
+        for (size_t j = 0; j < x.size(); ++j) {
+            R.r.push_back(p * h + 0.5 * h * (x[j] + 1.0));
+            R.w.push_back(0.5 * h * w[j]);
+        }
+    return R;
+}
+
+inline double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
+
+// I(a, b) by the quadrature rule (any lambda > -3), for checks and for the
+// pairs the closed form cannot take accurately.
+inline double I_quad(double lam, double L, double a, double b) {
+    const RadialRule Q = radial_rule(L, std::fabs(a) + std::fabs(b));
+    double acc = 0.0;
+    for (size_t i = 0; i < Q.r.size(); ++i) acc += Q.w[i] * std::pow(Q.r[i], lam + 2.0) * sinc(a * Q.r[i]) * sinc(b * Q.r[i]);
+    return acc;
+}
+
+}  // namespace radial
+}  // namespace bte

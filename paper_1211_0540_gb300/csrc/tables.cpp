@@ -1,8 +1,8 @@
 // Host FP64 tabulation of the convolution weights Ghat (Sec. 2.2, Eq. GHat_calc)
 // and their packing into the layouts the GPU kernels stream.
 //
-// Ghat(xi, zeta) = sqrt(2/pi) [ I(|zeta|/2, |xi - zeta/2|) - J(|xi|) ]  (beta = 1,
-// b = 1/(4 pi), d = 3, radial integral cut off at r0 = L, Sec. 3.1) with
+// Ghat(xi, zeta) = sqrt(2/pi) [ I(beta |zeta|/2, |xi - beta zeta/2|) - J(|xi|) ]
+// (b = 1/(4 pi), d = 3, radial integral cut off at r0 = L, Sec. 3.1) with
 //   I(a, b) = int_0^L r^{lam+2} sinc(ar) sinc(br) dr,  J(c) = int_0^L r^{lam+2} sinc(cr) dr.
 // The paper notes that for integer lambda these integrals have closed forms;
 // for lambda = 0, 1 they are
@@ -15,6 +15,12 @@
 //   s = |m'|^2 (|xi| = (dz/2) sqrt(4s)),  k' = k - N/2, m' = m - N/2.
 // With I(0, b) and J evaluated by the same function at bitwise-equal
 // arguments, Ghat(xi, 0) = 0 exactly, as in the continuous weights.
+// Non-integer lambda (0 < lambda < 1, variable hard potentials): the same
+// tables by quadrature (quadrature_tables). Inelastic collisions (beta < 1,
+// restitution parameter of the rule v' = v + (beta/2)(|u| sigma - u)): the gain
+// arguments are a = beta hz sqrt(p), b = hz |2m' - beta k'|, no longer on the
+// lattice of I, so the gain integral is evaluated per pair (closed form, or
+// quadrature where it would cancel); J is unchanged.
 //
 // FP32 pair-symmetrised layout (the fast path). For a zeta point k the terms m
 // and n = k - m + N/2 (zeta - xi_m = xi_n) multiply the same product
@@ -33,34 +39,46 @@
 #include <vector>
 
 #include "bte_internal.h"
+#include "radial.h"
 
 namespace bte {
 
 namespace {
 
-constexpr double kPi = 3.14159265358979323846;
+using radial::kPi;
+using radial::Radial;
+using radial::RadialRule;
+using radial::radial_rule;
+using radial::sinc;
 
-struct Radial {
-    double L, lam;
-    double C(double k) const {
-        if (k == 0.0) return lam == 0.0 ? L : 0.5 * L * L;
-        double sk = std::sin(k * L) / k;
-        if (lam == 0.0) return sk;
-        double h = std::sin(0.5 * k * L);
-        return L * sk - 2.0 * h * h / (k * k);
-    }
-    double J(double c) const {
-        if (c == 0.0) return std::pow(L, lam + 3.0) / (lam + 3.0);
-        double x = c * L, s = std::sin(x), co = std::cos(x);
-        if (lam == 0.0) return (s - x * co) / (c * c * c);
-        return (2.0 * x * s - (x * x - 2.0) * co - 2.0) / (c * c * c * c);
-    }
-    double I(double a, double b) const {
-        if (a == 0.0) return J(b);
-        if (b == 0.0) return J(a);
-        return (C(a - b) - C(a + b)) / (2.0 * a * b);
-    }
-};
+// I[p][q] = int_0^L r^(lam+2) sinc(a_p r) sinc(b_q r) dr and J[s] = I[0][4s]
+// (a_p = hz sqrt p, b_q = hz sqrt q) for every p < np, q < nq of the parity of
+// p, by one rule for the whole table: A_p[i] = w_i r_i^(lam+2) sinc(a_p r_i),
+// I[p][q] = sum_i A_p[i] sinc(b_q r_i). J is read off the same sums, so
+// Ghat(xi, 0) = I(0, |xi|) - J(|xi|) is exactly 0.
+void quadrature_tables(Table &t, double hz) {
+    const int nrow = std::max(t.nq, 4 * (t.ns - 1) + 1);
+    const RadialRule R = radial_rule(t.L, hz * (std::sqrt((double)(t.np - 1)) + std::sqrt((double)(nrow - 1))));
+    const size_t nn = R.r.size();
+    std::vector<double> S((size_t)nrow * nn), A((size_t)t.np * nn);
+#pragma omp parallel for schedule(static)
+    for (int q = 0; q < nrow; ++q)
+        for (size_t i = 0; i < nn; ++i) S[(size_t)q * nn + i] = sinc(hz * std::sqrt((double)q) * R.r[i]);
+#pragma omp parallel for schedule(static)
+    for (int p = 0; p < t.np; ++p)
+        for (size_t i = 0; i < nn; ++i)
+            A[(size_t)p * nn + i] = R.w[i] * std::pow(R.r[i], t.lam + 2.0) * S[(size_t)p * nn + i];
+    auto dot = [&](int p, int q) {
+        const double *a = &A[(size_t)p * nn], *b = &S[(size_t)q * nn];
+        double acc = 0.0;
+        for (size_t i = 0; i < nn; ++i) acc += a[i] * b[i];
+        return acc;
+    };
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int p = 0; p < t.np; ++p)
+        for (int q = (p & 1); q < t.nq; q += 2) t.I[(size_t)p * t.nq + q] = dot(p, q);
+    for (int s = 0; s < t.ns; ++s) t.J[s] = dot(0, 4 * s);
+}
 
 inline int box_lo(int k, int N) { return std::max(0, k - N / 2 + 1); }
 inline int box_hi(int k, int N) { return std::min(N - 1, k + N / 2); }
@@ -90,7 +108,25 @@ double Table::ghat(int k1, int k2, int k3, int m1, int m2, int m3) const {
         q += (2 * m[d] - k[d]) * (2 * m[d] - k[d]);
         s += m[d] * m[d];
     }
-    return std::sqrt(2.0 / kPi) * (I[(size_t)p * nq + q] - J[s]);
+    if (beta == 1.0) return std::sqrt(2.0 / kPi) * (I[(size_t)p * nq + q] - J[s]);
+    // inelastic: gain arguments a = beta |zeta| / 2, b = |xi - beta zeta / 2| (Eq. GHat_calc)
+    const double hz = 0.5 * dz;
+    double b2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double c = 2.0 * m[d] - beta * k[d];
+        b2 += c * c;
+    }
+    const double a = beta * hz * std::sqrt((double)p), b = hz * std::sqrt(b2);
+    return std::sqrt(2.0 / kPi) * (gain_inelastic(a, b) - J[s]);
+}
+
+// The closed form loses digits when a b L^2 is small (C(a - b) and C(a + b)
+// nearly cancel); such pairs (|xi - beta zeta / 2| near 0, which the elastic
+// lattice never produces) take the quadrature rule instead.
+double Table::gain_inelastic(double a, double b) const {
+    Radial R{L, lam};
+    if (a == 0.0 || b == 0.0 || b * L >= 0.25) return R.I(a, b);
+    return radial::I_quad(lam, L, a, b);
 }
 
 int build_table(Table &t, std::string &err) {
@@ -103,8 +139,17 @@ int build_table(Table &t, std::string &err) {
         err = "L must be finite and > 0";
         return BTE_EINVAL;
     }
-    if (t.lam != 0.0 && t.lam != 1.0) {
-        err = "lambda must be 0 (Maxwell molecules) or 1 (hard spheres)";
+    if (!(t.lam >= 0.0 && t.lam <= 1.0)) {
+        err = "lambda must lie in [0, 1] (Maxwell molecules, variable hard potentials, hard spheres)";
+        return BTE_EINVAL;
+    }
+    if (!(t.beta > 0.0 && t.beta <= 1.0)) {
+        err = "beta must lie in (0, 1] (beta = 1: elastic collisions)";
+        return BTE_EINVAL;
+    }
+    const bool integer_lam = t.lam == 0.0 || t.lam == 1.0;
+    if (t.beta != 1.0 && !integer_lam) {
+        err = "inelastic weights (beta < 1) need lambda = 0 or 1 (closed forms)";
         return BTE_EINVAL;
     }
     const int h = N / 2;
@@ -120,17 +165,21 @@ int build_table(Table &t, std::string &err) {
     t.ns = 3 * h * h + 1;
     t.I.assign((size_t)t.np * t.nq, 0.0);
     t.J.assign(t.ns, 0.0);
-    Radial R{t.L, t.lam};
+    if (integer_lam) {
+        Radial R{t.L, t.lam};
 #pragma omp parallel for schedule(dynamic, 4)
-    for (int p = 0; p < t.np; ++p) {
-        double a = hz * std::sqrt((double)p);
-        for (int q = 0; q < t.nq; ++q) {
-            if ((p - q) % 2 != 0) continue;  // q = |2m'-k'|^2 has the parity of |k'|^2
-            double b = hz * std::sqrt((double)q);
-            t.I[(size_t)p * t.nq + q] = R.I(a, b);
+        for (int p = 0; p < t.np; ++p) {
+            double a = hz * std::sqrt((double)p);
+            for (int q = 0; q < t.nq; ++q) {
+                if ((p - q) % 2 != 0) continue;  // q = |2m'-k'|^2 has the parity of |k'|^2
+                double b = hz * std::sqrt((double)q);
+                t.I[(size_t)p * t.nq + q] = R.I(a, b);
+            }
         }
+        for (int s = 0; s < t.ns; ++s) t.J[s] = R.J(hz * std::sqrt((double)(4 * s)));
+    } else {
+        quadrature_tables(t, hz);
     }
-    for (int s = 0; s < t.ns; ++s) t.J[s] = R.J(hz * std::sqrt((double)(4 * s)));
 
     // pencil descriptors: kept (m1, m2) blocks
     std::vector<uint32_t> desc;
@@ -190,7 +239,11 @@ int build_table(Table &t, std::string &err) {
             }
         }
 
-    // projection constants: A = sum_j c_j c_j^T, c_j = (1, v1, v2, v3, |v|^2)
+    // projection constants: A = sum_j c_j c_j^T, c_j = (1, v1, v2, v3, |v|^2);
+    // inelastic collisions do not conserve energy (Sec. 3.3): the constraint set
+    // is then the first four rows, and (C C^T)^{-1} is the 4 x 4 inverse bordered
+    // by zeros (so the energy multiplier is 0)
+    const int nr = t.beta == 1.0 ? 5 : 4;
     double A[5][5] = {{0}};
     for (int j1 = 0; j1 < N; ++j1)
         for (int j2 = 0; j2 < N; ++j2)
@@ -200,25 +253,25 @@ int build_table(Table &t, std::string &err) {
                 for (int a = 0; a < 5; ++a)
                     for (int b = 0; b < 5; ++b) A[a][b] += c[a] * c[b];
             }
-    // Gauss-Jordan inverse with partial pivoting
+    // Gauss-Jordan inverse of the leading nr x nr block with partial pivoting
     double Ai[5][10];
-    for (int a = 0; a < 5; ++a)
-        for (int b = 0; b < 10; ++b) Ai[a][b] = b < 5 ? A[a][b] : (b - 5 == a ? 1.0 : 0.0);
-    for (int c = 0; c < 5; ++c) {
+    for (int a = 0; a < nr; ++a)
+        for (int b = 0; b < 2 * nr; ++b) Ai[a][b] = b < nr ? A[a][b] : (b - nr == a ? 1.0 : 0.0);
+    for (int c = 0; c < nr; ++c) {
         int piv = c;
-        for (int r = c + 1; r < 5; ++r)
+        for (int r = c + 1; r < nr; ++r)
             if (std::fabs(Ai[r][c]) > std::fabs(Ai[piv][c])) piv = r;
-        for (int b = 0; b < 10; ++b) std::swap(Ai[c][b], Ai[piv][b]);
+        for (int b = 0; b < 2 * nr; ++b) std::swap(Ai[c][b], Ai[piv][b]);
         double d = Ai[c][c];
-        for (int b = 0; b < 10; ++b) Ai[c][b] /= d;
-        for (int r = 0; r < 5; ++r)
+        for (int b = 0; b < 2 * nr; ++b) Ai[c][b] /= d;
+        for (int r = 0; r < nr; ++r)
             if (r != c) {
                 double f = Ai[r][c];
-                for (int b = 0; b < 10; ++b) Ai[r][b] -= f * Ai[c][b];
+                for (int b = 0; b < 2 * nr; ++b) Ai[r][b] -= f * Ai[c][b];
             }
     }
     for (int a = 0; a < 5; ++a)
-        for (int b = 0; b < 5; ++b) t.ainv[a * 5 + b] = Ai[a][b + 5];
+        for (int b = 0; b < 5; ++b) t.ainv[a * 5 + b] = (a < nr && b < nr) ? Ai[a][b + nr] : 0.0;
 
     // DFT roots exp(2 pi i t / N)
     std::vector<float2> r32(N);

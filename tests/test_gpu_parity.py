@@ -391,7 +391,11 @@ def test_invalid_arguments_rejected(bte):
     with pytest.raises(bte.BteError):
         d.init_weights([(10, L, 1.0)])  # unsupported N
     with pytest.raises(bte.BteError):
-        d.init_weights([(16, L, 0.5)])  # no closed form for this lambda
+        d.init_weights([(16, L, 1.5)])  # lambda outside [0, 1]
+    with pytest.raises(bte.BteError):
+        d.init_weights([(8, L, 0.5, 0.8)])  # inelastic weights need lambda = 0 or 1
+    with pytest.raises(bte.BteError):
+        d.init_weights([(8, L, 1.0, 0.0)])  # beta outside (0, 1]
     d.close()
 
 
@@ -685,3 +689,51 @@ def test_contexts_on_two_host_threads(bte):
     for e in errs:
         assert not isinstance(e, Exception), e
         assert e is not None and e <= TOL32, e
+
+
+@pytest.mark.parametrize("N,ncells,lam", [(8, 40, 0.5), (12, 33, 0.3), (16, 34, 0.75)])
+def test_non_integer_lambda_matches_oracle(bte, N, ncells, lam):
+    """Variable hard potentials (0 < lambda < 1): the library's weights come from
+    its own Clenshaw-Curtis quadrature, the oracle's from graded Gauss-Legendre
+    (Sec. 2.2: other lambda by a 1-D quadrature). Both paths against the oracle,
+    on every cell at N = 8, 12 and on sampled cells at N = 16."""
+    f = inputs.homogeneous_cells(N, L, ncells, seed=700 + N)
+    pick = list(range(ncells)) if N < 16 else [0, 17, ncells - 1]
+    Qo = oracle.collide(N, L, lam, f[pick])
+    norm = loss_norm(N, lam, f[pick])
+    for mode, tol in ((bte.FP64_PLAIN, TOL64), (bte.FP32, TOL32)):
+        Qg = run_collide(bte, N, lam, f, mode)
+        err = np.linalg.norm(Qg[pick] - Qo, axis=1) / norm
+        assert err.max() <= tol, (mode, err.max())
+        assert np.all(np.abs(oracle.moments(N, L, Qg)) <= 1e-12 * abs_moment_scale(N, Qg))
+
+
+@pytest.mark.parametrize("N,ncells,lam,beta", [(8, 40, 1.0, 0.8), (12, 33, 0.0, 0.6), (16, 34, 1.0, 0.9)])
+def test_inelastic_collisions_match_oracle(bte, N, ncells, lam, beta):
+    """Inelastic collisions (beta < 1 in Eq. GHat_calc; Sec. 3.3 drops the energy
+    row of the constraints): both paths against the oracle, mass and momentum
+    conserved to 1e-12, energy dissipated; one Heun step against the oracle's."""
+    f = inputs.homogeneous_cells(N, L, ncells, seed=800 + N)
+    c = ctx_for(bte, ((N, L, lam, beta),))
+    pick = list(range(ncells)) if N < 16 else [0, 17, ncells - 1]
+    Qo = oracle.collide(N, L, lam, f[pick], beta=beta)
+    norm = np.linalg.norm(oracle.collide(N, L, lam, f[pick], part=1, project=False, beta=beta), axis=1)
+    for mode, tol in ((bte.FP64_PLAIN, TOL64), (bte.FP32, TOL32)):
+        Q = c.collide(torch.from_numpy(f).cuda(), mode=mode)
+        c.sync_status()
+        Qg = Q.cpu().numpy()
+        err = np.linalg.norm(Qg[pick] - Qo, axis=1) / norm
+        assert err.max() <= tol, (mode, err.max())
+        m = oracle.moments(N, L, Qg)
+        scale = abs_moment_scale(N, Qg)
+        assert np.all(np.abs(m[:, :4]) <= 1e-12 * scale[:, :4])
+        assert np.all(m[:, 4] < 0.0)
+    if N < 16:
+        ft = torch.from_numpy(f.copy()).cuda()
+        s = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            c.step(ft, 0.01, 1.0, mode=bte.FP32, stream=s)
+        c.sync_status(s)
+        ref = oracle.rk2_homogeneous(N, L, lam, f, 0.01, 1.0, beta=beta)
+        assert np.abs(ft.cpu().numpy() - ref).max() / np.abs(f).max() <= 1e-7
