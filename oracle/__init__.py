@@ -21,11 +21,12 @@ __all__ = [
     "lib", "gauss_legendre", "sinc", "radial_I", "radial_J", "ghat_pair", "weights",
     "ghat_dense", "dft_forward_direct", "dft_forward", "dft_inverse", "convolve",
     "convolve_dense", "moments", "project", "collide", "rk2_homogeneous", "transport",
-    "strang_step", "BC_DIFFUSE", "BC_SPECULAR", "set_threads", "get_threads", "weights_beta",
+    "strang_step", "BC_DIFFUSE", "BC_SPECULAR", "BC_NOFLUX", "set_threads", "get_threads", "weights_beta",
 ]
 
 BC_DIFFUSE = 0
 BC_SPECULAR = 1
+BC_NOFLUX = 2
 
 # How each function is pinned to something other than itself (tests/test_oracle_*.py).
 PINS = {
@@ -42,6 +43,9 @@ PINS = {
     "rk2_homogeneous": "explicit Heun stages; conservation over 20 steps; second order in dt "
                        "(successive differences shrink by ~4 per halving)",
     "transport": "constant state, exact mass balance at the walls, second-order convergence",
+    "transport(dx)": "uniform widths reproduce the uniform path bit for bit; constant state and "
+                     "mass sum(dx f) kept on a stretched grid; second order on a smoothly stretched "
+                     "grid; no-flux boundary invariants",
     "weights_beta / collide(beta)": "beta = 1 reproduces the elastic tables; weak-form brute force with the "
                                     "inelastic rule; energy dissipation -beta(1-beta)(rho E - |P|^2) for "
                                     "Maxwell molecules and its hard-sphere Maxwellian value, converging in N",
@@ -86,6 +90,8 @@ def lib():
         "ora_transport": (None, [i, d, i, d, d, i, i, d, d, d, p]),
         "ora_strang_step": (None, [i, d, i, d, d, i, i, d, d, p, p, d, d, p]),
         "ora_project_rows": (None, [i, d, i, i, p]),
+        "ora_transport_grid": (None, [i, d, i, p, i, i, d, d, d, p]),
+        "ora_strang_step_grid": (None, [i, d, i, p, i, i, d, d, p, p, d, d, p]),
         "ora_weights_sizes_beta": (None, [i, p, p]),
         "ora_weights_build_beta": (i, [i, d, d, d, p, p]),
         "ora_convolve_beta": (None, [i, d, i, p, p, i, p, p]),
@@ -311,19 +317,36 @@ def rk2_homogeneous(N, L, lam, f, dt, eps=1.0, beta=1.0):
 
 
 def transport(N, L, f, tau, x0=0.0, x1=1.0, bc_left=BC_DIFFUSE, bc_right=BC_SPECULAR,
-              Tw_left=1.0, Tw_right=1.0):
+              Tw_left=1.0, Tw_right=1.0, dx=None):
+    """Heun transport sub-step (Sec. 3.4) on nx uniform cells of [x0, x1], or on
+    cells of widths dx (nx values) when given."""
     f2, nx = _cells(f, N)
     f2 = f2.copy()
+    if dx is not None:
+        dx = _f64(dx)
+        if dx.size != nx or nx < 2:
+            raise ValueError("dx needs one width per cell (nx >= 2)")
+        lib().ora_transport_grid(int(N), float(L), nx, _p(dx), int(bc_left), int(bc_right),
+                                 float(Tw_left), float(Tw_right), float(tau), _p(f2))
+        return f2
     lib().ora_transport(int(N), float(L), nx, float(x0), float(x1), int(bc_left), int(bc_right),
                         float(Tw_left), float(Tw_right), float(tau), _p(f2))
     return f2
 
 
 def strang_step(N, L, lam, f, dt, eps, x0=0.0, x1=1.0, bc_left=BC_DIFFUSE,
-                bc_right=BC_SPECULAR, Tw_left=1.0, Tw_right=1.0):
+                bc_right=BC_SPECULAR, Tw_left=1.0, Tw_right=1.0, dx=None):
     f2, nx = _cells(f, N)
     f2 = f2.copy()
     w = weights(N, L, lam)
+    if dx is not None:
+        dx = _f64(dx)
+        if dx.size != nx or nx < 2:
+            raise ValueError("dx needs one width per cell (nx >= 2)")
+        lib().ora_strang_step_grid(int(N), float(L), nx, _p(dx), int(bc_left), int(bc_right),
+                                   float(Tw_left), float(Tw_right), _p(w.I), _p(w.J), float(dt),
+                                   float(eps), _p(f2))
+        return f2
     lib().ora_strang_step(int(N), float(L), nx, float(x0), float(x1), int(bc_left),
                           int(bc_right), float(Tw_left), float(Tw_right), _p(w.I), _p(w.J),
                           float(dt), float(eps), _p(f2))

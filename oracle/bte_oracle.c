@@ -35,7 +35,11 @@
  *   - RK2 = Heun (SSP-RK2), with the projection applied at each stage;
  *   - Strang ordering T(dt/2) C(dt) T(dt/2), collision sub-step dt/eps;
  *   - diffuse wall sigma_w normalised by the discrete outgoing flux, specular
- *     mirror i -> N - i on the asymmetric v1 grid (i = 0 has no partner: ghost 0).
+ *     mirror i -> N - i on the asymmetric v1 grid (i = 0 has no partner: ghost 0);
+ *   - non-uniform cells: the reconstruction uses the upwind cell's width, the
+ *     minmod slope divided differences over centre distances; ghost widths
+ *     mirror the adjacent cells; "no flux for the incoming characteristics":
+ *     incoming ghost components 0, outgoing ones copied.
  *
  * Layout: one cell holds M = N^3 values, index (k1*N + k2)*N + k3 (k3 fastest).
  * Complex arrays are interleaved (re, im) pairs.
@@ -763,6 +767,7 @@ void ora_rk2_homogeneous_beta(int N, double L, int ncells, const double *I3, con
 
 #define ORA_BC_DIFFUSE 0
 #define ORA_BC_SPECULAR 1
+#define ORA_BC_NOFLUX 2
 
 static double ora_minmod(double a, double b) {
     if (a * b <= 0.0) return 0.0;
@@ -783,6 +788,17 @@ static void ora_fill_ghosts(int N, double L, int side, int bc, double Tw, const 
                             const double *f1, double *g0, double *g1) {
     int M = N * N * N, h = N / 2;
     double dv = 2.0 * L / N;
+    if (bc == ORA_BC_NOFLUX) {
+        /* no flux for the incoming characteristics (Sec. 3.4, for boundaries
+         * without wall interaction): incoming components (v.n > 0) are 0 in the
+         * ghosts, outgoing ones copy the adjacent cell (they leave freely). */
+        for (int j = 0; j < M; ++j) {
+            double v1 = dv * (j / (N * N) - h);
+            double vn = side == 0 ? v1 : -v1;
+            g0[j] = g1[j] = vn > 0.0 ? 0.0 : f0[j];
+        }
+        return;
+    }
     if (bc == ORA_BC_SPECULAR) {
         /* mirror v1 -> -v1: index i -> N - i; i = 0 (v1 = -L) has no partner on the grid. */
         for (int j = 0; j < M; ++j) {
@@ -822,9 +838,15 @@ static void ora_fill_ghosts(int N, double L, int side, int bc, double Tw, const 
     }
 }
 
-/* Right-hand side -(F_{j+1/2} - F_{j-1/2}) / dx for all interior cells of the
- * extended array e (nx + 4 cells: two ghosts each side, interior at 2..nx+1). */
-static void ora_transport_rhs(int N, double L, int nx, double dx, const double *e, double *rhs) {
+/* Right-hand side -(F_{j+1/2} - F_{j-1/2}) / dx_j for all interior cells of the
+ * extended array e (nx + 4 cells: two ghosts each side, interior at 2..nx+1),
+ * on cells of widths w (nx + 4 entries; the ghosts mirror the widths of the
+ * adjacent interior cells). Eq. upwind with the cell width of the upwind cell
+ * in the reconstruction, F = v1 (f_j + dx_j/2 s_j) for v1 >= 0, and the minmod
+ * slope of divided differences over the distances between cell centres,
+ * s_j = minmod((f_j - f_{j-1}) / h_{j-1/2}, (f_{j+1} - f_j) / h_{j+1/2}),
+ * h_{j+1/2} = (dx_j + dx_{j+1}) / 2 (on a uniform grid: dx). */
+static void ora_transport_rhs(int N, double L, int nx, const double *w, const double *e, double *rhs) {
     int M = N * N * N, h = N / 2;
     double dv = 2.0 * L / N;
 #pragma omp parallel for schedule(static)
@@ -836,17 +858,20 @@ static void ora_transport_rhs(int N, double L, int nx, double dx, const double *
             for (int face = 0; face < 2; ++face) {
                 int lft = x - 1 + face, rgt = x + face; /* face between lft and rgt */
                 double fl = e[(size_t)lft * M + j], fr = e[(size_t)rgt * M + j];
+                double hc = 0.5 * (w[lft] + w[rgt]);
                 if (v1 >= 0.0) {
                     double fll = e[(size_t)(lft - 1) * M + j];
-                    double sig = ora_minmod((fl - fll) / dx, (fr - fl) / dx);
-                    F[face] = v1 * (fl + 0.5 * dx * sig);
+                    double hl = 0.5 * (w[lft - 1] + w[lft]);
+                    double sig = ora_minmod((fl - fll) / hl, (fr - fl) / hc);
+                    F[face] = v1 * (fl + 0.5 * w[lft] * sig);
                 } else {
                     double frr = e[(size_t)(rgt + 1) * M + j];
-                    double sig = ora_minmod((fr - fl) / dx, (frr - fr) / dx);
-                    F[face] = v1 * (fr - 0.5 * dx * sig);
+                    double hr = 0.5 * (w[rgt] + w[rgt + 1]);
+                    double sig = ora_minmod((fr - fl) / hc, (frr - fr) / hr);
+                    F[face] = v1 * (fr - 0.5 * w[rgt] * sig);
                 }
             }
-            rhs[(size_t)c * M + j] = -(F[1] - F[0]) / dx;
+            rhs[(size_t)c * M + j] = -(F[1] - F[0]) / w[x];
         }
     }
 }
@@ -860,24 +885,40 @@ static void ora_extend(int N, double L, int nx, const double *f, int bc_l, int b
                     e + (nx + 3) * M);
 }
 
-/* Transport sub-step of length tau on f (nx cells of M values on [x0, x1],
- * uniform dx) by Heun's method: f1 = f + tau R(f); f <- (f + f1 + tau R(f1)) / 2. */
-void ora_transport(int N, double L, int nx, double x0, double x1, int bc_l, int bc_r, double Tw_l,
-                   double Tw_r, double tau, double *f) {
+/* Transport sub-step of length tau on f (nx cells of M values, widths dx[0..nx),
+ * Sec. 3.4: "cells of size dx_j, not necessarily uniform") by Heun's method:
+ * f1 = f + tau R(f); f <- (f + f1 + tau R(f1)) / 2. */
+void ora_transport_grid(int N, double L, int nx, const double *dx, int bc_l, int bc_r, double Tw_l,
+                        double Tw_r, double tau, double *f) {
     size_t M = (size_t)N * N * N, n = M * nx;
-    double dx = (x1 - x0) / nx;
+    double *w = (double *)malloc(sizeof(double) * (nx + 4));
+    for (int c = 0; c < nx; ++c) w[c + 2] = dx[c];
+    w[1] = dx[0]; /* ghost widths mirror the adjacent interior cells */
+    w[0] = dx[1];
+    w[nx + 2] = dx[nx - 1];
+    w[nx + 3] = dx[nx - 2];
     double *e = (double *)malloc(sizeof(double) * M * (nx + 4));
     double *r = (double *)malloc(sizeof(double) * n);
     double *f1 = (double *)malloc(sizeof(double) * n);
     ora_extend(N, L, nx, f, bc_l, bc_r, Tw_l, Tw_r, e);
-    ora_transport_rhs(N, L, nx, dx, e, r);
+    ora_transport_rhs(N, L, nx, w, e, r);
     for (size_t i = 0; i < n; ++i) f1[i] = f[i] + tau * r[i];
     ora_extend(N, L, nx, f1, bc_l, bc_r, Tw_l, Tw_r, e);
-    ora_transport_rhs(N, L, nx, dx, e, r);
+    ora_transport_rhs(N, L, nx, w, e, r);
     for (size_t i = 0; i < n; ++i) f[i] = 0.5 * (f[i] + f1[i] + tau * r[i]);
+    free(w);
     free(e);
     free(r);
     free(f1);
+}
+
+/* The same on nx uniform cells of [x0, x1]. */
+void ora_transport(int N, double L, int nx, double x0, double x1, int bc_l, int bc_r, double Tw_l,
+                   double Tw_r, double tau, double *f) {
+    double *dx = (double *)malloc(sizeof(double) * nx);
+    for (int c = 0; c < nx; ++c) dx[c] = (x1 - x0) / nx;
+    ora_transport_grid(N, L, nx, dx, bc_l, bc_r, Tw_l, Tw_r, tau, f);
+    free(dx);
 }
 
 /* One Strang step T(dt/2) C(dt) T(dt/2) of the space-inhomogeneous problem. */
@@ -887,4 +928,13 @@ void ora_strang_step(int N, double L, int nx, double x0, double x1, int bc_l, in
     ora_transport(N, L, nx, x0, x1, bc_l, bc_r, Tw_l, Tw_r, 0.5 * dt, f);
     ora_rk2_homogeneous(N, L, nx, Itab, Jtab, dt, eps, f);
     ora_transport(N, L, nx, x0, x1, bc_l, bc_r, Tw_l, Tw_r, 0.5 * dt, f);
+}
+
+/* The Strang step on cells of widths dx[0..nx). */
+void ora_strang_step_grid(int N, double L, int nx, const double *dx, int bc_l, int bc_r, double Tw_l,
+                          double Tw_r, const double *Itab, const double *Jtab, double dt, double eps,
+                          double *f) {
+    ora_transport_grid(N, L, nx, dx, bc_l, bc_r, Tw_l, Tw_r, 0.5 * dt, f);
+    ora_rk2_homogeneous(N, L, nx, Itab, Jtab, dt, eps, f);
+    ora_transport_grid(N, L, nx, dx, bc_l, bc_r, Tw_l, Tw_r, 0.5 * dt, f);
 }

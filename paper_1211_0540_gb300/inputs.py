@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "velocity_nodes", "maxwellian", "bi_maxwellian", "bkw", "random_bi_maxwellian_params",
     "homogeneous_cells", "wall_heating_initial", "precision_sweep_cells", "uneven_batch",
-    "training_states", "surrogate_training_states",
+    "training_states", "surrogate_training_states", "sudden_heating_grid",
 ]
 
 
@@ -74,6 +74,24 @@ def wall_heating_initial(N, L, nx):
     """Gas at rest, rho = 1, T = 1 in every cell (sudden wall heating, Sec. 5)."""
     m = maxwellian(N, L, 1.0, (0.0, 0.0, 0.0), 1.0)
     return np.tile(m, (nx, 1))
+
+
+def sudden_heating_grid(X=20.0, dx_wall=0.125, wall_len=2.0, dx_bulk=0.5, ratio=1.2):
+    """Cell widths of the paper's sudden-heating run (Sec. 5): eight cells per
+    mean free path next to the wall, two in the interior (Knudsen number 1, so
+    the mean free path is the unit length). Recipe: uniform dx_wall over
+    [0, wall_len], then widths growing by `ratio` per cell up to dx_bulk, then
+    equal cells no wider than dx_bulk up to X. Returns the widths (sum X)."""
+    w = [dx_wall] * int(round(wall_len / dx_wall))
+    x = sum(w)
+    d = dx_wall * ratio
+    while d < dx_bulk and x + d < X:
+        w.append(d)
+        x += d
+        d *= ratio
+    n = int(math.ceil((X - x) / dx_bulk - 1e-12))
+    w += [(X - x) / n] * n
+    return np.array(w)
 
 
 def precision_sweep_cells(N, L, ncells, seed):

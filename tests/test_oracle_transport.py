@@ -93,3 +93,85 @@ def test_upwind_direction():
             assert c1 < c0
         else:
             assert abs(c1 - c0) < 1e-14
+
+
+# --- cells of unequal width (Sec. 3.4: "cells of size dx_j, not necessarily uniform") ---
+
+def test_uniform_widths_reproduce_the_uniform_path():
+    N, nx = 8, 12
+    f = inputs.wall_heating_initial(N, L, nx) * (1.0 + 0.2 * np.sin(np.arange(nx)))[:, None]
+    a = oracle.transport(N, L, f, 2e-3, Tw_left=2.0)
+    b = oracle.transport(N, L, f, 2e-3, Tw_left=2.0, dx=np.full(nx, 1.0 / nx))
+    assert np.array_equal(a, b)
+
+
+def test_stretched_grid_keeps_constant_state_and_mass():
+    N = 8
+    dx = inputs.sudden_heating_grid()
+    nx = dx.size
+    f = inputs.wall_heating_initial(N, L, nx)
+    g = oracle.transport(N, L, f, 1e-2, bc_left=oracle.BC_SPECULAR, bc_right=oracle.BC_SPECULAR, dx=dx)
+    interior = slice(2, nx - 2)  # the walls' v1 = -L components have no mirror partner (e^-18-level)
+    assert np.array_equal(g[interior], f[interior])
+    assert np.abs(g - f).max() <= 1e-7 * f.max()
+    rng = np.random.default_rng(1)
+    f = f * (1.0 + 0.3 * rng.uniform(size=(nx, 1)))
+    dv3 = (2 * L / N) ** 3
+    m0 = (dx[:, None] * f).sum() * dv3
+    for _ in range(10):
+        f = oracle.transport(N, L, f, 1e-2, bc_left=oracle.BC_DIFFUSE, Tw_left=2.0,
+                             bc_right=oracle.BC_SPECULAR, dx=dx)
+    assert abs((dx[:, None] * f).sum() * dv3 - m0) <= 1e-13 * m0
+
+
+def test_second_order_convergence_on_a_smoothly_stretched_grid():
+    """Cells from the smooth map x(s) = s + 0.3 sin(2 pi s) / (2 pi) of uniform s:
+    L1 error against cell averages of the exact solution f0(x - v1 t) shrinks
+    at about second order."""
+    N, t = 4, 0.02
+    prof = lambda x: 1.0 + 0.3 * np.tanh((x - 0.5) / 0.08)  # noqa: E731
+    errs = []
+    for nx in (128, 256, 512):
+        s = np.arange(nx + 1) / nx
+        edges = s + 0.3 * np.sin(2 * math.pi * s) / (2 * math.pi)
+        dx = np.diff(edges)
+        M = inputs.maxwellian(N, L, 1.0, (0.0, 0.0, 0.0), 4.0)
+        gx, gw = np.polynomial.legendre.leggauss(4)
+
+        def avg(shift):
+            mid, half = 0.5 * (edges[1:] + edges[:-1]), 0.5 * dx
+            return sum(w * prof(mid + half * q - shift) for q, w in zip(gx, gw)) * 0.5
+
+        f = avg(0.0)[:, None] * M[None, :]
+        steps = int(round(t / (0.2 * dx.min() / L)))
+        g = f.copy()
+        for _ in range(steps):
+            g = oracle.transport(N, L, g, t / steps, bc_left=oracle.BC_SPECULAR, bc_right=oracle.BC_SPECULAR,
+                                 dx=dx)
+        v1 = 2 * L / N * (np.arange(N) - N // 2)
+        mid = 0.5 * (edges[1:] + edges[:-1])
+        interior = (mid > 0.25) & (mid < 0.75)
+        err = 0.0
+        for i, vv in enumerate(v1):
+            j = i * N * N
+            err = max(err, np.sum(np.abs(g[interior, j] / M[j] - avg(vv * t)[interior]) * dx[interior]))
+        errs.append(err)
+    r1, r2 = math.log2(errs[0] / errs[1]), math.log2(errs[1] / errs[2])
+    assert r1 > 1.7 and r2 > 1.8, (errs, r1, r2)
+
+
+def test_no_flux_boundary_lets_nothing_in():
+    """No flux for the incoming characteristics at x = X: a constant state keeps
+    its outgoing components everywhere and its incoming ones everywhere but in
+    the two cells next to that boundary, which lose mass (nothing enters)."""
+    N = 8
+    dx = inputs.sudden_heating_grid()
+    nx = dx.size
+    f = inputs.wall_heating_initial(N, L, nx)
+    g = oracle.transport(N, L, f, 1e-2, bc_left=oracle.BC_SPECULAR, bc_right=oracle.BC_NOFLUX, dx=dx)
+    v1 = (2 * L / N * (np.arange(N ** 3) // (N * N) - N // 2))
+    incoming = v1 < 0  # v . n > 0 for the inward normal -e1 at x = X
+    assert np.array_equal(g[:, ~incoming], f[:, ~incoming])
+    assert np.array_equal(g[:-2][:, incoming], f[:-2][:, incoming])
+    lost = (f[-2:][:, incoming] - g[-2:][:, incoming]).sum()
+    assert lost > 0.0 and np.all(g >= 0.0)
