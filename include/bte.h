@@ -58,7 +58,11 @@ typedef enum {
     BTE_LEARNED = 2       /* MLP surrogate + FP64 projection + exact fallback   */
 } bte_mode;
 
-typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1 } bte_bc;
+/* Boundary of the 1-D slab: diffuse wall (Sec. 2.1, Eq. BC), specular wall,
+ * or no flux for the incoming characteristics (Sec. 3.4: for boundaries
+ * without wall interaction; incoming components enter as 0, outgoing ones
+ * leave freely). */
+typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1, BTE_BC_NOFLUX = 2 } bte_bc;
 
 /* bte_collide_ex flags */
 #define BTE_FLAG_RAW 1u          /* return Qt (skip the conservation projection)  */
@@ -92,13 +96,25 @@ typedef struct {
 
 /* 1-D slab [x0, x1] of nx uniform cells with a wall at each end (Sec. 2.1,
  * Eq. BC; Sec. 3.4). bc_*: BTE_BC_DIFFUSE (wall temperature Tw_*, zero wall
- * velocity) or BTE_BC_SPECULAR. */
+ * velocity), BTE_BC_SPECULAR or BTE_BC_NOFLUX. */
 typedef struct {
     int nx;
     double x0, x1;
     int bc_left, bc_right;
     double Tw_left, Tw_right;
 } bte_transport;
+
+/* The slab with cells of unequal width (Sec. 3.4: cells of size dx_j, "not
+ * necessarily uniform"; the paper refines the grid near a wall, Sec. 5).
+ * dx: HOST array of nx positive widths, or NULL for nx uniform cells of
+ * [x0, x1] (x0, x1 are ignored when dx is given). */
+typedef struct {
+    int nx;
+    const double *dx;
+    double x0, x1;
+    int bc_left, bc_right;
+    double Tw_left, Tw_right;
+} bte_transport_ex;
 
 /* Create a context on CUDA device `device`. *ctx receives the handle.
  * Errors: BTE_EINVAL (ctx NULL, bad device), BTE_ECUDA. */
@@ -169,9 +185,16 @@ bte_status bte_project(bte_ctx *ctx, double *Q, const bte_instance *inst, int64_
  *   discrete outgoing flux) or specular walls, C = the homogeneous step above
  *   over all tr->nx cells (inst must be NULL and ninst == tr->nx).
  * The homogeneous and Strang steps are replayed from a CUDA graph captured on
- * the first call with a given shape. Asynchronous. Errors as bte_collide. */
+ * the first call with a given shape. Asynchronous. Errors as bte_collide.
+ * bte_step_ex: the same with a bte_transport_ex slab. On cells of unequal
+ * width the upwind reconstruction of Eq. upwind uses the upwind cell's width
+ * dx_j, and the minmod slope divided differences over the distances between
+ * cell centres, (dx_j + dx_{j+1}) / 2; the two ghost cells at each end mirror
+ * the widths of the adjacent cells; the update divides by dx_j. */
 bte_status bte_step(bte_ctx *ctx, double *f, const bte_instance *inst, int64_t ninst, double dt,
                     double eps, const bte_transport *tr, int mode, void *stream);
+bte_status bte_step_ex(bte_ctx *ctx, double *f, const bte_instance *inst, int64_t ninst, double dt,
+                       double eps, const bte_transport_ex *tr, int mode, void *stream);
 
 /* Synchronise `stream`, read and clear the device status word.
  * Returns BTE_OK, BTE_ETIMEOUT, BTE_ENONFINITE or BTE_ECUDA. */

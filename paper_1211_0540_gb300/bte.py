@@ -16,6 +16,7 @@ FP32 = 1
 LEARNED = 2
 BC_DIFFUSE = 0
 BC_SPECULAR = 1
+BC_NOFLUX = 2
 FLAG_RAW = 1
 FLAG_NO_FALLBACK = 2
 
@@ -24,7 +25,7 @@ STATUS = {0: "BTE_OK", -1: "BTE_EINVAL", -2: "BTE_ENOMEM", -3: "BTE_ECUDA", -4: 
 
 # Every symbol include/bte.h declares (checked by the ABI tests).
 EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "bte_init_weights_ex", "bte_collide",
-           "bte_collide_ex", "bte_project", "bte_step", "bte_sync_status", "bte_moments",
+           "bte_collide_ex", "bte_project", "bte_step", "bte_step_ex", "bte_sync_status", "bte_moments",
            "bte_version", "bte_profile_enable", "bte_profile_read", "bte_launch_count", "bte_batch_count", "bte_graph_count",
            "bte_set_option", "bte_get_option", "bte_collide_noalloc", "bte_tc_gemm", "bte_mlp_init", "bte_mlp_info",
            "bte_mlp_set_scales", "bte_mlp_fit_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
@@ -48,6 +49,12 @@ class Instance(ctypes.Structure):
 
 class Transport(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int),
+                ("Tw_left", ctypes.c_double), ("Tw_right", ctypes.c_double)]
+
+
+class TransportEx(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("dx", ctypes.c_void_p), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("bc_left", ctypes.c_int), ("bc_right", ctypes.c_int),
                 ("Tw_left", ctypes.c_double), ("Tw_right", ctypes.c_double)]
 
@@ -86,6 +93,8 @@ def load(path=None):
         "bte_project": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
         "bte_step": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_d, c_d,
                              ctypes.POINTER(Transport), c_int, vp]),
+        "bte_step_ex": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_d, c_d,
+                                ctypes.POINTER(TransportEx), c_int, vp]),
         "bte_sync_status": (c_int, [vp, vp]),
         "bte_moments": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
         "bte_version": (ctypes.c_char_p, []),
@@ -248,18 +257,26 @@ class Context:
         return out
 
     def step(self, f, dt, eps=1.0, transport=None, inst=None, mode=FP32, stream=None):
-        """One RK2 (homogeneous) or Strang (transport dict given) step, in place."""
+        """One RK2 (homogeneous) or Strang (transport dict given) step, in place.
+        transport keys: nx, x0, x1, bc_left, bc_right, Tw_left, Tw_right, and dx
+        (a sequence of nx cell widths, for cells of unequal width)."""
         _check_f64(f, "f")
         arr, n = self._inst(inst, f)
         tr = None
+        keep = None
         if transport is not None:
             t = transport
-            tr = Transport(int(t.get("nx", n)), float(t.get("x0", 0.0)), float(t.get("x1", 1.0)),
-                           int(t.get("bc_left", BC_DIFFUSE)), int(t.get("bc_right", BC_SPECULAR)),
-                           float(t.get("Tw_left", 1.0)), float(t.get("Tw_right", 1.0)))
+            dxp = None
+            if t.get("dx") is not None:
+                keep = (ctypes.c_double * len(t["dx"]))(*[float(x) for x in t["dx"]])
+                dxp = ctypes.cast(keep, ctypes.c_void_p)
+            tr = TransportEx(int(t.get("nx", n)), dxp, float(t.get("x0", 0.0)), float(t.get("x1", 1.0)),
+                             int(t.get("bc_left", BC_DIFFUSE)), int(t.get("bc_right", BC_SPECULAR)),
+                             float(t.get("Tw_left", 1.0)), float(t.get("Tw_right", 1.0)))
             tr = ctypes.byref(tr)
-        self._rc(self._lib.bte_step(self._h, _ptr(f), arr, n, float(dt), float(eps), tr, int(mode),
-                                    _stream(stream)), "bte_step")
+        self._rc(self._lib.bte_step_ex(self._h, _ptr(f), arr, n, float(dt), float(eps), tr, int(mode),
+                                       _stream(stream)), "bte_step")
+        del keep
         return f
 
     def profile_enable(self, on=True):

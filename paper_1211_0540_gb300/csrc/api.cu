@@ -724,6 +724,44 @@ bte_status prime_configs(bte_ctx *c) {
     return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "convolution kernel configuration");
 }
 
+// Transport coefficients of a slab with cells of widths dx[0..nx) (cached per
+// width list): alpha_c = dx_c / (2 h_{c-1/2}), gamma_c = dx_c / (2 h_{c+1/2})
+// for c = -1 .. nx (h = distance between cell centres; the ghost widths mirror
+// the adjacent cells: dx_{-1} = dx_0, dx_{-2} = dx_1, dx_nx = dx_{nx-1},
+// dx_{nx+1} = dx_{nx-2}) and 1/dx_c for c = 0 .. nx-1.
+bte_status grid_coefficients(bte_ctx *c, const double *dx, int nx, TransportArgs *ta) {
+    std::vector<double> key(dx, dx + nx);
+    auto it = c->grids.find(key);
+    if (it == c->grids.end()) {
+        auto w = [&](int k) {  // width of cell k in [-2, nx + 1]
+            if (k == -1) return dx[0];
+            if (k == -2) return dx[1];
+            if (k == nx) return dx[nx - 1];
+            if (k == nx + 1) return dx[nx - 2];
+            return dx[k];
+        };
+        std::vector<double> h((size_t)(2 * (nx + 2) + nx));
+        for (int k = -1; k <= nx; ++k) {
+            h[k + 1] = w(k) / (w(k - 1) + w(k));               // dx_k / (2 h_{k-1/2})
+            h[nx + 2 + k + 1] = w(k) / (w(k) + w(k + 1));      // dx_k / (2 h_{k+1/2})
+        }
+        for (int k = 0; k < nx; ++k) h[2 * (nx + 2) + k] = 1.0 / dx[k];
+        double *d = nullptr;
+        cudaError_t e = cudaMalloc(&d, sizeof(double) * h.size());
+        if (e != cudaSuccess) return cuda_fail(c, e, "transport grid allocation");
+        e = cudaMemcpy(d, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(c, e, "transport grid upload");
+        }
+        it = c->grids.emplace(std::move(key), d).first;
+    }
+    ta->g_alpha = it->second;
+    ta->g_gamma = it->second + (nx + 2);
+    ta->g_rdx = it->second + 2 * (nx + 2);
+    return BTE_OK;
+}
+
 bte_status check_mode(bte_ctx *c, int mode) {
     if (mode == BTE_FP64_PLAIN || mode == BTE_FP32) return BTE_OK;
     if (mode == BTE_LEARNED) {
@@ -889,6 +927,7 @@ void bte_destroy(bte_ctx *c) {
     cudaFree(c->d_counter);
     cudaFree(c->d_wall);
     for (auto &kv : c->walls) cudaFree(kv.second.d);
+    for (auto &kv : c->grids) cudaFree(kv.second);
     delete c;
 }
 
@@ -982,6 +1021,13 @@ bte_status bte_moments(bte_ctx *c, const double *f, double *out, const bte_insta
 
 bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t ninst, double dt, double eps,
                     const bte_transport *tr, int mode, void *stream) {
+    if (!tr) return bte_step_ex(c, f, inst, ninst, dt, eps, nullptr, mode, stream);
+    const bte_transport_ex ex{tr->nx, nullptr, tr->x0, tr->x1, tr->bc_left, tr->bc_right, tr->Tw_left, tr->Tw_right};
+    return bte_step_ex(c, f, inst, ninst, dt, eps, &ex, mode, stream);
+}
+
+bte_status bte_step_ex(bte_ctx *c, double *f, const bte_instance *inst, int64_t ninst, double dt, double eps,
+                       const bte_transport_ex *tr, int mode, void *stream) {
     if (!c) return BTE_EINVAL;
     if (!f) return fail(c, BTE_EINVAL, "bte_step: null f");
     if (!(dt > 0.0) || !(eps > 0.0) || !std::isfinite(dt) || !std::isfinite(eps))
@@ -993,9 +1039,14 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
     if (tr) {
         if (inst) return fail(c, BTE_EINVAL, "bte_step: transport needs uniform cells (inst == NULL)");
         if (tr->nx != ninst || tr->nx < 2) return fail(c, BTE_EINVAL, "bte_step: tr->nx must equal ninst (>= 2)");
-        if (!(tr->x1 > tr->x0)) return fail(c, BTE_EINVAL, "bte_step: x1 must exceed x0");
+        if (!tr->dx && !(tr->x1 > tr->x0)) return fail(c, BTE_EINVAL, "bte_step: x1 must exceed x0");
         for (int bc : {tr->bc_left, tr->bc_right})
-            if (bc != BTE_BC_DIFFUSE && bc != BTE_BC_SPECULAR) return fail(c, BTE_EINVAL, "bte_step: unknown wall type");
+            if (bc != BTE_BC_DIFFUSE && bc != BTE_BC_SPECULAR && bc != BTE_BC_NOFLUX)
+                return fail(c, BTE_EINVAL, "bte_step: unknown boundary type");
+        if (tr->dx)
+            for (int k = 0; k < tr->nx; ++k)
+                if (!(tr->dx[k] > 0.0) || !std::isfinite(tr->dx[k]))
+                    return fail(c, BTE_EINVAL, "bte_step: cell widths must be finite and > 0");
         if ((tr->bc_left == BTE_BC_DIFFUSE && !(tr->Tw_left > 0.0)) ||
             (tr->bc_right == BTE_BC_DIFFUSE && !(tr->Tw_right > 0.0)))
             return fail(c, BTE_EINVAL, "bte_step: wall temperatures must be > 0");
@@ -1004,9 +1055,10 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         ta.N = t0->N;
         ta.nx = tr->nx;
         ta.dv = t0->dv;
-        ta.dx = (tr->x1 - tr->x0) / tr->nx;
+        ta.dx = tr->dx ? 0.0 : (tr->x1 - tr->x0) / tr->nx;
         ta.bc_left = tr->bc_left;
         ta.bc_right = tr->bc_right;
+        if (tr->dx && (s = grid_coefficients(c, tr->dx, tr->nx, &ta)) != BTE_OK) return s;
         if (ta.bc_left == BTE_BC_DIFFUSE &&
             (s = wall_table(c, t0, tr->Tw_left, 0, &ta.mw_left, &ta.den_left)) != BTE_OK)
             return s;
@@ -1046,13 +1098,22 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         return r;
     }
     if (mode == BTE_LEARNED) return fail(c, BTE_EINVAL, "bte_step: use bte_collide for the learned mode");
+    // the slab (walls, temperatures, cell widths) is baked into the graph too
+    std::vector<double> trdesc;
+    if (tr) {
+        trdesc = {(double)tr->nx, tr->x0, tr->x1, (double)tr->bc_left, (double)tr->bc_right, tr->Tw_left,
+                  tr->Tw_right, tr->dx ? 1.0 : 0.0};
+        if (tr->dx) trdesc.insert(trdesc.end(), tr->dx, tr->dx + tr->nx);
+    }
+    const int trkey = tr ? (int)(fnv1a(trdesc.data(), sizeof(double) * trdesc.size()) & 0x7fffffff) | 1 : 0;
     GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
-                 tr ? 1 : 0, dt, eps, f, stream};
+                 trkey, dt, eps, f, stream};
     auto it = c->graphs.find(key);
-    if (it != c->graphs.end() && inst &&
-        (it->second.inst.size() != (size_t)ninst ||
-         std::memcmp(it->second.inst.data(), inst, sizeof(bte_instance) * ninst) != 0)) {
-        // another instance list with the same count and hash: capture anew. A
+    if (it != c->graphs.end() &&
+        ((inst && (it->second.inst.size() != (size_t)ninst ||
+                   std::memcmp(it->second.inst.data(), inst, sizeof(bte_instance) * ninst) != 0)) ||
+         it->second.trdesc != trdesc)) {
+        // another instance list or slab with the same hashes: capture anew. A
         // replay of the old graph may still be in flight, which the driver lets
         // finish before it frees the executable.
         cudaGraphExecDestroy(it->second.exec);
@@ -1085,6 +1146,7 @@ bte_status bte_step(bte_ctx *c, double *f, const bte_instance *inst, int64_t nin
         rec.prof = c->cap_prof;
         rec.launches = c->cap_launches;
         if (inst) rec.inst.assign(inst, inst + ninst);
+        rec.trdesc = trdesc;
         c->cap_prof.clear();
         if (r != BTE_OK || e != cudaSuccess) {
             if (g) cudaGraphDestroy(g);

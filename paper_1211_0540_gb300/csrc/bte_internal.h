@@ -120,6 +120,7 @@ struct GraphRec {
     std::vector<ProfEntry> prof;  // events baked into the graph
     int64_t launches = 0;         // kernels per replay
     std::vector<bte_instance> inst;  // the instance list the graph was captured for (the key holds a hash)
+    std::vector<double> trdesc;      // the slab it was captured for (walls, temperatures, widths; hashed in the key)
 };
 
 }  // namespace bte
@@ -155,6 +156,9 @@ struct bte_ctx {
     int64_t launches = 0, cap_launches = 0;
     double *d_wall = nullptr;  // unused scratch word pair
     std::map<std::tuple<int, double, double>, bte::WallTable> walls;  // (N, dv, T_w) -> M_w
+    // transport coefficients of slabs with cells of unequal width, per width list:
+    // device array [alpha (nx + 2) | gamma (nx + 2) | 1/dx (nx)]
+    std::map<std::vector<double>, double *> grids;
     int conv_warps = 4;        // warps per CTA of the convolution kernel
     int conv_stages = 0;       // pipeline depth (blocks in flight per warp); 0 = automatic
     int conv_merge = 16;       // blocks per compensated (TwoSum) merge

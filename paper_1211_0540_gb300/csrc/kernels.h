@@ -104,6 +104,9 @@ struct TransportArgs {
     int bc_left, bc_right;
     const double *mw_left, *mw_right;
     double den_left, den_right;
+    // cells of unequal width (null: uniform dx): device arrays alpha, gamma
+    // (cells -1 .. nx, index c + 1) and 1/dx (cells 0 .. nx-1); see transport.cu
+    const double *g_alpha = nullptr, *g_gamma = nullptr, *g_rdx = nullptr;
     // filled per sub-step by launch_transport_half:
     double rden_left, rden_right;   // 1 / den (0 when den is 0)
     double kv[kTransportMaxN];      // (tau / dx) v1_i,  v1_i = dv (i - N/2)

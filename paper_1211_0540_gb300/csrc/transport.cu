@@ -1,4 +1,5 @@
-// Transport sub-step of Sec. 3.4 on a 1-D slab of nx uniform cells:
+// Transport sub-step of Sec. 3.4 on a 1-D slab of nx cells (uniform, or of
+// unequal widths: transport_grid_stage_kernel below):
 //   df/dt + v1 df/dx = 0, finite volumes with the second-order upwind flux of
 //   Eq. upwind: F_{j+1/2} = v1 (f_j + dx/2 s_j) if v1 >= 0, else
 //   v1 (f_{j+1} - dx/2 s_{j+1}), s_j = minmod((f_j - f_{j-1})/dx, (f_{j+1} - f_j)/dx),
@@ -18,6 +19,8 @@
 //   leaving copy the adjacent cell (zero gradient).
 // - specular: v1 -> -v1 mirror, index i -> N - i; i = 0 (v1 = -L) has no
 //   partner on the grid and its ghost value is 0.
+// - no flux for the incoming characteristics (open boundary, Sec. 3.4):
+//   incoming components 0, outgoing ones copy the adjacent cell.
 // f is [cell][M] FP64, M = N^3, velocity index fastest (coalesced rows).
 #include "kernels.h"
 
@@ -81,7 +84,10 @@ __device__ __forceinline__ double ext(const double *__restrict__ f, int x, int j
         return f[(int64_t)src * M + jm];
     }
     const bool incoming = left ? (i > h) : (i < h);  // v . n > 0
-    if (incoming) return left ? sig_l * a.mw_left[j] : sig_r * a.mw_right[j];
+    if (incoming) {
+        if (bc == BTE_BC_NOFLUX) return 0.0;  // nothing enters through an open boundary
+        return left ? sig_l * a.mw_left[j] : sig_r * a.mw_right[j];
+    }
     return f[(int64_t)(left ? 0 : a.nx - 1) * M + j];
 }
 
@@ -143,6 +149,64 @@ __global__ void __launch_bounds__(kTThreads) transport_stage_kernel(const double
         }
     }
 }
+// Cells of unequal width dx_c (Sec. 3.4). The reconstruction at a face uses
+// the upwind cell's width and the minmod slope of divided differences over
+// the distances between cell centres, h_{c+1/2} = (dx_c + dx_{c+1}) / 2:
+//   dx_c/2 s_c = minmod(alpha_c (f_c - f_{c-1}), gamma_c (f_{c+1} - f_c)),
+//   alpha_c = dx_c / (2 h_{c-1/2}),  gamma_c = dx_c / (2 h_{c+1/2})
+// (both 1/2 on a uniform grid; minmod commutes with positive factors). With
+// mm the coefficient-weighted minmod of each stencil cell, the two face values
+// of cell c differ by g = D_{c} +- (mm_upwind - mm_other) as in the uniform
+// kernel, and tau R = -(tau / dx_c) v1 g. The ghost cells' widths mirror the
+// adjacent interior cells (alpha, gamma of cells -1 and nx use them).
+template <int STAGE>
+__global__ void __launch_bounds__(kTThreads) transport_grid_stage_kernel(const double *__restrict__ src,
+                                                                          double *__restrict__ out,
+                                                                          double *__restrict__ half,
+                                                                          const __grid_constant__ TransportArgs a,
+                                                                          double tau) {
+    const int M = a.N * a.N * a.N, NN = a.N * a.N, h = a.N / 2;
+    const int c0 = blockIdx.y * kTChunk, c1 = min(c0 + kTChunk, a.nx);
+    const int ilo = (int)(blockIdx.x * blockDim.x) / NN;
+    const int ihi = min((int)((blockIdx.x + 1) * blockDim.x) - 1, M - 1) / NN;
+    double sig_l = 0.0, sig_r = 0.0;
+    if (c0 < 2 && a.bc_left == BTE_BC_DIFFUSE && ihi > h) sig_l = wall_sigma(src, a, 0);
+    if (c1 > a.nx - 2 && a.bc_right == BTE_BC_DIFFUSE && ilo < h) sig_r = wall_sigma(src, a, 1);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int i = j / NN;
+    const bool pos = i >= h;
+    const double v1 = a.dv * (double)(i - h);
+    const int x0 = pos ? c0 - 2 : c0 - 1;  // first stencil point of cell c0
+    const int ne = c1 - c0 + 3;
+    double e[kTChunk + 3];
+#pragma unroll
+    for (int d = 0; d < kTChunk + 3; ++d) e[d] = d < ne ? ext(src, x0 + d, j, i, a, sig_l, sig_r) : 0.0;
+    double D[kTChunk + 2], mm[kTChunk + 1];
+#pragma unroll
+    for (int d = 0; d < kTChunk + 2; ++d) D[d] = e[d + 1] - e[d];
+#pragma unroll
+    for (int d = 0; d < kTChunk + 1; ++d) {
+        const int cell = x0 + d + 1;  // in [-1, nx]
+        const bool live = d < ne - 2;
+        mm[d] = live ? minmod(a.g_alpha[cell + 1] * D[d], a.g_gamma[cell + 1] * D[d + 1]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < kTChunk; ++q) {
+        if (c0 + q >= c1) break;
+        const int c = c0 + q;
+        const double g = pos ? D[q + 1] + (mm[q + 1] - mm[q]) : D[q + 1] - (mm[q + 1] - mm[q]);
+        const double kv = tau * v1 * a.g_rdx[c];
+        const double own = pos ? e[q + 2] : e[q + 1];
+        const int64_t idx = (int64_t)c * M + j;
+        if (STAGE == 1) {
+            out[idx] = fma(-kv, g, own);
+            half[idx] = fma(-0.5 * kv, g, own);
+        } else {
+            out[idx] = fma(-0.5 * kv, g, half[idx]);
+        }
+    }
+}
 }  // namespace
 
 void launch_transport_half(double *f, double *f1, double *fh, const TransportArgs &ta, double tau,
@@ -159,6 +223,11 @@ void launch_transport_half(double *f, double *f1, double *fh, const TransportArg
     a.rden_left = ta.den_left > 0.0 ? 1.0 / ta.den_left : 0.0;
     a.rden_right = ta.den_right > 0.0 ? 1.0 / ta.den_right : 0.0;
     dim3 grid((M + kTThreads - 1) / kTThreads, (ta.nx + kTChunk - 1) / kTChunk);
+    if (ta.g_rdx) {
+        transport_grid_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, fh, a, tau);
+        transport_grid_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f1, f, fh, a, tau);
+        return;
+    }
     transport_stage_kernel<1><<<grid, kTThreads, 0, st>>>(f, f1, fh, a);
     transport_stage_kernel<2><<<grid, kTThreads, 0, st>>>(f1, f, fh, a);
 }

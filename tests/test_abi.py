@@ -39,3 +39,17 @@ def test_binding_rejects_missing_library(tmp_path):
             bte.load(str(tmp_path / "missing.so"))
         finally:
             bte._lib = None
+
+
+def test_binding_argument_counts_match_the_header():
+    """Every ctypes signature of the binding has as many arguments as the
+    declaration in include/bte.h (a CPU-side check of the marshalling)."""
+    from paper_1211_0540_gb300 import bte
+    src = open(os.path.join(ROOT, "include", "bte.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    lib = bte.load()
+    for name in declared_symbols():
+        m = re.search(r"\b" + name + r"\s*\(([^)]*)\)", src)
+        params = m.group(1).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes) == n, name
