@@ -42,7 +42,8 @@ WORKLOAD = ("sudden wall heating: 128 cells x N=16^3 velocities (L=6, hard spher
             "Tw=2 diffuse / specular), one Strang step = 2 transport half steps + RK2 over "
             "128 cells = 256 collision evals")
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-WORKLOADS = ("wall-heating", "wall-heating-200", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16")
+WORKLOADS = ("wall-heating", "wall-heating-200", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16",
+             "sudden-heating-refined", "collision-models")
 SMS, FP32_LANES = 152, 128
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -889,6 +890,118 @@ def run_wall200(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         "clocks": clocks})
 
 
+def run_refined(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """The paper's own sudden-heating set-up (Sec. 5): Knudsen number 1, eight
+    cells per mean free path at the heated wall and two inside (56 cells of
+    unequal width on [0, 20]), diffuse wall at T = 2, no flux for incoming
+    characteristics at the far end; N = 16, hard spheres; 100 Strang steps at
+    CFL 0.5 of the smallest cell, FP32 path and plain FP64 operator."""
+    n, lam, eps, nsteps = 16, 1.0, 1.0, 100
+    dx = inputs.sudden_heating_grid()
+    nx = dx.size
+    ctx.init_weights([(n, L, lam)])
+    dt = 0.5 * dx.min() / L
+    tr = dict(nx=nx, dx=list(dx), bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_NOFLUX, Tw_left=TW, Tw_right=1.0)
+    f0 = inputs.wall_heating_initial(n, L, nx)
+    tuned = tune(args, ctx, torch.from_numpy(f0).cuda(), stream, reps=5)
+    out, ms = {}, {}
+    sampler.start()
+    n0 = ctx.launch_count()
+    for name, mode in (("fp32", bte.FP32), ("fp64_plain", bte.FP64_PLAIN)):
+        f = torch.from_numpy(f0.copy()).cuda()
+        with torch.cuda.stream(stream):
+            ctx.step(f, dt, eps, transport=tr, mode=mode, stream=stream)  # capture, then restart
+        ctx.sync_status(stream)
+        f.copy_(torch.from_numpy(f0))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(nsteps):
+                ctx.step(f, dt, eps, transport=tr, mode=mode, stream=stream)
+            e1.record(stream)
+        ctx.sync_status(stream)
+        ms[name] = e0.elapsed_time(e1)
+        out[name] = f.cpu().numpy().reshape(nx, -1)
+        if name == "fp32":
+            launches = ctx.launch_count() - n0
+    clocks = sampler.stop()
+    dv3 = (2 * L / n) ** 3
+    mass = {k: float((dx[:, None] * v).sum() * dv3) for k, v in out.items()}
+    dev = float(np.abs(out["fp32"] - out["fp64_plain"]).max() / np.abs(out["fp64_plain"]).max())
+    pick = [0, 1, 8, 16, 30, nx - 1]
+    Qg = ctx.collide(torch.from_numpy(out["fp32"]).cuda().reshape(-1), mode=bte.FP32, stream=stream)
+    ctx.sync_status(stream)
+    Qg = Qg.cpu().numpy().reshape(nx, -1)
+    Qo = oracle.collide(n, L, lam, out["fp32"][pick])
+    Qm = oracle.collide(n, L, lam, out["fp32"][pick], part=1, project=False)
+    rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+    evals = 2 * nx
+    value = evals * nsteps / (ms["fp32"] * 1e-3)
+    # bulk velocity profile u1(x) of the final state (the quantity of the paper's Fig. 1)
+    v1 = inputs.velocity_nodes(n, L)[0].ravel()
+    rho = out["fp32"].sum(axis=1) * dv3
+    u1 = (out["fp32"] * v1).sum(axis=1) * dv3 / rho
+    wl = ("sudden heating on the paper's refined grid (Sec. 5): Kn = 1, 56 cells of [0, 20] (dx 1/8 at the wall, "
+          "~1/2 inside), diffuse wall Tw = 2 / no flux for incoming characteristics, N = 16, L = 6, hard spheres, "
+          "100 Strang steps at CFL 0.5 of the smallest cell")
+    return _line(args, "cell-collision evals/s, refined-grid sudden heating (FP32 operator)", value, UNIT,
+                 ms["fp32"] / nsteps, wl, {
+        "steps": nsteps, "fp64_plain": {"value": evals * nsteps / (ms["fp64_plain"] * 1e-3), "unit": UNIT},
+        "autotuned": tuned, "dt": dt,
+        "mass": {"initial": float((dx[:, None] * f0).sum() * dv3), "final": mass,
+                 "note": "the open boundary lets gas leave; the diffuse wall keeps its own balance"},
+        "bulk_velocity_u1": {"x_centres": (np.cumsum(dx) - 0.5 * dx).round(4).tolist(), "u1": u1.round(6).tolist()},
+        "accuracy": {"state_max_dev_fp32_vs_fp64_rel": dev,
+                     "final_state_Q_rel_l2_loss_norm_max": float(rel.max()), "cells_checked": pick},
+        "gpu_launches": launches, "clocks": clocks})
+
+
+def run_models(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+    """One projected FP32 collision evaluation of 128 bi-Maxwellian cells at N = 16
+    for each collision model the weights encode (Sec. 2.2): hard spheres,
+    variable hard potentials (lambda = 0.5, weights by quadrature), Maxwell
+    molecules, and inelastic collisions (beta = 0.8, 0.6; energy row dropped)."""
+    n, nc = 16, 128
+    models = [(1.0, 1.0), (0.5, 1.0), (0.0, 1.0), (1.0, 0.8), (0.0, 0.6)]
+    ids = ctx.init_weights([(n, L, lam, beta) for lam, beta in models])
+    f = inputs.homogeneous_cells(n, L, nc, seed=9)
+    M = n ** 3
+    buf = np.concatenate([f.reshape(-1)] * len(models))
+    fb = torch.from_numpy(buf).cuda()
+    rows = []
+    sampler.start()
+    tuned = None
+    for k, (lam, beta) in enumerate(models):
+        inst = [(ids[k], (k * nc + c) * M) for c in range(nc)]
+        if k == 0:  # one batch shape for all models: one configuration
+            tuned = tune(args, ctx, fb, stream, inst=inst, reps=3)
+        Q = torch.zeros_like(fb)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ctx.collide(fb, Q, inst=inst, mode=bte.FP32, stream=stream)
+        ms = _timed_steps(torch, lambda: ctx.collide(fb, Q, inst=inst, mode=bte.FP32, stream=stream), args.steps,
+                          stream, flush, tag="model%d" % k)
+        ctx.sync_status(stream)
+        Qg = Q.cpu().numpy()[k * nc * M:(k + 1) * nc * M].reshape(nc, M)
+        pick = [0, 37, nc - 1]
+        Qo = oracle.collide(n, L, lam, f[pick], beta=beta)
+        Qm = oracle.collide(n, L, lam, f[pick], part=1, project=False, beta=beta)
+        rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
+        mom = oracle.moments(n, L, Qg)
+        rows.append({"lambda": lam, "beta": beta, "evals_per_s": nc * args.steps / (sum(ms) * 1e-3),
+                     "rel_l2_loss_norm_max": float(rel.max()), "cells_checked": pick,
+                     "max_abs_mass_momentum_moment": float(np.abs(mom[:, :4]).max()),
+                     "energy_moment_mean": float(mom[:, 4].mean())})
+    clocks = sampler.stop()
+    wl = ("collision models in the weights (Sec. 2.2): 128 bi-Maxwellian cells at N = 16, L = 6; (lambda, beta) "
+          "= (1, 1), (0.5, 1), (0, 1), (1, 0.8), (0, 0.6); one projected FP32 evaluation per step")
+    value = rows[0]["evals_per_s"]
+    return _line(args, "cell-collision evals/s per collision model (FP32 operator, N=16)", value, UNIT,
+                 nc / value * 1e3, wl, {"models": rows, "autotuned": tuned, "clocks": clocks})
+
+
 def run_secondary(args):
     import torch
 
@@ -914,7 +1027,8 @@ def run_secondary(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)
     fn = {"homog-1cell": run_homog1, "sweep-n32": run_sweep32, "uneven-4096": run_uneven,
-          "learned-n16": run_learned, "wall-heating-200": run_wall200}[args.workload]
+          "learned-n16": run_learned, "wall-heating-200": run_wall200, "sudden-heating-refined": run_refined,
+          "collision-models": run_models}[args.workload]
     line = fn(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler)
     print(json.dumps(line), flush=True)
     ctx.close()
