@@ -92,6 +92,7 @@ def parse():
     ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
                     help="wall-heating (the headline line) or one of the secondary workloads")
+    ap.add_argument("--cells", type=int, default=256, help="sweep-n32: number of cells (default 256)")
     ap.add_argument("--train-states", type=int, default=200000, help="learned-n16: training pairs")
     ap.add_argument("--epochs", type=int, default=30, help="learned-n16: training epochs")
     return ap.parse_args()
@@ -566,7 +567,7 @@ def run_homog1(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
 def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     """256 bi-Maxwellian cells at N = 32 (means ~ U(-1.5, 1.5)^3), FP32 operator;
     oracle on 16 seeded cells; plain FP64 operator timed once."""
-    n, lam, nc = 32, 1.0, 256
+    n, lam, nc = 32, 1.0, args.cells
     ctx.init_weights([(n, L, lam)])
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
@@ -611,8 +612,8 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     pairs = conv_pairs_per_cell(n)
     conv_ms = conv[0] / max(conv[1], 1)
     achieved = 10.0 * pairs * nc / (conv_ms * 1e-3) / 1e12
-    wl = ("precision sweep: 256 bi-Maxwellian cells (means ~ U(-1.5,1.5)^3, T ~ U(0.5,2), seed 3), "
-          "N=32, L=6, hard spheres; one projected collision evaluation of all cells per step")
+    wl = ("precision sweep: %d bi-Maxwellian cells (means ~ U(-1.5,1.5)^3, T ~ U(0.5,2), seed 3), "
+          "N=32, L=6, hard spheres; one projected collision evaluation of all cells per step" % nc)
     return _line(args, "cell-collision evals/s at N=32 (FP32 operator)", value, UNIT, tot / args.steps, wl, {
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

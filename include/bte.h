@@ -245,7 +245,12 @@ bte_status bte_graph_count(const bte_ctx *ctx, int64_t *count);
  *                      thread (2 CTAs per SM), 4 (default) = as 2 with each
  *                      warp's compensated sums in shared memory instead of
  *                      registers (the b-row stays in registers as packed
- *                      operands for the whole block);
+ *                      operands for the whole block), 5 = as 4 with the weights
+ *                      built on the fly: each warp computes its block's
+ *                      pair-symmetrised weights from the radial integrals
+ *                      I(|k'|^2, |2m' - k'|^2) and J(|m'|^2) (FP32 tables of
+ *                      0.5 MB at N = 16, 9 MB at N = 32) instead of streaming
+ *                      the stored weight table (elastic tables only);
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
  *       "conv_stages" blocks in flight per warp (1..4; 0 = automatic, the
  *                      default: the deepest ring up to 2 that keeps the

@@ -534,6 +534,10 @@ bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
     } else if (mode == BTE_FP32) {
         ConvLaunch L;
         const ConvCfg g = cfg_of(c, B);
+        if (g.impl == 5)
+            for (const Segment &sg : B->segs)
+                if (!c->tables[sg.table]->d_I32)
+                    return fail(c, BTE_EINVAL, "conv_impl 5 (weights on the fly) needs elastic tables (beta = 1)");
         cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, g.warps, g.stages, g.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
     }
@@ -597,7 +601,7 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, cfg.warps, cfg.stages, cfg.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
         ConvParams p{};
-        const bool split = cfg.impl == 4 && cfg.csplit && B->nsplit > 0;
+        const bool split = cfg.impl >= 4 && cfg.csplit && B->nsplit > 0;
         p.items = split ? B->d_items_split : B->d_items;
         p.nitems = split ? B->nitems_split : B->nitems;
         p.counter = B->d_counters;
@@ -609,8 +613,14 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         p.F = (const float2 *)c->scratch[SC_F];
         p.Qh = (float2 *)c->scratch[SC_QH];
         for (size_t i = 0; i < c->tables.size() && i < (size_t)kMaxTables; ++i) {
-            p.W[i] = c->tables[i]->d_w32;
-            p.D[i] = c->tables[i]->d_desc;
+            const Table *t = c->tables[i];
+            p.W[i] = t->d_w32;
+            p.D[i] = t->d_desc;
+            p.I32[i] = t->d_I32;
+            p.J32[i] = t->d_J32;
+            p.E[i] = t->d_etab;
+            p.nq[i] = t->nq;
+            p.estride[i] = t->estride;
         }
         p.status = c->d_status;
         p.merge = cfg.merge;
@@ -1228,7 +1238,7 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 }
 
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
-    if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 4; return &c->conv_impl; }
+    if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 5; return &c->conv_impl; }
     if (!std::strcmp(name, "dft_split")) { *lo = 1; *hi = 4; return &c->dft_split; }
     if (!std::strcmp(name, "debug_conv_stall")) { *lo = 0; *hi = 1; return &c->debug_conv_stall; }
     if (!std::strcmp(name, "profile_mask")) { *lo = 0; *hi = 63; return &c->prof_mask; }
@@ -1547,7 +1557,7 @@ bte_status bte_tune_load(bte_ctx *c, const char *path, int *loaded) {
                         "\"split\": %d, \"csplit\": %d, \"ms\": %lf}",
                         key, &g.impl, &g.warps, &g.stages, &g.merge, &g.split, &g.csplit, &g.ms) != 8)
             return fail(c, BTE_EINVAL, "bte_tune_load: malformed entry: " + line);
-        if (g.impl < 0 || g.impl > 4 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
+        if (g.impl < 0 || g.impl > 5 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
             g.csplit < 0 || g.csplit > 1 ||
             (g.split != 1 && g.split != 2 && g.split != 4))
             return fail(c, BTE_EINVAL, "bte_tune_load: out-of-range entry: " + line);

@@ -67,6 +67,12 @@ struct Table {
     double *d_w64 = nullptr;
     uint64_t *d_w64_off = nullptr;       // per k (M + 1 entries)
     size_t n_w64 = 0;
+    // On-the-fly weights (beta = 1): I and J in FP32 times sqrt(2/pi) dz^3, and
+    // per k3 tile and block entry (kernel order) the third components of the
+    // weight invariants as four 16-bit fields (estride entries per tile)
+    float *d_I32 = nullptr, *d_J32 = nullptr;
+    uint16_t *d_etab = nullptr;
+    int estride = 0;
     // Work items of one 32-cell group (fofs 0, table 0), every k3 tile and
     // pencil with kept blocks, costliest first: the set-up-time template from
     // which bte_collide_noalloc expands its work list on the device.

@@ -141,8 +141,9 @@ struct WarpRing {
     int stage_bytes;
 };
 
-// Issue the three bulk copies of block j of the item into stage s (lane 0 only).
-template <class K>
+// Issue the three bulk copies of block j of the item into stage s (lane 0 only);
+// with OTF only the two rows (the warp builds the weights, gen_weights).
+template <class K, bool OTF = false>
 __device__ __forceinline__ void issue_block(const WarpRing &r, int s, const ConvItem &it,
                                             const ConvParams &p, int j) {
     const uint32_t d = p.D[it.table][it.desc_off + j];
@@ -158,10 +159,62 @@ __device__ __forceinline__ void issue_block(const WarpRing &r, int s, const Conv
     const float *w = p.W[it.table] + it.wofs + (size_t)j * K::cpad;
     char *dst = r.base + s * r.stage_bytes;
     const uint32_t bar = r.bars + 8u * s;
-    mbar_expect_tx(bar, (uint32_t)K::stage_bytes);
+    mbar_expect_tx(bar, (uint32_t)(OTF ? 2 * K::row_bytes : K::stage_bytes));
     bulk_g2s(smem_u32(dst), arow, K::row_bytes, bar);
     bulk_g2s(smem_u32(dst + K::row_bytes), brow, K::row_bytes, bar);
-    bulk_g2s(smem_u32(dst + 2 * K::row_bytes), w, K::cpad * 4, bar);
+    if (!OTF) bulk_g2s(smem_u32(dst + 2 * K::row_bytes), w, K::cpad * 4, bar);
+}
+
+// The weights of block j of the item, built by the whole warp into the weight
+// slot of stage s from the radial integrals (conv_impl 5, the weights computed
+// on the fly instead of streamed, Sec. 5's remark on storing Ghat). With
+// k' = k - N/2 (likewise m', n' = k' - m') the block's pair weight is
+//   Ghat(k, m) + Ghat(k, n) = [I(|k'|^2, |2m' - k'|^2) - J(|m'|^2)] + [I(..) - J(|n'|^2)],
+// the gain arguments of m and n being equal (|2n' - k'| = |k' - 2m'|); a block
+// that pairs with itself keeps Ghat(k, m). I and J carry sqrt(2/pi) dz^3.
+// Entry e of the tile has the third-component parts of the four invariants
+// precomputed, C[e] = (k3'^2 | (2m3' - k3')^2 << 16, m3'^2 | n3'^2 << 16); the
+// padding up to cpad is 0. Lane l builds entries l, l + 32, ...: all its
+// table reads are issued before the first weight is formed (one memory
+// latency per block instead of one per entry).
+template <class K>
+__device__ __forceinline__ void gen_weights(const WarpRing &r, int s, const ConvItem &it, const ConvParams &p, int jb,
+                                            int lane) {
+    constexpr int NE = (K::cpad + kLanes - 1) / kLanes;
+    const uint32_t d = p.D[it.table][it.desc_off + jb];
+    const int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16);
+    const int n1 = (int)it.k1 - m1 + K::H, n2 = (int)it.k2 - m2 + K::H;
+    const bool valid = m1 < K::N && m2 < K::N && n1 >= 0 && n1 < K::N && n2 >= 0 && n2 < K::N;
+    const int k1 = (int)it.k1 - K::H, k2 = (int)it.k2 - K::H, a1 = m1 - K::H, a2 = m2 - K::H;
+    const int p12 = k1 * k1 + k2 * k2;
+    const int q12 = (2 * a1 - k1) * (2 * a1 - k1) + (2 * a2 - k2) * (2 * a2 - k2);
+    const int sm12 = a1 * a1 + a2 * a2, sn12 = (k1 - a1) * (k1 - a1) + (k2 - a2) * (k2 - a2);
+    const bool pair = !(m1 == n1 && m2 == n2);
+    const float *__restrict__ I = p.I32[it.table];
+    const float *__restrict__ J = p.J32[it.table];
+    const int nq = p.nq[it.table];
+    const uint2 *__restrict__ C =
+        reinterpret_cast<const uint2 *>(p.E[it.table]) + (K::K0 / K::T) * p.estride[it.table];
+    float g[NE], gm[NE], gn[NE];
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+        const int e = lane + t * kLanes;
+        g[t] = gm[t] = gn[t] = 0.f;
+        if (valid && e < K::count()) {
+            const uint2 c = __ldg(C + e);
+            const int pp = p12 + (int)(c.x & 0xffffu), q = q12 + (int)(c.x >> 16);
+            g[t] = __ldg(I + (size_t)pp * nq + q);
+            gm[t] = __ldg(J + sm12 + (int)(c.y & 0xffffu));
+            gn[t] = __ldg(J + sn12 + (int)(c.y >> 16));
+        }
+    }
+    float *w = reinterpret_cast<float *>(r.base + s * r.stage_bytes + 2 * K::row_bytes);
+#pragma unroll
+    for (int t = 0; t < NE; ++t) {
+        const int e = lane + t * kLanes;
+        const float a = g[t] - gm[t];
+        if (e < K::cpad) w[e] = pair ? a + (g[t] - gn[t]) : a;
+    }
 }
 
 // Process one item; returns false if a wait timed out (the ring is drained).
@@ -489,7 +542,7 @@ constexpr int kSumsBytes = 4 * 16 * kLanes * 4;
 // bytes. Returns false if this warp timed out.
 // pre: the copies of this warp's first block were issued before (during the
 // previous item's reduction).
-template <class K>
+template <class K, bool OTF>
 __device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane, int warp,
                              int nwarps, float *sums, bool pre) {
     constexpr int T = K::T;
@@ -498,7 +551,9 @@ __device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &
     const int mine = nb > warp ? (nb - warp + nwarps - 1) / nwarps : 0;
     if (lane == 0)
         for (int s = pre ? 1 : 0; s < S && s < mine; ++s)
-            if (!(p.stall && s == 0)) issue_block<K>(r, s, it, p, warp + s * nwarps);
+            if (!(p.stall && s == 0)) issue_block<K, OTF>(r, s, it, p, warp + s * nwarps);
+    if (OTF)
+        for (int s = pre ? 1 : 0; s < S && s < mine; ++s) gen_weights<K>(r, s, it, p, warp + s * nwarps, lane);
 #pragma unroll
     for (int q = 0; q < 4 * T; ++q) sums[q * kLanes + lane] = 0.f;
     __syncwarp();
@@ -536,7 +591,11 @@ __device__ bool coop_item_sm(WarpRing &r, const ConvItem &it, const ConvParams &
             }
         }
         __syncwarp();
-        if (lane == 0 && i + S < mine) issue_block<K>(r, s, it, p, warp + (i + S) * nwarps);
+        if (lane == 0 && i + S < mine) issue_block<K, OTF>(r, s, it, p, warp + (i + S) * nwarps);
+        if (OTF && i + S < mine) {
+            gen_weights<K>(r, s, it, p, warp + (i + S) * nwarps, lane);
+            __syncwarp();
+        }
     }
     if (!ok) {
         const int last = mine < i + S ? mine : i + S;
@@ -595,18 +654,35 @@ __device__ __forceinline__ void coop_reduce_split(const ConvItem &it, const Conv
 
 // Copies of this warp's first block of item it into stage 0 (lane 0 only),
 // for any kind compiled into the kernel.
-template <unsigned MASK>
+template <unsigned MASK, bool OTF>
 __device__ __forceinline__ void issue_first_any(const WarpRing &r, const ConvItem &it, const ConvParams &p,
                                                 int warp) {
     if ((int)it.nblocks <= warp || p.stall) return;
     switch (it.kind) {
-        case 0: if (MASK & 1u) issue_block<K8>(r, 0, it, p, warp); break;
-        case 1: if (MASK & 2u) issue_block<K12>(r, 0, it, p, warp); break;
-        case 2: if (MASK & 4u) issue_block<K16>(r, 0, it, p, warp); break;
-        case 3: if (MASK & 8u) issue_block<K24a>(r, 0, it, p, warp); break;
-        case 4: if (MASK & 16u) issue_block<K24b>(r, 0, it, p, warp); break;
-        case 5: if (MASK & 32u) issue_block<K32a>(r, 0, it, p, warp); break;
-        case 6: if (MASK & 64u) issue_block<K32b>(r, 0, it, p, warp); break;
+        case 0: if (MASK & 1u) issue_block<K8, OTF>(r, 0, it, p, warp); break;
+        case 1: if (MASK & 2u) issue_block<K12, OTF>(r, 0, it, p, warp); break;
+        case 2: if (MASK & 4u) issue_block<K16, OTF>(r, 0, it, p, warp); break;
+        case 3: if (MASK & 8u) issue_block<K24a, OTF>(r, 0, it, p, warp); break;
+        case 4: if (MASK & 16u) issue_block<K24b, OTF>(r, 0, it, p, warp); break;
+        case 5: if (MASK & 32u) issue_block<K32a, OTF>(r, 0, it, p, warp); break;
+        case 6: if (MASK & 64u) issue_block<K32b, OTF>(r, 0, it, p, warp); break;
+        default: break;
+    }
+}
+
+// The weights of that first block (all lanes of the warp; conv_impl 5).
+template <unsigned MASK>
+__device__ __forceinline__ void gen_first_any(const WarpRing &r, const ConvItem &it, const ConvParams &p, int warp,
+                                              int lane) {
+    if ((int)it.nblocks <= warp || p.stall) return;
+    switch (it.kind) {
+        case 0: if (MASK & 1u) gen_weights<K8>(r, 0, it, p, warp, lane); break;
+        case 1: if (MASK & 2u) gen_weights<K12>(r, 0, it, p, warp, lane); break;
+        case 2: if (MASK & 4u) gen_weights<K16>(r, 0, it, p, warp, lane); break;
+        case 3: if (MASK & 8u) gen_weights<K24a>(r, 0, it, p, warp, lane); break;
+        case 4: if (MASK & 16u) gen_weights<K24b>(r, 0, it, p, warp, lane); break;
+        case 5: if (MASK & 32u) gen_weights<K32a>(r, 0, it, p, warp, lane); break;
+        case 6: if (MASK & 64u) gen_weights<K32b>(r, 0, it, p, warp, lane); break;
         default: break;
     }
 }
@@ -615,11 +691,11 @@ __device__ __forceinline__ void issue_first_any(const WarpRing &r, const ConvIte
 // item is taken from the queue (into *s_next) and each warp issues the copies
 // of its first block into its now idle ring before the CTA reduces this item's
 // sums, which live outside the rings.
-template <class K, unsigned MASK>
+template <class K, unsigned MASK, bool OTF>
 __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
                                             int warp, int nwarps, char *ring0, int *abort_flag, float *sums,
                                             int sums_off, int sp, int *s_last, bool pre, int *s_next) {
-    const bool ok = coop_item_sm<K>(r, it, p, lane, warp, nwarps, sums, pre);
+    const bool ok = coop_item_sm<K, OTF>(r, it, p, lane, warp, nwarps, sums, pre);
     if (!ok && lane == 0) {
         atomicOr(p.status, ST_TIMEOUT);
         *abort_flag = 1;
@@ -631,7 +707,11 @@ __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, con
     if (nx < p.nitems && lane == 0) {
         // the ring was last read by generic loads; order them before the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        issue_first_any<MASK>(r, p.items[nx], p, warp);
+        issue_first_any<MASK, OTF>(r, p.items[nx], p, warp);
+    }
+    if (OTF && nx < p.nitems) {
+        gen_first_any<MASK>(r, p.items[nx], p, warp, lane);
+        __syncwarp();
     }
     if (!*abort_flag) {
         if (sp < 0) coop_reduce<K>(it, p, lane, warp, nwarps, ring0, p.warp_smem, sums_off);
@@ -642,7 +722,7 @@ __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, con
     return !*abort_flag;
 }
 
-template <unsigned MASK>
+template <unsigned MASK, bool OTF = false>
 __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
     extern __shared__ __align__(128) char smem[];
     __shared__ int s_item, s_abort, s_last;
@@ -672,13 +752,13 @@ __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
         const int sp = p.split ? p.split[idx] : -1;
         bool ok = true, ran = true;
         switch (it.kind) {
-            case 0: if (MASK & 1u) ok = coop_run_sm<K8, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 1: if (MASK & 2u) ok = coop_run_sm<K12, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 2: if (MASK & 4u) ok = coop_run_sm<K16, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 3: if (MASK & 8u) ok = coop_run_sm<K24a, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 4: if (MASK & 16u) ok = coop_run_sm<K24b, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 5: if (MASK & 32u) ok = coop_run_sm<K32a, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 6: if (MASK & 64u) ok = coop_run_sm<K32b, MASK>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 0: if (MASK & 1u) ok = coop_run_sm<K8, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 1: if (MASK & 2u) ok = coop_run_sm<K12, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 2: if (MASK & 4u) ok = coop_run_sm<K16, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 3: if (MASK & 8u) ok = coop_run_sm<K24a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 4: if (MASK & 16u) ok = coop_run_sm<K24b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 5: if (MASK & 32u) ok = coop_run_sm<K32a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 6: if (MASK & 64u) ok = coop_run_sm<K32b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
             default: ran = false; break;
         }
         if (!ok) break;
@@ -788,7 +868,7 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     for (int k = 0; k < kNumKinds; ++k)
         if (kinds_mask & (1u << k)) stage = stage > conv_stage_bytes(k) ? stage : conv_stage_bytes(k);
     L.stages = stages > kMaxStages ? kMaxStages : stages;
-    L.warp_smem = stage * L.stages + (impl == 4 ? kSumsBytes : 0);
+    L.warp_smem = stage * L.stages + (impl >= 4 ? kSumsBytes : 0);
     const int max_smem = 227 * 1024;
     const int max_warps = impl == 0 ? 8 : 4;
     int warps = warps_per_cta < 1 ? 1 : (warps_per_cta > max_warps ? max_warps : warps_per_cta);
@@ -807,7 +887,8 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
     } else {
         const bool packed = impl >= 2;
 #define BTE_PICK(M)                                                                             \
-    L.fn = impl == 4   ? conv32_sums_kernel<M>                                                 \
+    L.fn = impl == 5   ? conv32_sums_kernel<M, true>                                           \
+           : impl == 4 ? conv32_sums_kernel<M>                                                 \
            : impl == 3 ? conv32_coop_kernel<M, true, 2>                                        \
                        : (packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>)
         switch (kinds_mask) {

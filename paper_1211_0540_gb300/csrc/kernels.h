@@ -52,6 +52,15 @@ struct ConvParams {
     const int *split;
     float *part;
     unsigned *split_cnt;
+    // Weights built on the fly (conv_impl 5): per table the FP32 radial tables
+    // I32[p * nq + q] and J32[s] (already times sqrt(2/pi) dz^3) and per block
+    // entry (consumption order) the third components of the invariants,
+    // E + 4 (tile * estride + e): k3'^2, (2m3' - k3')^2, m3'^2, n3'^2.
+    const float *I32[kMaxTables];
+    const float *J32[kMaxTables];
+    const uint16_t *E[kMaxTables];
+    int nq[kMaxTables];
+    int estride[kMaxTables];
 };
 constexpr int kSplitFloats = 16 * 4 * 32;  // per half: T <= 16 outputs x (hi, lo) x (re, im) x 32 lanes
 int conv_stage_bytes(int kind);
@@ -63,7 +72,8 @@ struct ConvLaunch {
 // kinds_mask: bit i set when items of kind i are present. Sets the kernel's
 // shared-memory attribute: call outside stream capture.
 // impl: 0 = one warp per item, 1 = CTA-cooperative items, 2 = cooperative + packed f32x2,
-// 3 = as 2 at 2 CTAs per SM, 4 = as 2 with the compensated sums in shared memory.
+// 3 = as 2 at 2 CTAs per SM, 4 = as 2 with the compensated sums in shared memory,
+// 5 = as 4 with every block's weights built on the fly from the radial tables.
 cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta, int stages, int impl,
                              ConvLaunch *out);
 cudaError_t conv32_launch(const ConvLaunch &L, const ConvParams &p, cudaStream_t st);

@@ -158,6 +158,8 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
         std::snprintf(msg, sizeof msg, "bte_collide_noalloc: configuration: %s", cudaGetErrorString(e));
         return set_err(c, BTE_ECUDA, msg);
     }
+    if (g.impl == 5 && !t->d_I32)
+        return set_err(c, BTE_EINVAL, "bte_collide_noalloc: conv_impl 5 needs an elastic table 0 (beta = 1)");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nth = nitems > nslots ? nitems : nslots;
     noalloc_setup_kernel<<<(unsigned)((nth + 255) / 256), 256, 0, st>>>(t->d_tmpl, t->n_tmpl, (int)ngroups, M, ncells,
@@ -174,6 +176,11 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
     p.Qh = d_Q;
     p.W[0] = t->d_w32;
     p.D[0] = t->d_desc;
+    p.I32[0] = t->d_I32;
+    p.J32[0] = t->d_J32;
+    p.E[0] = t->d_etab;
+    p.nq[0] = t->nq;
+    p.estride[0] = t->estride;
     p.status = c->d_status;
     p.merge = g.merge;
     e = conv32_launch(L, p, st);

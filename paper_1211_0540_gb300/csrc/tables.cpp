@@ -310,10 +310,44 @@ int build_table(Table &t, std::string &err) {
     }
     t.n_tmpl = (int)tmpl.size();
 
+    // on-the-fly weights (elastic tables): radial integrals in FP32 with the
+    // constant factor, and each tile's entry list (m3 ascending, then k3)
+    std::vector<float> I32, J32;
+    std::vector<uint16_t> etab;
+    if (t.beta == 1.0) {
+        const double cw = std::sqrt(2.0 / kPi) * dz3;
+        I32.resize(t.I.size());
+        for (size_t i = 0; i < t.I.size(); ++i) I32[i] = (float)(cw * t.I[i]);
+        J32.resize(t.J.size());
+        for (size_t i = 0; i < t.J.size(); ++i) J32[i] = (float)(cw * t.J[i]);
+        // per entry (m3, k3) of a tile, in the kernel's order: the third
+        // components of the invariants, (k3'^2 | (2m3' - k3')^2 << 16,
+        // m3'^2 | n3'^2 << 16) with n3' = k3' - m3', as four 16-bit fields
+        t.estride = std::max(t.cpad[0], t.cpad[1]);
+        etab.assign((size_t)t.ntiles * t.estride * 4, 0);
+        for (int tile = 0; tile < t.ntiles; ++tile) {
+            int e = 0;
+            for (int m3 = 0; m3 < N; ++m3)
+                for (int j = 0; j < T; ++j) {
+                    const int k3 = tile * T + j, n3 = k3 - m3 + h;
+                    if (n3 < 0 || n3 >= N) continue;
+                    const int kp = k3 - h, mp = m3 - h, np3 = kp - mp;
+                    uint16_t *c = &etab[((size_t)tile * t.estride + e++) * 4];
+                    c[0] = (uint16_t)(kp * kp);
+                    c[1] = (uint16_t)((2 * mp - kp) * (2 * mp - kp));
+                    c[2] = (uint16_t)(mp * mp);
+                    c[3] = (uint16_t)(np3 * np3);
+                }
+        }
+    }
+
     // upload
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&t.d_w32, sizeof(float) * std::max<size_t>(total, 4));
     if (e == cudaSuccess) e = cudaMalloc(&t.d_tmpl, sizeof(ConvItem) * std::max<size_t>(tmpl.size(), 1));
+    if (e == cudaSuccess && !I32.empty()) e = cudaMalloc(&t.d_I32, sizeof(float) * I32.size());
+    if (e == cudaSuccess && !J32.empty()) e = cudaMalloc(&t.d_J32, sizeof(float) * J32.size());
+    if (e == cudaSuccess && !etab.empty()) e = cudaMalloc(&t.d_etab, sizeof(uint16_t) * etab.size());
     if (e == cudaSuccess) e = cudaMalloc(&t.d_desc, sizeof(uint32_t) * std::max<size_t>(t.n_desc, 1));
     if (e == cudaSuccess) e = cudaMalloc(&t.d_root32, sizeof(float2) * N);
     if (e == cudaSuccess) e = cudaMalloc(&t.d_root64, sizeof(double2) * N);
@@ -325,6 +359,12 @@ int build_table(Table &t, std::string &err) {
     e = cudaMemcpy(t.d_w32, w32.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !tmpl.empty())
         e = cudaMemcpy(t.d_tmpl, tmpl.data(), sizeof(ConvItem) * tmpl.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !I32.empty())
+        e = cudaMemcpy(t.d_I32, I32.data(), sizeof(float) * I32.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !J32.empty())
+        e = cudaMemcpy(t.d_J32, J32.data(), sizeof(float) * J32.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !etab.empty())
+        e = cudaMemcpy(t.d_etab, etab.data(), sizeof(uint16_t) * etab.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(t.d_desc, desc.data(), sizeof(uint32_t) * t.n_desc, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(t.d_root32, r32.data(), sizeof(float2) * N, cudaMemcpyHostToDevice);
@@ -383,7 +423,12 @@ int build_table_fp64(Table &t, std::string &err) {
 void free_table(Table &t) {
     cudaFree(t.d_w32);
     cudaFree(t.d_tmpl);
+    cudaFree(t.d_I32);
+    cudaFree(t.d_J32);
+    cudaFree(t.d_etab);
     t.d_tmpl = nullptr;
+    t.d_I32 = t.d_J32 = nullptr;
+    t.d_etab = nullptr;
     cudaFree(t.d_desc);
     cudaFree(t.d_w64);
     cudaFree(t.d_w64_off);

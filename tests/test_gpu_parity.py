@@ -67,7 +67,7 @@ def run_collide(bte, N, lam, f, mode, raw=False):
     return Q.cpu().numpy().reshape(f.shape)
 
 
-@pytest.mark.parametrize("impl", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("impl", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("N,ncells,lam", [(8, 5, 1.0), (8, 70, 0.0), (12, 37, 1.0), (16, 33, 1.0),
                                           (24, 3, 1.0)])
 def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
@@ -75,7 +75,7 @@ def test_fp32_collide_matches_oracle(bte, N, ncells, lam, impl):
     c = ctx_for(bte, ((N, L, lam),))
     impl0, merge0 = c.get_option("conv_impl"), c.get_option("conv_merge")
     c.set_option("conv_impl", impl)
-    c.set_option("conv_merge", (1 + impl) * (1 + impl))  # 1, 4, 9, 16, 25: merges inside and across blocks
+    c.set_option("conv_merge", (1 + impl) * (1 + impl))  # 1, 4, 9, 16, 25, 36: merges inside and across blocks
     try:
         Qg = run_collide(bte, N, lam, f, bte.FP32)
     finally:
@@ -805,3 +805,33 @@ def test_refined_grid_conserves_mass_with_walls(bte):
     m0 = (dx[:, None] * f).sum()
     m1 = (dx[:, None] * ft.cpu().numpy()).sum()
     assert abs(m1 - m0) <= 1e-13 * m0
+
+
+@pytest.mark.parametrize("N,ncells,nsample,lam", [(16, 128, 4, 1.0), (32, 256, 2, 1.0), (24, 40, 2, 0.0),
+                                                  (16, 33, 3, 0.5)])
+def test_weights_on_the_fly_match_oracle(bte, N, ncells, nsample, lam):
+    """conv_impl 5: every block's weights built by the warp from the radial
+    integrals (no stored weight table read), full batches at the benchmark's
+    sizes, oracle on sampled cells, and the same split/queue machinery as
+    variant 4; refused for inelastic tables."""
+    f = inputs.precision_sweep_cells(N, L, ncells, seed=900 + N)
+    c = ctx_for(bte, ((N, L, lam),))
+    impl0 = c.get_option("conv_impl")
+    c.set_option("conv_impl", 5)
+    try:
+        Qg = run_collide(bte, N, lam, f, bte.FP32)
+    finally:
+        c.set_option("conv_impl", impl0)
+    rng = np.random.default_rng(N)
+    pick = np.sort(rng.choice(ncells - 1, size=nsample - 1, replace=False)).tolist() + [ncells - 1]
+    Qo = oracle.collide(N, L, lam, f[pick])
+    err = np.linalg.norm(Qg[pick] - Qo, axis=1) / loss_norm(N, lam, f[pick])
+    assert err.max() <= TOL32, err.max()
+    assert np.all(np.abs(oracle.moments(N, L, Qg)) <= 1e-12 * abs_moment_scale(N, Qg))
+    d = bte.Context(0)
+    d.init_weights([(8, L, 1.0, 0.8)])
+    d.set_option("conv_impl", 5)
+    with pytest.raises(bte.BteError) as e:
+        d.collide(torch.zeros(8 ** 3, dtype=torch.float64, device="cuda"), mode=bte.FP32)
+    assert e.value.code == -1
+    d.close()
