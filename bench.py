@@ -42,8 +42,8 @@ WORKLOAD = ("sudden wall heating: 128 cells x N=16^3 velocities (L=6, hard spher
             "Tw=2 diffuse / specular), one Strang step = 2 transport half steps + RK2 over "
             "128 cells = 256 collision evals")
 FLUSH_BYTES = 512 << 20  # > 129 MB L2
-WORKLOADS = ("wall-heating", "wall-heating-200", "homog-1cell", "sweep-n32", "uneven-4096", "learned-n16",
-             "sudden-heating-refined", "collision-models")
+WORKLOADS = ("wall-heating", "wall-heating-200", "homog-1cell", "sweep-n32", "sweep-n48", "uneven-4096",
+             "learned-n16", "sudden-heating-refined", "collision-models")
 SMS, FP32_LANES = 152, 128
 PROFILES = os.path.join(ROOT, "profiles")
 
@@ -564,15 +564,22 @@ def run_homog1(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                   "gpu_launches": launches, "clocks": clocks})
 
 
-def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
+def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler, n=32):
     """256 bi-Maxwellian cells at N = 32 (means ~ U(-1.5, 1.5)^3), FP32 operator;
-    oracle on 16 seeded cells; plain FP64 operator timed once."""
-    n, lam, nc = 32, 1.0, args.cells
+    oracle on 16 seeded cells; plain FP64 operator timed once. With n = 48 (the
+    sweep-n48 workload): 64 cells, weights on the fly (the stored table would
+    be 10 GB), oracle on 2 cells, no FP64 comparator (its table: 41 GB)."""
+    lam, nc = 1.0, args.cells if n == 32 else min(args.cells, 64)
     ctx.init_weights([(n, L, lam)])
+    if n > 32:
+        ctx.set_option("conv_impl", 5)
+        if args.conv_warps is None:
+            ctx.set_option("conv_warps", 3)  # 2 CTAs per SM with the 27 KB stages of N = 48 (measured best of 2-4)
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
     Q = torch.empty_like(f)
-    tuned = tune(args, ctx, f, stream, reps=2)
+    explicit = args.conv_impl is not None or args.conv_warps is not None or n > 32
+    tuned = None if explicit else tune(args, ctx, f, stream, reps=2)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -596,13 +603,16 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     tot = float(sum(ms))
     value = nc * args.steps / (tot * 1e-3)
     # plain FP64 operator (table build and first call outside the timing)
-    Q64 = torch.empty_like(f)
-    with torch.cuda.stream(stream):
-        ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream)
-    ctx.sync_status(stream)
-    ms64 = _timed_steps(torch, lambda: ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream), 1, stream, flush)
-    fp64_value = nc / (ms64[0] * 1e-3)
-    pick = np.sort(np.random.default_rng(3).choice(nc, 16, replace=False))
+    fp64_value = None
+    if n <= 32:
+        Q64 = torch.empty_like(f)
+        with torch.cuda.stream(stream):
+            ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream)
+        ctx.sync_status(stream)
+        ms64 = _timed_steps(torch, lambda: ctx.collide(f, Q64, mode=bte.FP64_PLAIN, stream=stream), 1, stream,
+                            flush)
+        fp64_value = nc / (ms64[0] * 1e-3)
+    pick = np.sort(np.random.default_rng(3).choice(nc, 16 if n <= 32 else 2, replace=False))
     Qo = oracle.collide(n, L, lam, fn[pick])
     Qm = oracle.collide(n, L, lam, fn[pick], part=1, project=False)
     rel = np.linalg.norm(Qg[pick] - Qo, axis=1) / np.linalg.norm(Qm, axis=1)
@@ -613,14 +623,17 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     conv_ms = conv[0] / max(conv[1], 1)
     achieved = 10.0 * pairs * nc / (conv_ms * 1e-3) / 1e12
     wl = ("precision sweep: %d bi-Maxwellian cells (means ~ U(-1.5,1.5)^3, T ~ U(0.5,2), seed 3), "
-          "N=32, L=6, hard spheres; one projected collision evaluation of all cells per step" % nc)
-    return _line(args, "cell-collision evals/s at N=32 (FP32 operator)", value, UNIT, tot / args.steps, wl, {
+          "N=%d, L=6, hard spheres; one projected collision evaluation of all cells per step%s"
+          % (nc, n, "; weights built on the fly (conv_impl 5)" if n > 32 or args.conv_impl == 5 else ""))
+    return _line(args, "cell-collision evals/s at N=%d (FP32 operator)" % n, value, UNIT, tot / args.steps, wl, {
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_basis": _peak_basis(clk, fma), "measured_fma": fma,
                      "flops_per_launch": 10.0 * pairs * nc, "conv_ms_per_launch": conv_ms,
                      "weight_gbs": 4.0 * pairs / (conv_ms * 1e-3) / 1e9},
-        "fp64_plain": {"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value},
+        "fp64_plain": ({"value": fp64_value, "unit": UNIT, "speedup_fp32_over_fp64": value / fp64_value}
+                       if fp64_value else None),
+        "conv_impl": ctx.get_option("conv_impl") if tuned is None else tuned.get("conv_impl"),
         "autotuned": tuned,
         "accuracy": {"rel_l2_loss_norm_max": float(rel.max()), "rel_l2_loss_norm_median": float(np.median(rel)),
                      "rel_l2_plain_max": float(relp.max()), "cells_checked": pick.tolist(),
@@ -1027,7 +1040,8 @@ def run_secondary(args):
     stream = torch.cuda.Stream()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sampler = ClockSampler(local)
-    fn = {"homog-1cell": run_homog1, "sweep-n32": run_sweep32, "uneven-4096": run_uneven,
+    fn = {"homog-1cell": run_homog1, "sweep-n32": run_sweep32,
+          "sweep-n48": lambda *a: run_sweep32(*a, n=48), "uneven-4096": run_uneven,
           "learned-n16": run_learned, "wall-heating-200": run_wall200, "sudden-heating-refined": run_refined,
           "collision-models": run_models}[args.workload]
     line = fn(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler)

@@ -528,16 +528,24 @@ bte_status prepare(bte_ctx *c, Batch *B, int mode, bool step, bool transport) {
         if (fused_dft_supported(c->tables[sg.table]->N)) fused_dft_prepare(c->tables[sg.table]->N);
     if (mode == BTE_FP64_PLAIN) {
         for (const Segment &sg : B->segs) {
+            if (c->tables[sg.table]->N > 32)
+                return fail(c, BTE_EINVAL, "the plain FP64 operator is limited to N <= 32 (its table holds 8 V(N) "
+                                           "bytes: 41 GB at N = 48)");
             int r = build_table_fp64(*c->tables[sg.table], c->err);
             if (r != BTE_OK) return (bte_status)r;
         }
     } else if (mode == BTE_FP32) {
         ConvLaunch L;
         const ConvCfg g = cfg_of(c, B);
-        if (g.impl == 5)
-            for (const Segment &sg : B->segs)
-                if (!c->tables[sg.table]->d_I32)
-                    return fail(c, BTE_EINVAL, "conv_impl 5 (weights on the fly) needs elastic tables (beta = 1)");
+        for (const Segment &sg : B->segs) {
+            Table *t = c->tables[sg.table];
+            if (g.impl == 5 && !t->d_I32)
+                return fail(c, BTE_EINVAL, "conv_impl 5 (weights on the fly) needs elastic tables (beta = 1)");
+            if (g.impl != 5) {  // variants that stream the stored weights (built lazily at N = 48)
+                const int r = build_table_fp32(*t, c->err);
+                if (r != BTE_OK) return (bte_status)r;
+            }
+        }
         cudaError_t e = conv32_configure(B->kinds_mask, c->num_sms, g.warps, g.stages, g.impl, &L);
         if (e != cudaSuccess) return cuda_fail(c, e, "convolution kernel configuration");
     }
@@ -728,7 +736,7 @@ bte_status prime_configs(bte_ctx *c) {
     for (const Table *t : c->tables)
         if (fused_dft_supported(t->N)) fused_dft_prepare(t->N);
     const Table *t = c->tables[0];
-    const unsigned mask = 1u << t->kind0 | (t->ntiles > 1 ? 1u << (t->kind0 + 1) : 0u);
+    const unsigned mask = t->kinds_mask();
     ConvLaunch L;
     cudaError_t e = conv32_configure(mask, c->num_sms, c->conv_warps, c->conv_stages, c->conv_impl, &L);
     return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "convolution kernel configuration");
@@ -1062,6 +1070,7 @@ bte_status bte_step_ex(bte_ctx *c, double *f, const bte_instance *inst, int64_t 
             return fail(c, BTE_EINVAL, "bte_step: wall temperatures must be > 0");
         const Table *t0 = c->tables.empty() ? nullptr : c->tables[0];
         if (!t0) return fail(c, BTE_ESTATE, "no weight tables: call bte_init_weights first");
+        if (t0->N > kTransportMaxN) return fail(c, BTE_EINVAL, "bte_step: transport needs N <= 32");
         ta.N = t0->N;
         ta.nx = tr->nx;
         ta.dv = t0->dv;

@@ -24,15 +24,17 @@ constexpr int kLanes = 32;  // cells per group: one warp lane per cell
 struct ConvKind {
     int N, T, K0;
 };
-constexpr int kNumKinds = 7;
+constexpr int kNumKinds = 10;
 // kind ids: 0:(8,8,0) 1:(12,12,0) 2:(16,16,0) 3:(24,12,0) 4:(24,12,12) 5:(32,16,0) 6:(32,16,16)
+//           7:(48,16,0) 8:(48,16,16) 9:(48,16,32)
 inline ConvKind conv_kind(int id) {
-    static const ConvKind k[kNumKinds] = {{8, 8, 0},    {12, 12, 0},  {16, 16, 0}, {24, 12, 0},
-                                          {24, 12, 12}, {32, 16, 0},  {32, 16, 16}};
+    static const ConvKind k[kNumKinds] = {{8, 8, 0},    {12, 12, 0},  {16, 16, 0}, {24, 12, 0},  {24, 12, 12},
+                                          {32, 16, 0},  {32, 16, 16}, {48, 16, 0}, {48, 16, 16}, {48, 16, 32}};
     return k[id];
 }
 int first_kind_for_N(int N);  // -1 if unsupported
 int tiles_for_N(int N);
+constexpr int kMaxTiles = 3;
 
 // One warp-sized unit of convolution work: cell group g (32 lanes), pencil
 // (k1, k2), k3 tile. Sorted by cost (descending) before upload.
@@ -59,7 +61,7 @@ struct Table {
     std::vector<uint64_t> wofs;          // per (tile, k1, k2)
     std::vector<uint32_t> desc_off;      // per (k1, k2)
     std::vector<uint32_t> nblocks;       // per (k1, k2)
-    int cpad[2] = {0, 0};
+    int cpad[kMaxTiles] = {0, 0, 0};
     size_t n_w32 = 0, n_desc = 0;
     float *d_w32 = nullptr;
     uint32_t *d_desc = nullptr;          // m1 | (m2 << 16)
@@ -86,6 +88,13 @@ struct Table {
     // Host FP64 radial tables on integer invariants (kept for the lazy FP64 table)
     std::vector<double> I, J;            // I[p * nq + q], J[s]
     int np = 0, nq = 0, ns = 0;
+    // the convolution kinds of this table's k3 tiles (bit kind0 + tile)
+    unsigned kinds_mask() const {
+        unsigned m = 0;
+        for (int i = 0; i < ntiles; ++i) m |= 1u << (kind0 + i);
+        return m;
+    }
+    std::vector<uint32_t> desc_host;     // block descriptors (host copy, for the lazy FP32 table)
     double ghat(int k1, int k2, int k3, int m1, int m2, int m3) const;  // FP64, no dz^3
     double gain_inelastic(double a, double b) const;                    // I(a, b) off the lattice
 };
@@ -187,6 +196,7 @@ namespace bte {
 
 // tables.cpp
 int build_table(Table &t, std::string &err);
+int build_table_fp32(Table &t, std::string &err);  // the stored FP32 weights (built by build_table for N <= 32)
 int build_table_fp64(Table &t, std::string &err);
 void free_table(Table &t);
 

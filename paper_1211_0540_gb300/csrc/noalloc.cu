@@ -142,7 +142,7 @@ extern "C" bte_status bte_collide_noalloc(bte_ctx *c, const double *f, double *Q
     g.stages = c->conv_stages;
     g.merge = c->conv_merge;
     g.split = c->dft_split;
-    const unsigned mask = 1u << t->kind0 | (t->ntiles > 1 ? 1u << (t->kind0 + 1) : 0u);
+    const unsigned mask = t->kinds_mask();
     {
         char key[48];
         std::snprintf(key, sizeof key, "k%u:s%lld", mask, (long long)nslots);

@@ -7,7 +7,7 @@
 namespace bte {
 
 constexpr int kProjThreads = 256;
-constexpr int kProjMaxN = 32;
+constexpr int kProjMaxN = 48;
 
 struct ProjShared {
     double red[32][5];  // one row per warp (up to 1024 threads)

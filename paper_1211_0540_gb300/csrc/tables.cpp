@@ -93,11 +93,12 @@ int first_kind_for_N(int N) {
         case 16: return 2;
         case 24: return 3;
         case 32: return 5;
+        case 48: return 7;
         default: return -1;
     }
 }
 
-int tiles_for_N(int N) { return (N == 24 || N == 32) ? 2 : 1; }
+int tiles_for_N(int N) { return N == 48 ? 3 : ((N == 24 || N == 32) ? 2 : 1); }
 
 double Table::ghat(int k1, int k2, int k3, int m1, int m2, int m3) const {
     const int h = N / 2;
@@ -132,7 +133,7 @@ double Table::gain_inelastic(double a, double b) const {
 int build_table(Table &t, std::string &err) {
     const int N = t.N;
     if (first_kind_for_N(N) < 0) {
-        err = "unsupported N (supported: 8, 12, 16, 24, 32)";
+        err = "unsupported N (supported: 8, 12, 16, 24, 32, 48)";
         return BTE_EINVAL;
     }
     if (!(t.L > 0.0) || !std::isfinite(t.L)) {
@@ -217,27 +218,7 @@ int build_table(Table &t, std::string &err) {
         }
     }
     t.n_w32 = total;
-    std::vector<float> w32(total, 0.0f);
-#pragma omp parallel for collapse(2) schedule(dynamic, 1)
-    for (int tile = 0; tile < t.ntiles; ++tile)
-        for (int kk = 0; kk < N * N; ++kk) {
-            const int k1 = kk / N, k2 = kk % N, K0 = tile * T;
-            size_t o = t.wofs[(size_t)tile * N * N + kk];
-            for (uint32_t b = 0; b < t.nblocks[kk]; ++b) {
-                uint32_t d = desc[t.desc_off[kk] + b];
-                int m1 = d & 0xffff, m2 = d >> 16, n1 = k1 - m1 + h, n2 = k2 - m2 + h;
-                bool pair = !(m1 == n1 && m2 == n2);
-                size_t wi = o + (size_t)b * t.cpad[tile];
-                for (int m3 = 0; m3 < N; ++m3)
-                    for (int j = 0; j < T; ++j) {
-                        int k3 = K0 + j, n3 = k3 - m3 + h;
-                        if (n3 < 0 || n3 >= N) continue;
-                        double g = t.ghat(k1, k2, k3, m1, m2, m3);
-                        if (pair) g += t.ghat(k1, k2, k3, n1, n2, n3);
-                        w32[wi++] = (float)(g * dz3);
-                    }
-            }
-        }
+    t.desc_host = desc;
 
     // projection constants: A = sum_j c_j c_j^T, c_j = (1, v1, v2, v3, |v|^2);
     // inelastic collisions do not conserve energy (Sec. 3.3): the constraint set
@@ -323,7 +304,7 @@ int build_table(Table &t, std::string &err) {
         // per entry (m3, k3) of a tile, in the kernel's order: the third
         // components of the invariants, (k3'^2 | (2m3' - k3')^2 << 16,
         // m3'^2 | n3'^2 << 16) with n3' = k3' - m3', as four 16-bit fields
-        t.estride = std::max(t.cpad[0], t.cpad[1]);
+        t.estride = std::max(t.cpad[0], std::max(t.cpad[1], t.cpad[2]));
         etab.assign((size_t)t.ntiles * t.estride * 4, 0);
         for (int tile = 0; tile < t.ntiles; ++tile) {
             int e = 0;
@@ -343,8 +324,7 @@ int build_table(Table &t, std::string &err) {
 
     // upload
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&t.d_w32, sizeof(float) * std::max<size_t>(total, 4));
-    if (e == cudaSuccess) e = cudaMalloc(&t.d_tmpl, sizeof(ConvItem) * std::max<size_t>(tmpl.size(), 1));
+    e = cudaMalloc(&t.d_tmpl, sizeof(ConvItem) * std::max<size_t>(tmpl.size(), 1));
     if (e == cudaSuccess && !I32.empty()) e = cudaMalloc(&t.d_I32, sizeof(float) * I32.size());
     if (e == cudaSuccess && !J32.empty()) e = cudaMalloc(&t.d_J32, sizeof(float) * J32.size());
     if (e == cudaSuccess && !etab.empty()) e = cudaMalloc(&t.d_etab, sizeof(uint16_t) * etab.size());
@@ -356,7 +336,6 @@ int build_table(Table &t, std::string &err) {
         free_table(t);
         return BTE_ENOMEM;
     }
-    e = cudaMemcpy(t.d_w32, w32.data(), sizeof(float) * total, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !tmpl.empty())
         e = cudaMemcpy(t.d_tmpl, tmpl.data(), sizeof(ConvItem) * tmpl.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !I32.empty())
@@ -372,6 +351,57 @@ int build_table(Table &t, std::string &err) {
     if (e != cudaSuccess) {
         err = std::string("cudaMemcpy (weight table): ") + cudaGetErrorString(e);
         free_table(t);
+        return BTE_ECUDA;
+    }
+    // the stored FP32 weights: built now up to N = 32; at N = 48 (10 GB) only
+    // when a variant that streams them runs (weights on the fly need none)
+    if (N <= 32) {
+        const int r = build_table_fp32(t, err);
+        if (r != BTE_OK) {
+            free_table(t);
+            return r;
+        }
+    }
+    return BTE_OK;
+}
+
+// The FP32 pair-symmetrised weights (times dz^3) in the kernel's layout:
+// per (tile, k1, k2) its kept blocks, per block m3 ascending then k3.
+int build_table_fp32(Table &t, std::string &err) {
+    if (t.d_w32) return BTE_OK;
+    const int N = t.N, h = N / 2, T = conv_kind(t.kind0).T;
+    const double dz3 = t.dz * t.dz * t.dz;
+    std::vector<float> w32(t.n_w32, 0.0f);
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int tile = 0; tile < t.ntiles; ++tile)
+        for (int kk = 0; kk < N * N; ++kk) {
+            const int k1 = kk / N, k2 = kk % N, K0 = tile * T;
+            size_t o = t.wofs[(size_t)tile * N * N + kk];
+            for (uint32_t b = 0; b < t.nblocks[kk]; ++b) {
+                uint32_t d = t.desc_host[t.desc_off[kk] + b];
+                int m1 = d & 0xffff, m2 = d >> 16, n1 = k1 - m1 + h, n2 = k2 - m2 + h;
+                bool pair = !(m1 == n1 && m2 == n2);
+                size_t wi = o + (size_t)b * t.cpad[tile];
+                for (int m3 = 0; m3 < N; ++m3)
+                    for (int j = 0; j < T; ++j) {
+                        int k3 = K0 + j, n3 = k3 - m3 + h;
+                        if (n3 < 0 || n3 >= N) continue;
+                        double g = t.ghat(k1, k2, k3, m1, m2, m3);
+                        if (pair) g += t.ghat(k1, k2, k3, n1, n2, n3);
+                        w32[wi++] = (float)(g * dz3);
+                    }
+            }
+        }
+    cudaError_t e = cudaMalloc(&t.d_w32, sizeof(float) * std::max<size_t>(t.n_w32, 4));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        t.d_w32 = nullptr;
+        err = std::string("cudaMalloc (FP32 weight table): ") + cudaGetErrorString(e);
+        return BTE_ENOMEM;
+    }
+    e = cudaMemcpy(t.d_w32, w32.data(), sizeof(float) * t.n_w32, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpy (FP32 weight table): ") + cudaGetErrorString(e);
         return BTE_ECUDA;
     }
     return BTE_OK;
