@@ -99,11 +99,12 @@ def parse():
 
 
 def source_hash():
-    """Hash of the convolution kernel's source (conv32.cu holds the kernel, its
-    item loop and its launch configuration)."""
+    """Hash of the convolution kernel's source (conv32_device.cuh holds the
+    kernels and their item loop, conv32.cu their launch configuration)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1211_0540_gb300", "csrc", "conv32.cu"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("conv32_device.cuh", "conv32.cu"):
+        with open(os.path.join(ROOT, "paper_1211_0540_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
