@@ -165,8 +165,10 @@ bte_status bte_collide(bte_ctx *ctx, const double *f, double *Q, const bte_insta
  *   ind = ||F[Q](zeta_s) - Qhat(zeta_s)|| / ||Qhat_loss(zeta_s)||
  * (Qhat_loss: the same sum with the loss term of Ghat only). Cells with ind
  * above the option "learned_tol_ppm" * 1e-6 (default 1e-2) are recomputed with
- * the FP32 operator. Synchronises `stream` once. BTE_FLAG_NO_FALLBACK skips
- * the indicator. Counts: bte_learned_stats. */
+ * the FP32 operator (conv_impl 5 if chosen, else 4, unsplit work list). The
+ * list of those cells and the recompute's work list are built on the device,
+ * so the call does not synchronise (it is asynchronous like the FP32 mode).
+ * BTE_FLAG_NO_FALLBACK skips the indicator. Counts: bte_learned_stats. */
 bte_status bte_collide_ex(bte_ctx *ctx, const double *f, double *Q, const bte_instance *inst,
                           int64_t ninst, int mode, unsigned flags, void *stream);
 
@@ -189,6 +191,11 @@ bte_status bte_project(bte_ctx *ctx, double *Q, const bte_instance *inst, int64_
  *   over all tr->nx cells (inst must be NULL and ninst == tr->nx).
  * The homogeneous and Strang steps are replayed from a CUDA graph captured on
  * the first call with a given shape. Asynchronous. Errors as bte_collide.
+ * mode BTE_LEARNED (uniform cells of table 0): both stages take Q from the
+ *   learned mode of bte_collide_ex (surrogate, projection, indicator, FP32
+ *   recompute of the flagged cells, all on the device), so a replayed graph
+ *   recomputes whichever cells each stage flags. The graph is captured anew
+ *   when the surrogate's buffers or scales change.
  * bte_step_ex: the same with a bte_transport_ex slab. On cells of unequal
  * width the upwind reconstruction of Eq. upwind uses the upwind cell's width
  * dx_j, and the minmod slope divided differences over the distances between
@@ -357,8 +364,8 @@ bte_status bte_tc_gemm(bte_ctx *ctx, const void *A, const void *B, float *D, int
  *   copies the gradient (nparams floats) to host_grads and the loss to *loss.
  * bte_mlp_infer: Q_nn for n cells (device FP64; no projection).
  * bte_mlp_get/set_params: host FP32 vector of nparams values.
- * The surrogate is used by bte_collide with mode BTE_LEARNED (projection and
- * fallback there). Errors: BTE_EINVAL, BTE_ESTATE (no surrogate), BTE_ENOMEM, BTE_ECUDA. */
+ * The surrogate is used by bte_collide and bte_step with mode BTE_LEARNED
+ * (projection and fallback there). Errors: BTE_EINVAL, BTE_ESTATE (no surrogate), BTE_ENOMEM, BTE_ECUDA. */
 bte_status bte_mlp_init(bte_ctx *ctx, int table, int width, uint64_t seed);
 bte_status bte_mlp_info(const bte_ctx *ctx, int64_t *nparams, int *width, int *ndim, double *s_in, double *s_out);
 bte_status bte_mlp_set_scales(bte_ctx *ctx, double s_in, double s_out);
@@ -377,7 +384,10 @@ bte_status bte_mlp_grads(bte_ctx *ctx, const double *f, const double *Q, int64_t
 bte_status bte_mlp_infer(bte_ctx *ctx, const double *f, double *Q, int64_t n, void *stream);
 
 /* Cells evaluated and recomputed by the learned mode since the last reset, and
- * the largest indicator seen. */
+ * the largest indicator seen (counted on the device by every learned collide
+ * and every stage of a learned step; BTE_FLAG_NO_FALLBACK calls are not
+ * counted). Waits for the work this context has enqueued; reset != 0 clears
+ * the counts. Outputs (HOST) are optional. */
 bte_status bte_learned_stats(bte_ctx *ctx, int64_t *cells, int64_t *fallbacks, double *max_indicator, int reset);
 
 /* The fallback indicator of the learned mode (no counterpart in the paper).

@@ -63,7 +63,7 @@ using namespace bte;
 
 namespace {
 
-enum ScratchId { SC_T1 = 0, SC_T2, SC_F, SC_QH, SC_FS, SC_Q1, SC_Q2, SC_MISC };
+enum ScratchId { SC_T1 = 0, SC_T2, SC_F, SC_QH, SC_FS, SC_Q1, SC_Q2, SC_MISC, SC_FB };
 
 // NVTX range over a host-side stage (enqueue of its launches; inside stream
 // capture it marks the capture, not the replays). A no-op without a profiler.
@@ -681,10 +681,25 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
 
 // Heun step of the homogeneous problem on f (in place); the stage updates are
 // fused into the projection that ends each collide.
-bte_status enqueue_rk2(bte_ctx *c, Batch *B, double *f, double dt, double eps, int mode, cudaStream_t st) {
+bte_status enqueue_learned(bte_ctx *c, Batch *B, const double *f, double *Q, unsigned flags, const ConvCfg &cfg,
+                           cudaStream_t st);
+
+bte_status enqueue_rk2(bte_ctx *c, Batch *B, double *f, double dt, double eps, int mode, cudaStream_t st,
+                       const ConvCfg *lcfg = nullptr) {
     double *fs = (double *)c->scratch[SC_FS];
     double *q1 = (double *)c->scratch[SC_Q1];
     double *q2 = (double *)c->scratch[SC_Q2];
+    if (mode == BTE_LEARNED) {  // Q from the learned path, then the stage updates
+        const int64_t n = (int64_t)B->segs[0].nvalid * cell_M(c->tables[0]);
+        bte_status s = enqueue_learned(c, B, f, q1, 0u, *lcfg, st);
+        if (s != BTE_OK) return s;
+        launch_stage_update(q1, f, fs, nullptr, dt / eps, n, 1, st);
+        if ((s = enqueue_learned(c, B, fs, q2, 0u, *lcfg, st)) != BTE_OK) return s;
+        launch_stage_update(q2, nullptr, f, q1, 0.5 * dt / eps, n, 2, st);
+        count_launches(c, 2);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned step: launch");
+    }
     bte_status s = enqueue_collide(c, B, f, q1, mode, POST_STAGE1, f, fs, nullptr, dt / eps, st);
     if (s != BTE_OK) return s;
     return enqueue_collide(c, B, fs, q2, mode, POST_STAGE2, nullptr, f, q1, 0.5 * dt / eps, st);
@@ -831,24 +846,87 @@ bte_status enqueue_indicator(bte_ctx *c, Batch *B, const double *f, const double
     return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "indicator launch");
 }
 
-// Learned path on a uniform batch of table `mlp->table`: surrogate, projection,
-// sampled-mode indicator, FP32 recompute of the flagged cells. Synchronises
-// the stream once (the flagged set decides the fallback launch).
-bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int64_t ncells, unsigned flags,
+constexpr int64_t kLearnedChunk = 8192;  // cells per surrogate pass
+
+// Device work arrays of the learned mode's fallback for a uniform batch of
+// nslots slots (in SC_FB): queue counter, work-list length, slot offsets, work list.
+struct FallbackArrays {
+    unsigned *counter;
+    int *nitems;
+    int64_t *off;
+    ConvItem *items;
+};
+size_t fallback_bytes(int nslots, int ntmpl) {
+    const size_t off = 256 + (((size_t)nslots * sizeof(int64_t) + 255) & ~(size_t)255);
+    return off + sizeof(ConvItem) * (size_t)(nslots / kLanes) * (size_t)std::max(ntmpl, 1);
+}
+FallbackArrays fallback_arrays(bte_ctx *c, int nslots) {
+    unsigned char *b = (unsigned char *)c->scratch[SC_FB];
+    FallbackArrays a;
+    a.counter = (unsigned *)b;
+    a.nitems = (int *)(b + 64);
+    a.off = (int64_t *)(b + 256);
+    a.items = (ConvItem *)(b + 256 + (((size_t)nslots * sizeof(int64_t) + 255) & ~(size_t)255));
+    return a;
+}
+
+// Everything the learned mode allocates or configures for the uniform batch B
+// (never inside stream capture): surrogate activations, the indicator's
+// pencils and scratch, the fallback's arrays and statistics, the FP32
+// convolution (variant 4, or 5 when chosen; both read the work-list length
+// from the device). *cfg receives the fallback's configuration.
+bte_status prepare_learned(bte_ctx *c, Batch *B, ConvCfg *cfg) {
+    Mlp *m = c->mlp;
+    if (!B->uniform || B->segs.size() != 1 || B->uniform_table != 0 || m->table != 0)
+        return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
+    Table *t = c->tables[0];
+    if (t->N > 16 || !fused_dft_supported(t->N)) return fail(c, BTE_EINVAL, "learned mode: N = 8, 12 or 16");
+    bte_status s;
+    if (!m->ensure_batch((int)std::min<int64_t>(kLearnedChunk, B->segs[0].nvalid)))
+        return fail(c, BTE_ENOMEM, "learned mode: activations");
+    if ((s = ensure_indicator(c)) != BTE_OK) return s;
+    if ((s = ensure_scratch(c, SC_MISC, sizeof(float) * indicator_scratch_floats(*c->ind, t->N, B->nslots))) !=
+        BTE_OK)
+        return s;
+    if ((s = ensure_scratch(c, SC_FB, fallback_bytes(B->nslots, t->n_tmpl))) != BTE_OK) return s;
+    if (!c->d_lstats) {
+        cudaError_t e = cudaMalloc(&c->d_lstats, 4 * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(c->d_lstats, 0, 4 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: statistics");
+    }
+    ConvCfg g = cfg_of(c, B);
+    if (g.impl < 4 || (g.impl == 5 && !t->d_I32)) g.impl = 4;
+    g.csplit = 0;
+    if (g.impl == 4) {
+        const int r = build_table_fp32(*t, c->err);
+        if (r != BTE_OK) return (bte_status)r;
+    }
+    ConvLaunch L;
+    cudaError_t e = conv32_configure(t->kinds_mask(), c->num_sms, g.warps, g.stages, g.impl, &L);
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: convolution configuration");
+    *cfg = g;
+    return BTE_OK;
+}
+
+// Learned path on the uniform batch B (prepared by prepare_learned), all on
+// the stream with no host round trip, so that it also runs inside a captured
+// step: 1. surrogate in chunks of up to kLearnedChunk cells, 2. its output
+// projected (fused), 3. the indicator at the sampled modes, 4. on the device,
+// the list of cells whose indicator exceeds the tolerance and the FP32
+// operator's batch for them, 5. that operator (forward transform, convolution
+// over the listed groups only, inverse transform with the projection), which
+// overwrites Q of those cells.
+bte_status enqueue_learned(bte_ctx *c, Batch *B, const double *f, double *Q, unsigned flags, const ConvCfg &cfg,
                            cudaStream_t st) {
     NvtxRange range("bte_learned");
     Mlp *m = c->mlp;
-    if (!B->uniform || B->segs.size() != 1 || m->table != 0)
-        return fail(c, BTE_EINVAL, "learned mode: uniform cells of table 0 only (inst == NULL)");
     const Table *t = c->tables[0];
-    if (t->N > 16) return fail(c, BTE_EINVAL, "learned mode: N <= 16");
+    const int64_t ncells = B->segs[0].nvalid;
+    const int64_t M = cell_M(t);
     bte_status s;
-    // 1. surrogate in chunks of up to 8192 cells, 2. its output projected (fused)
-    const int64_t chunk = 8192;
-    for (int64_t c0 = 0; c0 < ncells; c0 += chunk) {
-        const int n = (int)std::min<int64_t>(chunk, ncells - c0);
-        if (!m->ensure_batch(n)) return fail(c, BTE_ENOMEM, "learned mode: activations");
-        const int64_t o = c0 * cell_M(t);
+    for (int64_t c0 = 0; c0 < ncells; c0 += kLearnedChunk) {
+        const int n = (int)std::min<int64_t>(kLearnedChunk, ncells - c0);
+        const int64_t o = c0 * M;
         if (m->run(f + o, nullptr, n, false, c->d_status, st, m->rowuni))
             return fail(c, BTE_ECUDA, "learned mode: surrogate");
         launch_post_project(m->Y, m->rho, n, t->N, m->s_out, proj_args(t), Q + o, st);
@@ -858,27 +936,44 @@ bte_status learned_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned mode: launch");
     }
-    // 3. indicator at the sampled modes
     float *ind = nullptr;
     if ((s = enqueue_indicator(c, B, f, Q, &ind, st)) != BTE_OK) return s;
-    std::vector<float> h(B->nslots);
-    cudaError_t e = cudaMemcpyAsync(h.data(), ind, sizeof(float) * B->nslots, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: indicator");
-    // 4. exact fallback for the flagged cells (the host slot order is the cell order)
+    const FallbackArrays fa = fallback_arrays(c, B->nslots);
     const double tol = 1e-6 * c->learned_tol_ppm;
-    std::vector<bte_instance> redo;
-    for (int64_t i = 0; i < ncells; ++i) {
-        c->learned_max_ind = std::max(c->learned_max_ind, (double)h[i]);
-        if (!(h[i] <= tol)) redo.push_back(bte_instance{0, 0, i * cell_M(t)});
-    }
-    c->learned_cells += ncells;
-    c->learned_fallbacks += (int64_t)redo.size();
-    if (redo.empty()) return BTE_OK;
-    Batch *R = nullptr;
-    if ((s = get_batch(c, redo.data(), (int64_t)redo.size(), &R)) != BTE_OK) return s;
-    if ((s = prepare(c, R, BTE_FP32, false, false)) != BTE_OK) return s;
-    return enqueue_collide(c, R, f, Q, BTE_FP32, POST_PROJECT, nullptr, nullptr, nullptr, 0.0, st);
+    launch_fallback_setup(ind, (int)ncells, tol, M, t->d_tmpl, t->n_tmpl, B->nslots, fa.off, fa.items, fa.nitems,
+                          fa.counter, c->d_lstats, st);
+    DftSeg ds{t->N, 0, B->nslots, 0};
+    const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+    const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
+    launch_dft_forward_fused(f, fa.off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st, cfg.split);
+    ConvLaunch L;
+    cudaError_t e = conv32_configure(t->kinds_mask(), c->num_sms, cfg.warps, cfg.stages, cfg.impl, &L);
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: convolution configuration");
+    ConvParams p{};
+    p.items = fa.items;
+    p.nitems = (B->nslots / kLanes) * t->n_tmpl;  // capacity (sizes the grid); the kernel reads the length
+    p.nitems_dev = fa.nitems;
+    p.counter = fa.counter;
+    p.F = (const float2 *)c->scratch[SC_F];
+    p.Qh = (float2 *)c->scratch[SC_QH];
+    p.W[0] = t->d_w32;
+    p.D[0] = t->d_desc;
+    p.I32[0] = t->d_I32;
+    p.J32[0] = t->d_J32;
+    p.E[0] = t->d_etab;
+    p.nq[0] = t->nq;
+    p.estride[0] = t->estride;
+    p.status = c->d_status;
+    p.merge = cfg.merge;
+    p.stall = c->debug_conv_stall;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned mode: launch");
+    if ((e = conv32_launch(L, p, st)) != cudaSuccess) return cuda_fail(c, e, "learned mode: convolution launch");
+    launch_dft_inverse_fused((const float2 *)c->scratch[SC_QH], fa.off, ds, t->d_root32, si, Q, proj_args(t),
+                             POST_PROJECT, nullptr, nullptr, nullptr, 0.0, st, cfg.split);
+    count_launches(c, 4);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned mode: launch");
 }
 
 }  // namespace
@@ -944,6 +1039,7 @@ void bte_destroy(bte_ctx *c) {
     cudaFree(c->d_status);
     cudaFree(c->d_counter);
     cudaFree(c->d_wall);
+    cudaFree(c->d_lstats);
     for (auto &kv : c->walls) cudaFree(kv.second.d);
     for (auto &kv : c->grids) cudaFree(kv.second);
     delete c;
@@ -992,8 +1088,10 @@ bte_status bte_collide_ex(bte_ctx *c, const double *f, double *Q, const bte_inst
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
     if ((s = prepare(c, B, mode == BTE_LEARNED ? BTE_FP32 : mode, false, false)) != BTE_OK) return s;
-    if (mode == BTE_LEARNED) s = learned_collide(c, B, f, Q, ninst, flags, (cudaStream_t)stream);
-    else
+    if (mode == BTE_LEARNED) {
+        ConvCfg lc;
+        if ((s = prepare_learned(c, B, &lc)) == BTE_OK) s = enqueue_learned(c, B, f, Q, flags, lc, (cudaStream_t)stream);
+    } else
         s = enqueue_collide(c, B, f, Q, mode, (flags & BTE_FLAG_RAW) ? POST_RAW : POST_PROJECT, nullptr, nullptr,
                             nullptr, 0.0, (cudaStream_t)stream);
     fence_record(c, (cudaStream_t)stream);
@@ -1088,6 +1186,8 @@ bte_status bte_step_ex(bte_ctx *c, double *f, const bte_instance *inst, int64_t 
     Batch *B = nullptr;
     if ((s = get_batch(c, inst, ninst, &B)) != BTE_OK) return s;
     if ((s = prepare(c, B, mode, true, tr != nullptr)) != BTE_OK) return s;
+    ConvCfg lcfg;
+    if (mode == BTE_LEARNED && (s = prepare_learned(c, B, &lcfg)) != BTE_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     auto body = [&]() -> bte_status {
         if (tr) {
@@ -1098,7 +1198,7 @@ bte_status bte_step_ex(bte_ctx *c, double *f, const bte_instance *inst, int64_t 
             prof_end(c, on, pe, st);
             count_launches(c, 2);
         }
-        bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st);
+        bte_status r = enqueue_rk2(c, B, f, dt, eps, mode, st, &lcfg);
         if (r != BTE_OK) return r;
         if (tr) {
             NvtxRange range_tr("bte_transport");
@@ -1116,15 +1216,17 @@ bte_status bte_step_ex(bte_ctx *c, double *f, const bte_instance *inst, int64_t 
         fence_record(c, st);
         return r;
     }
-    if (mode == BTE_LEARNED) return fail(c, BTE_EINVAL, "bte_step: use bte_collide for the learned mode");
-    // the slab (walls, temperatures, cell widths) is baked into the graph too
+    // the slab (walls, temperatures, cell widths) is baked into the graph too,
+    // and so are the surrogate's buffers and scales in the learned mode
     std::vector<double> trdesc;
     if (tr) {
         trdesc = {(double)tr->nx, tr->x0, tr->x1, (double)tr->bc_left, (double)tr->bc_right, tr->Tw_left,
                   tr->Tw_right, tr->dx ? 1.0 : 0.0};
         if (tr->dx) trdesc.insert(trdesc.end(), tr->dx, tr->dx + tr->nx);
     }
-    const int trkey = tr ? (int)(fnv1a(trdesc.data(), sizeof(double) * trdesc.size()) & 0x7fffffff) | 1 : 0;
+    if (mode == BTE_LEARNED)
+        trdesc.insert(trdesc.end(), {-1.0, (double)c->mlp->gen, (double)c->mlp->s_in, (double)c->mlp->s_out});
+    const int trkey = trdesc.empty() ? 0 : (int)(fnv1a(trdesc.data(), sizeof(double) * trdesc.size()) & 0x7fffffff) | 1;
     GraphKey key{ninst, inst ? (int)(fnv1a(inst, sizeof(bte_instance) * ninst) & 0x7fffffff) : -1, mode,
                  trkey, dt, eps, f, stream};
     auto it = c->graphs.find(key);
@@ -1291,12 +1393,22 @@ bte_status bte_get_option(const bte_ctx *c, const char *name, int *value) {
 
 bte_status bte_learned_stats(bte_ctx *c, int64_t *cells, int64_t *fallbacks, double *max_indicator, int reset) {
     if (!c) return BTE_EINVAL;
-    if (cells) *cells = c->learned_cells;
-    if (fallbacks) *fallbacks = c->learned_fallbacks;
-    if (max_indicator) *max_indicator = c->learned_max_ind;
-    if (reset) {
-        c->learned_cells = c->learned_fallbacks = 0;
-        c->learned_max_ind = 0.0;
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (c->d_lstats) {
+        cudaSetDevice(c->device);
+        cudaError_t e = quiesce(c);  // the context's learned calls and steps have finished
+        if (e == cudaSuccess) e = cudaMemcpy(h, c->d_lstats, sizeof h, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && reset) e = cudaMemsetAsync(c->d_lstats, 0, sizeof h, 0);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+        if (e != cudaSuccess) return cuda_fail(c, e, "bte_learned_stats");
+    }
+    if (cells) *cells = (int64_t)h[0];
+    if (fallbacks) *fallbacks = (int64_t)h[1];
+    if (max_indicator) {
+        const unsigned bits = (unsigned)h[2];
+        float v;
+        std::memcpy(&v, &bits, sizeof v);
+        *max_indicator = (double)v;
     }
     return BTE_OK;
 }

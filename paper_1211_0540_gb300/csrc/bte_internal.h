@@ -188,8 +188,9 @@ struct bte_ctx {
     bte::IndicatorTable *ind = nullptr;  // sampled modes of the fallback indicator
     int learned_tol_ppm = 10000;         // fallback when the indicator exceeds 1e-6 * this
     int learned_samples = 64;
-    int64_t learned_cells = 0, learned_fallbacks = 0;
-    double learned_max_ind = 0.0;
+    // learned-mode statistics, accumulated on the device by every call and
+    // step: cells seen, cells recomputed, the largest indicator (FP32 bits)
+    unsigned long long *d_lstats = nullptr;
 };
 
 namespace bte {

@@ -708,22 +708,22 @@ __device__ __forceinline__ void gen_first_any(const WarpRing &r, const ConvItem 
 template <class K, unsigned MASK, bool OTF>
 __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, const ConvParams &p, int lane,
                                             int warp, int nwarps, char *ring0, int *abort_flag, float *sums,
-                                            int sums_off, int sp, int *s_last, bool pre, int *s_next) {
+                                            int sums_off, int sp, int *s_last, bool pre, int *s_next, int nitems) {
     const bool ok = coop_item_sm<K, OTF>(r, it, p, lane, warp, nwarps, sums, pre);
     if (!ok && lane == 0) {
         atomicOr(p.status, ST_TIMEOUT);
         *abort_flag = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) *s_next = *abort_flag ? p.nitems : (int)atomicAdd(p.counter, 1u);
+    if (threadIdx.x == 0) *s_next = *abort_flag ? nitems : (int)atomicAdd(p.counter, 1u);
     __syncthreads();
     const int nx = *s_next;
-    if (nx < p.nitems && lane == 0) {
+    if (nx < nitems && lane == 0) {
         // the ring was last read by generic loads; order them before the copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         issue_first_any<MASK, OTF>(r, p.items[nx], p, warp);
     }
-    if (OTF && nx < p.nitems) {
+    if (OTF && nx < nitems) {
         gen_first_any<MASK>(r, p.items[nx], p, warp, lane);
         __syncwarp();
     }
@@ -739,7 +739,7 @@ __device__ __forceinline__ bool coop_run_sm(WarpRing &r, const ConvItem &it, con
 template <unsigned MASK, bool OTF = false>
 __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
     extern __shared__ __align__(128) char smem[];
-    __shared__ int s_item, s_abort, s_last;
+    __shared__ int s_item, s_abort, s_last, s_nitems;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int ring = p.warp_smem - kSumsBytes;
@@ -755,27 +755,30 @@ __global__ void __launch_bounds__(128, 3) conv32_sums_kernel(ConvParams p) {
     }
     if (threadIdx.x == 0) {
         s_abort = 0;
+        // a work list built on the device (the learned path's fallback) carries its length there
+        s_nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
         s_item = (int)atomicAdd(p.counter, 1u);
     }
     __syncthreads();
+    const int nitems = s_nitems;
     bool pre = false;  // the first block of item s_item is already in flight
     for (;;) {
         const int idx = s_item;
-        if (idx >= p.nitems || s_abort) break;
+        if (idx >= nitems || s_abort) break;
         const ConvItem it = p.items[idx];
         const int sp = p.split ? p.split[idx] : -1;
         bool ok = true, ran = true;
         switch (it.kind) {
-            case 0: if (MASK & 1u) ok = coop_run_sm<K8, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 1: if (MASK & 2u) ok = coop_run_sm<K12, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 2: if (MASK & 4u) ok = coop_run_sm<K16, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 3: if (MASK & 8u) ok = coop_run_sm<K24a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 4: if (MASK & 16u) ok = coop_run_sm<K24b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 5: if (MASK & 32u) ok = coop_run_sm<K32a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 6: if (MASK & 64u) ok = coop_run_sm<K32b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 7: if (MASK & 128u) ok = coop_run_sm<K48a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 8: if (MASK & 256u) ok = coop_run_sm<K48b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
-            case 9: if (MASK & 512u) ok = coop_run_sm<K48c, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item); else ran = false; break;
+            case 0: if (MASK & 1u) ok = coop_run_sm<K8, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 1: if (MASK & 2u) ok = coop_run_sm<K12, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 2: if (MASK & 4u) ok = coop_run_sm<K16, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 3: if (MASK & 8u) ok = coop_run_sm<K24a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 4: if (MASK & 16u) ok = coop_run_sm<K24b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 5: if (MASK & 32u) ok = coop_run_sm<K32a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 6: if (MASK & 64u) ok = coop_run_sm<K32b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 7: if (MASK & 128u) ok = coop_run_sm<K48a, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 8: if (MASK & 256u) ok = coop_run_sm<K48b, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
+            case 9: if (MASK & 512u) ok = coop_run_sm<K48c, MASK, OTF>(r, it, p, lane, warp, nwarps, smem, &s_abort, sums, ring, sp, &s_last, pre, &s_item, nitems); else ran = false; break;
             default: ran = false; break;
         }
         if (!ok) break;

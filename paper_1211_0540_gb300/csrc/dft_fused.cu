@@ -156,6 +156,7 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
     float2 *B = A + S::NP * P;                          // [jl][k2][k3]
     const int r = (int)cl.block_rank(), sl = blockIdx.x / C, t = threadIdx.x;
     const int64_t off = slot_off[s.s0 + sl];
+    if (off == -2) return;  // a slot of a group that holds no cell this call (nothing reads it)
     float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
     if (off < 0) {  // padding lane of a group (the whole cluster leaves here): zero fhat
         for (int e = r * (M / C) + t; e < (r + 1) * (M / C); e += S::NT) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);

@@ -34,6 +34,7 @@ constexpr int kMaxTables = 16;
 struct ConvParams {
     const ConvItem *items;
     int nitems;
+    const int *nitems_dev = nullptr;  // variants 4, 5: item count read from the device when set
     unsigned *counter;
     const float2 *F;
     float2 *Qh;

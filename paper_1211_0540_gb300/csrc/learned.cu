@@ -240,6 +240,74 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
     }
 }
 
+// The fallback of the learned mode, laid out on the device (one CTA): cells
+// whose indicator is not <= tol are listed in increasing order, and the FP32
+// operator's batch for them is written for up to nslots_cap slots: offsets
+// (redo[s] M for the listed cells, -1 for the padding lanes of the last
+// 32-cell group, -2 for the groups that hold no cell: the transforms skip
+// them), the convolution's work list (the one-group template repeated for the
+// groups in use, all groups of the costliest pencil first), its length and a
+// zeroed queue counter. The statistics (cells seen, cells recomputed, the
+// largest indicator as FP32 bits) accumulate in stats. No host round trip.
+constexpr int kSetupThreads = 1024;
+__global__ void __launch_bounds__(kSetupThreads)
+fallback_setup_kernel(const float *__restrict__ ind, int ncells, double tol, int64_t M,
+                      const ConvItem *__restrict__ tmpl, int ntmpl, int nslots_cap, int64_t *__restrict__ off,
+                      ConvItem *__restrict__ items, int *__restrict__ nitems, unsigned *__restrict__ counter,
+                      unsigned long long *__restrict__ stats) {
+    __shared__ int warp_tot[kSetupThreads / 32];
+    __shared__ int s_base;
+    __shared__ unsigned s_max;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) {
+        s_base = 0;
+        s_max = 0u;
+    }
+    __syncthreads();
+    for (int c0 = 0; c0 < ncells; c0 += kSetupThreads) {
+        const int c = c0 + t;
+        const float v = c < ncells ? ind[c] : 0.f;
+        const int flag = (c < ncells && !((double)v <= tol)) ? 1 : 0;
+        // the largest indicator (non-negative floats order as their bit patterns; NaN is left out)
+        const unsigned vmax = __reduce_max_sync(0xffffffffu, (c < ncells && v >= 0.f) ? __float_as_uint(v) : 0u);
+        if (lane == 0 && vmax) atomicMax(&s_max, vmax);
+        // block-wide exclusive prefix sum of the flags (in cell order)
+        const unsigned bal = __ballot_sync(0xffffffffu, flag);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_tot[warp] = __popc(bal);
+        __syncthreads();
+        int wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += warp_tot[w];
+        const int base = s_base;
+        if (flag) off[base + wbase + before] = (int64_t)c * M;
+        __syncthreads();
+        if (t == kSetupThreads - 1) s_base = base + wbase + before + flag;
+        __syncthreads();
+    }
+    const int nredo = s_base, ngu = (nredo + kLanes - 1) / kLanes;
+    for (int sl = nredo + t; sl < nslots_cap; sl += kSetupThreads) off[sl] = sl < ngu * kLanes ? -1 : -2;
+    for (int i = t; i < ngu * ntmpl; i += kSetupThreads) {
+        ConvItem it = tmpl[i / ngu];
+        it.fofs = (uint64_t)((int64_t)(i % ngu) * M * kLanes);
+        items[i] = it;
+    }
+    if (t == 0) {
+        *nitems = ngu * ntmpl;
+        *counter = 0u;
+        atomicAdd(stats + 0, (unsigned long long)ncells);
+        atomicAdd(stats + 1, (unsigned long long)nredo);
+        atomicMax(stats + 2, (unsigned long long)s_max);
+    }
+}
+
+// y = x + a Q (mode 1) or y += a (qp + Q) (mode 2) on n values: the time update
+// of a Heun stage when Q comes from the learned mode.
+__global__ void stage_update_kernel(const double *__restrict__ Q, const double *__restrict__ x, double *__restrict__ y,
+                                    const double *__restrict__ qp, double a, int64_t n, int mode) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = mode == 1 ? fma(a, Q[i], x[i]) : fma(a, qp[i] + Q[i], y[i]);
+}
+
 // ind (one float per slot of a uniform batch, slot = cell) to the caller's doubles.
 __global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,6 +318,19 @@ __global__ void widen_kernel(const float *__restrict__ in, double *__restrict__ 
 
 void launch_widen(const float *in, double *out, int n, cudaStream_t st) {
     if (n > 0) widen_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+}
+
+void launch_fallback_setup(const float *ind, int ncells, double tol, int64_t M, const ConvItem *tmpl, int ntmpl,
+                           int nslots_cap, int64_t *off, ConvItem *items, int *nitems, unsigned *counter,
+                           unsigned long long *stats, cudaStream_t st) {
+    fallback_setup_kernel<<<1, kSetupThreads, 0, st>>>(ind, ncells, tol, M, tmpl, ntmpl, nslots_cap, off, items,
+                                                        nitems, counter, stats);
+}
+
+void launch_stage_update(const double *Q, const double *x, double *y, const double *qp, double a, int64_t n,
+                         int mode, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    stage_update_kernel<<<(unsigned)blocks, 256, 0, st>>>(Q, x, y, qp, a, n, mode);
 }
 
 int build_indicator_table(const Table &t, int modes, uint64_t seed, IndicatorTable &out) {

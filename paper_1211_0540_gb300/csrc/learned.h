@@ -36,6 +36,15 @@ void launch_post_project(const float *Y, const double *rho, int B, int N, float 
 size_t indicator_scratch_floats(const IndicatorTable &it, int N, int nslots);
 // out[i] = (double) in[i], i < n
 void launch_widen(const float *in, double *out, int n, cudaStream_t st);
+// The learned mode's fallback batch on the device (learned.cu): flagged cells
+// (ind > tol), offsets (-1 padding lanes, -2 unused groups), work list, its
+// length, the zeroed queue counter; statistics (cells, fallbacks, max ind bits).
+void launch_fallback_setup(const float *ind, int ncells, double tol, int64_t M, const ConvItem *tmpl, int ntmpl,
+                           int nslots_cap, int64_t *off, ConvItem *items, int *nitems, unsigned *counter,
+                           unsigned long long *stats, cudaStream_t st);
+// Heun stage update with a given Q: mode 1 y = x + a Q, mode 2 y += a (qp + Q).
+void launch_stage_update(const double *Q, const double *x, double *y, const double *qp, double a, int64_t n,
+                         int mode, cudaStream_t st);
 void launch_indicator(const IndicatorTable &it, const Table &t, const float2 *F, const float2 *QN, int64_t eoff,
                       int nslots, int nvalid, float *err2, float *den2, float *ind, cudaStream_t st);
 

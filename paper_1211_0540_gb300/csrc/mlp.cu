@@ -12,6 +12,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -220,9 +221,15 @@ bool Mlp::alloc(void **p, size_t bytes) {
     return true;
 }
 
+uint64_t mlp_next_gen() {
+    static std::atomic<uint64_t> g{0};
+    return ++g;
+}
+
 bool Mlp::ensure_batch(int B) {
     const int Bp = (B + 127) / 128 * 128;
     if (Bp <= bcap) return true;
+    gen = mlp_next_gen();
     for (void *p : act_allocs) cudaFree(p);
     act_allocs.clear();
     bcap = 0;
@@ -397,8 +404,11 @@ bte_status bte_mlp_init(bte_ctx *c, int table, int width, uint64_t seed) {
     if (width < 64 || width % 128 != 0) return mlp_fail(c, BTE_EINVAL, "bte_mlp_init: width must be a multiple of 128");
     cudaSetDevice(c->device);
     if (gemm_bf16_prepare() != cudaSuccess) return mlp_fail(c, BTE_ECUDA, "bte_mlp_init: GEMM set-up");
+    if (c->mlp) cudaDeviceSynchronize();  // work in flight may still read the old surrogate
     delete c->mlp;
+    c->mlp = nullptr;
     Mlp *m = new Mlp();
+    m->gen = mlp_next_gen();
     m->table = table;
     m->N = t->N;
     m->M = t->N * t->N * t->N;

@@ -14,6 +14,9 @@ struct Mlp {
     double dv3 = 0.0;
     float s_in = 10.0f, s_out = 1.0f;
     int64_t step = 0;
+    // identity of the device buffers a captured step reads (renewed whenever
+    // they are allocated anew; unique across surrogates)
+    uint64_t gen = 0;
     // parameters (FP32 master + AdamW state), flat: W1 b1 W2 b2 W3 b3
     float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
     __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w2t = nullptr, *w3t = nullptr;
@@ -44,6 +47,8 @@ struct Mlp {
             const int64_t *rows = nullptr);
     void adam_step(float lr, float wd, cudaStream_t st);
 };
+
+uint64_t mlp_next_gen();
 
 void launch_mlp_post(const float *Y, const double *rho, const int64_t *off, int B, int M, float s_out, double *Q,
                      cudaStream_t st);

@@ -104,6 +104,7 @@ def test_learned_mode_projection_and_fallback():
     c.mlp_set_scales(10.0, 50.0)
     f = inputs.homogeneous_cells(N, L, 40, seed=8)
     ft = torch.from_numpy(f).cuda().reshape(-1)
+    c.set_option("conv_split", 0)  # the fallback runs the unsplit work list: the same sums, bit for bit
     exact = c.collide(ft, mode=bte.FP32)
     c.set_option("learned_tol_ppm", 0)
     q0 = c.collide(ft, mode=bte.LEARNED)
@@ -126,6 +127,97 @@ def test_learned_mode_projection_and_fallback():
     dv3 = (2 * L / N) ** 3
     C = dv3 * np.stack([np.ones(N ** 3), v1.ravel(), v2.ravel(), v3.ravel(), (v1 ** 2 + v2 ** 2 + v3 ** 2).ravel()])
     assert np.all(np.abs(m) <= 1e-12 * (np.abs(Q1) @ np.abs(C).T))
+    c.close()
+
+
+def _learned_ctx(N=8, ncells=40):
+    from paper_1211_0540_gb300 import bte
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.mlp_init(0, 128, seed=5)
+    c.mlp_set_scales(10.0, 50.0)
+    f = torch.from_numpy(inputs.homogeneous_cells(N, L, ncells, seed=8)).cuda().reshape(-1)
+    return bte, c, f
+
+
+def test_learned_step_is_heun_on_the_learned_operator():
+    """bte_step in the learned mode (captured into a graph on a side stream)
+    is Heun's method on Q = the learned collide: f + dt/2 (Q(f) + Q(f + dt Q(f))),
+    with every cell served by the surrogate (unbounded tolerance) and with every
+    cell recomputed (tolerance 0: then it is the FP32 operator's step)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bte, c, f = _learned_ctx()
+    c.set_option("conv_split", 0)
+    dt, eps = 0.05, 1.0
+    s = torch.cuda.Stream()
+    for tol, ref_mode in ((1 << 30, bte.LEARNED), (0, bte.FP32)):
+        c.set_option("learned_tol_ppm", tol)
+        q1 = c.collide(f, mode=bte.LEARNED)
+        fs = f + dt / eps * q1
+        q2 = c.collide(fs, mode=bte.LEARNED)
+        want = f + 0.5 * dt / eps * (q1 + q2)
+        c.learned_stats(reset=True)
+        g = f.clone()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            c.step(g, dt, eps, mode=bte.LEARNED, stream=s)
+        c.sync_status(s)
+        st = c.learned_stats(reset=True)
+        assert st["cells"] == 2 * 40 and st["fallbacks"] == (0 if tol else 2 * 40)
+        scale = f.abs().max().item()
+        if ref_mode == bte.LEARNED:  # the surrogate's output moves with f + dt Q only at FP64 rounding
+            assert (g - want).abs().max().item() <= 1e-15 * scale
+        else:  # every cell recomputed: the FP32 operator's step, bit for bit
+            assert (g - want).abs().max().item() <= 1e-9 * scale
+            h = f.clone()
+            with torch.cuda.stream(s):
+                c.step(h, dt, eps, mode=bte.FP32, stream=s)
+            c.sync_status(s)
+            assert torch.equal(g, h)
+    assert c.graph_count() >= 1  # the side-stream steps replayed captured graphs
+    c.close()
+
+
+def test_learned_step_fallback_varies_between_replays():
+    """One captured learned step replayed on states whose flagged sets differ:
+    the fallback list is built on the device at every replay. Each replay
+    equals, bit for bit, the same step enqueued directly (legacy stream, no
+    graph), recomputes exactly the cells its stage-1 indicator flags, and is
+    Heun's method on the learned collide to the FP32 operator's rounding."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bte, c, f = _learned_ctx(ncells=70)
+    c.set_option("conv_split", 0)
+    s = torch.cuda.Stream()
+    q = c.collide(f, mode=bte.LEARNED, fallback=False)
+    ind = c.learned_indicator(f, q).cpu().numpy()
+    tol_ppm = int(np.median(ind) * 1e6)  # about half the cells of the first state fall back
+    c.set_option("learned_tol_ppm", tol_ppm)
+    dt = 0.02
+    g = f.clone()
+    for rep in range(3):
+        before = g.clone()
+        qnn = c.collide(before, mode=bte.LEARNED, fallback=False)
+        ind1 = c.learned_indicator(before, qnn).cpu().numpy()
+        flagged1 = int(np.sum(~(ind1 <= 1e-6 * tol_ppm)))
+        direct = before.clone()
+        c.step(direct, dt, 1.0, mode=bte.LEARNED)  # legacy stream: enqueued directly
+        torch.cuda.synchronize()
+        c.learned_stats(reset=True)
+        with torch.cuda.stream(s):
+            c.step(g, dt, 1.0, mode=bte.LEARNED, stream=s)
+        c.sync_status(s)
+        st = c.learned_stats(reset=True)
+        assert torch.equal(g, direct)
+        assert st["cells"] == 2 * 70 and flagged1 <= st["fallbacks"] <= flagged1 + 70
+        if rep == 0:
+            assert 0 < flagged1 < 70
+        q1 = c.collide(before, mode=bte.LEARNED)
+        q2 = c.collide(before + dt * q1, mode=bte.LEARNED)
+        want = before + 0.5 * dt * (q1 + q2)
+        assert (g - want).abs().max().item() <= 1e-9 * before.abs().max().item()
+    assert c.graph_count() == 1
     c.close()
 
 
