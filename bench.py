@@ -805,6 +805,27 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
         ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream)
     ms_64 = _timed_steps(torch, lambda: ctx.collide(fw, Q64, mode=bte.FP64_PLAIN, stream=stream), 1,
                          stream, flush, tag="fp64")
+    # whole Strang steps of the slab (two transport half steps and a Heun step
+    # whose two stages use the learned collide, fallback included), against
+    # the same steps with the FP32 operator; each from a copy of the state
+    dt = 0.5 * (1.0 / nx) / L
+    steps = {}
+    for name, mode in (("learned", bte.LEARNED), ("fp32", bte.FP32)):
+        fs = fw.clone()
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                ctx.step(fs, dt, EPS, transport=tr, mode=mode, stream=stream)
+        ctx.sync_status(stream)
+        ctx.learned_stats(reset=True)
+        ms = _timed_steps(torch, lambda: ctx.step(fs, dt, EPS, transport=tr, mode=mode, stream=stream),
+                          args.steps, stream, flush, tag="step-" + name)
+        sst = ctx.learned_stats(reset=True)
+        steps[name] = {"value": 2 * nx * args.steps / (sum(ms) * 1e-3), "unit": UNIT,
+                       "ms_per_step": sum(ms) / args.steps}
+        if name == "learned":
+            steps[name]["fallback_rate"] = sst["fallbacks"] / max(sst["cells"], 1)
+    steps["note"] = ("one Strang step of the 1024-cell slab = 2048 collision evaluations, replayed from a "
+                     "captured graph (the learned one builds its fallback list on the device)")
     Qnn = ctx.collide(fw, mode=bte.LEARNED, fallback=False, stream=stream)
     ctx.sync_status(stream)
     a32, al, ann = (x.cpu().numpy().reshape(nx, M) for x in (Q32, Ql, Qnn))
@@ -834,6 +855,7 @@ def run_learned(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                                 "note": "surrogate + projection + indicator, threshold set so that no cell "
                                         "falls back"},
         "surrogate_gemms": gemms,
+        "strang_steps": steps,
         "autotuned": tuned,
         "fallback": {"cells": st["cells"], "fallbacks": st["fallbacks"],
                      "rate": st["fallbacks"] / max(st["cells"], 1), "max_indicator": st["max_indicator"]},
