@@ -999,9 +999,10 @@ def run_models(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
     """One projected FP32 collision evaluation of 128 bi-Maxwellian cells at N = 16
     for each collision model the weights encode (Sec. 2.2): hard spheres,
     variable hard potentials (lambda = 0.5, weights by quadrature), Maxwell
-    molecules, and inelastic collisions (beta = 0.8, 0.6; energy row dropped)."""
+    molecules, variable soft potentials (lambda = -1, -2.5; Sec. 2.1), and
+    inelastic collisions (beta = 0.8, 0.6; energy row dropped)."""
     n, nc = 16, 128
-    models = [(1.0, 1.0), (0.5, 1.0), (0.0, 1.0), (1.0, 0.8), (0.0, 0.6)]
+    models = [(1.0, 1.0), (0.5, 1.0), (0.0, 1.0), (-1.0, 1.0), (-2.5, 1.0), (1.0, 0.8), (0.0, 0.6)]
     ids = ctx.init_weights([(n, L, lam, beta) for lam, beta in models])
     f = inputs.homogeneous_cells(n, L, nc, seed=9)
     M = n ** 3
@@ -1033,7 +1034,7 @@ def run_models(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
                      "energy_moment_mean": float(mom[:, 4].mean())})
     clocks = sampler.stop()
     wl = ("collision models in the weights (Sec. 2.2): 128 bi-Maxwellian cells at N = 16, L = 6; (lambda, beta) "
-          "= (1, 1), (0.5, 1), (0, 1), (1, 0.8), (0, 0.6); one projected FP32 evaluation per step")
+          "= (1, 1), (0.5, 1), (0, 1), (-1, 1), (-2.5, 1), (1, 0.8), (0, 0.6); one projected FP32 evaluation per step")
     value = rows[0]["evals_per_s"]
     return _line(args, "cell-collision evals/s per collision model (FP32 operator, N=16)", value, UNIT,
                  nc / value * 1e3, wl, {"models": rows, "autotuned": tuned, "clocks": clocks})

@@ -72,7 +72,9 @@ typedef enum { BTE_BC_DIFFUSE = 0, BTE_BC_SPECULAR = 1, BTE_BC_NOFLUX = 2 } bte_
 #define BTE_FLAG_NO_FALLBACK 2u  /* BTE_LEARNED: projected surrogate output only  */
 
 /* Velocity grid and collision kernel of one weight table: B = |u|^lambda / (4 pi)
- * (isotropic, Sec. 2.2). lambda = 0: Maxwell molecules, 1: hard spheres. */
+ * (isotropic, Sec. 2.2). lambda = 0: Maxwell molecules, 1: hard spheres,
+ * 0 < lambda < 1 variable hard and -3 < lambda < 0 variable soft potentials
+ * (Sec. 2.1). */
 typedef struct {
     int N;
     double L;
@@ -134,14 +136,16 @@ const char *bte_last_error(const bte_ctx *ctx);
  * Eq. GHat_calc (isotropic b, radial integral cut off at r0 = L, Sec. 3.1) in
  * FP64 on the host for each grid, and store them on the device: the FP32
  * pair-symmetrised table of the fast path and the moment/projection constants
- * of Sec. 3.3. lambda = 0, 1: closed forms of the radial integrals; 0 < lambda
- * < 1: the same integrals by composite Clenshaw-Curtis quadrature (the first
- * panel substituted r = h u^2), as Sec. 2.2 prescribes for other lambda.
+ * of Sec. 3.3. lambda = 0, 1: closed forms of the radial integrals; other
+ * lambda in (-3, 1), as Sec. 2.2 prescribes, by quadrature: the power series of
+ * the integrand integrated term by term on [0, 1/omega] (exact for the factor
+ * r^(lambda+2), singular at 0 for lambda < -2) and composite Clenshaw-Curtis
+ * panels beyond (omega: the table's largest radial frequency).
  * The FP64 table of the plain operator is built on the first BTE_FP64_PLAIN
  * call that needs it. table_ids[i] (host array of ngrids ints) receives the id
  * of grid i. Synchronous. bte_init_weights: elastic grids (beta = 1).
  * bte_init_weights_ex: any beta in (0, 1]; beta < 1 needs lambda = 0 or 1.
- * Errors: BTE_EINVAL (N unsupported, L <= 0, lambda outside [0, 1], beta
+ * Errors: BTE_EINVAL (N unsupported, L <= 0, lambda outside (-3, 1], beta
  * outside (0, 1]), BTE_ENOMEM. */
 bte_status bte_init_weights(bte_ctx *ctx, const bte_grid *grids, int ngrids, int *table_ids);
 bte_status bte_init_weights_ex(bte_ctx *ctx, const bte_grid_ex *grids, int ngrids, int *table_ids);

@@ -122,20 +122,24 @@ double ora_sinc(double x) {
 }
 
 #define ORA_GL_PER_PANEL 16
-#define ORA_GRADE_LEVELS 12
-#define ORA_GRADE_RATIO 0.15
 
 /* Composite Gauss-Legendre rule on [0, L] whose panel count resolves the
  * highest angular frequency omega: at least 16 nodes per half period. The
  * first panel [0, h] is graded geometrically towards r = 0 (sub-panels
- * [h s^(j+1), h s^j], j < 12, s = 0.15, and [0, h s^12]): for non-integer
+ * [h s^(j+1), h s^j], j < levels, and [0, h s^levels]): for non-integer
  * lambda the factor r^(lambda+2) is not smooth at 0, and one 16-point panel
  * there leaves errors of ~1e-9 relative; graded, the rule reaches FP64
- * accuracy (checked against 30-digit quadrature in the tests). The caller
- * frees *r and *w. Returns the node count. */
-static int ora_radial_rule(double L, double omega, double **r, double **w) {
+ * accuracy (checked against 30-digit quadrature in the tests). For
+ * lambda >= 0: s = 0.15, 12 levels. For the soft potentials, -3 < lambda < 0
+ * (Sec. 2.1), the factor r^(lambda+2) may be singular: s = 0.3 (each graded
+ * panel then keeps the singularity a panel width away) and enough levels that
+ * the innermost panel's share, (h s^levels)^(lambda+3), falls below 1e-17 of
+ * the first panel's. The caller frees *r and *w. Returns the node count. */
+static int ora_radial_rule(double L, double omega, double lam, double **r, double **w) {
+    const double ratio = lam >= 0.0 ? 0.15 : 0.3;
+    const int levels = lam >= 0.0 ? 12 : (int)ceil(17.0 * log(10.0) / ((lam + 3.0) * -log(ratio))) + 4;
     int panels = (int)ceil(omega * L / ORA_PI) + 4;
-    int nseg = panels - 1 + ORA_GRADE_LEVELS + 1;
+    int nseg = panels - 1 + levels + 1;
     int n = nseg * ORA_GL_PER_PANEL;
     double gx[ORA_GL_PER_PANEL], gw[ORA_GL_PER_PANEL];
     ora_gauss_legendre(ORA_GL_PER_PANEL, gx, gw);
@@ -148,13 +152,13 @@ static int ora_radial_rule(double L, double omega, double **r, double **w) {
         if (seg < panels - 1) { /* the uniform panels [p h, (p + 1) h], p >= 1 */
             a = (seg + 1) * h;
             b = (seg + 2) * h;
-        } else if (seg < panels - 1 + ORA_GRADE_LEVELS) { /* graded sub-panels of [0, h] */
+        } else if (seg < panels - 1 + levels) { /* graded sub-panels of [0, h] */
             int j = seg - (panels - 1);
-            b = h * pow(ORA_GRADE_RATIO, j);
-            a = b * ORA_GRADE_RATIO;
+            b = h * pow(ratio, j);
+            a = b * ratio;
         } else {
             a = 0.0;
-            b = h * pow(ORA_GRADE_RATIO, ORA_GRADE_LEVELS);
+            b = h * pow(ratio, levels);
         }
         for (int q = 0; q < ORA_GL_PER_PANEL; ++q, ++k) {
             (*r)[k] = a + 0.5 * (b - a) * (gx[q] + 1.0);
@@ -168,7 +172,7 @@ static int ora_radial_rule(double L, double omega, double **r, double **w) {
  * radial integral cut off at r0 = L, Sec. 3.1). */
 double ora_radial_I(double lam, double L, double a, double b) {
     double *r, *w;
-    int n = ora_radial_rule(L, fabs(a) + fabs(b), &r, &w);
+    int n = ora_radial_rule(L, fabs(a) + fabs(b), lam, &r, &w);
     double s = 0.0;
     for (int i = 0; i < n; ++i)
         s += w[i] * pow(r[i], lam + 2.0) * ora_sinc(a * r[i]) * ora_sinc(b * r[i]);
@@ -180,7 +184,7 @@ double ora_radial_I(double lam, double L, double a, double b) {
 /* J_lambda(c) = int_0^L r^{lambda+2} sinc(c r) dr  (Eq. GHat_calc, loss term). */
 double ora_radial_J(double lam, double L, double c) {
     double *r, *w;
-    int n = ora_radial_rule(L, fabs(c), &r, &w);
+    int n = ora_radial_rule(L, fabs(c), lam, &r, &w);
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += w[i] * pow(r[i], lam + 2.0) * ora_sinc(c * r[i]);
     free(r);
@@ -235,7 +239,7 @@ int ora_weights_build(int N, double L, double lam, double *Itab, double *Jtab) {
      * both, Ghat(xi, 0) = I(0, 4s) - J(s) is exactly 0 as in the continuous form. */
     int nt = nq > 4 * (ns - 1) + 1 ? nq : 4 * (ns - 1) + 1;
     double *r, *w;
-    int nn = ora_radial_rule(L, hz * (sqrt((double)(np - 1)) + sqrt((double)(nt - 1))), &r, &w);
+    int nn = ora_radial_rule(L, hz * (sqrt((double)(np - 1)) + sqrt((double)(nt - 1))), lam, &r, &w);
     double *S = (double *)malloc(sizeof(double) * (size_t)nt * nn);
     double *wr = (double *)malloc(sizeof(double) * nn); /* w_i r_i^{lambda+2} */
     for (int i = 0; i < nn; ++i) wr[i] = w[i] * pow(r[i], lam + 2.0);

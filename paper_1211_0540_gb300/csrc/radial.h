@@ -2,9 +2,10 @@
 //
 //   I(a, b) = int_0^L r^(lam+2) sinc(ar) sinc(br) dr,  J(c) = int_0^L r^(lam+2) sinc(cr) dr
 // (Sec. 2.2, Eq. GHat_calc, cut off at r0 = L). For lambda = 0, 1 they have
-// closed forms (Radial); for other lambda a composite Clenshaw-Curtis rule
-// (RadialRule). Kept in a header of its own so that a host program can check
-// both against high-precision quadrature.
+// closed forms (Radial); for other lambda > -3 the series-and-panels rule
+// (SeriesRule); RadialRule is the plain panel rule the inelastic weights use
+// where a closed form would cancel. Kept in a header of its own so that a host
+// program can check them against high-precision quadrature.
 #pragma once
 
 #include <cmath>
@@ -37,12 +38,9 @@ struct Radial {
     }
 };
 
-// Radial quadrature for non-integer lambda (Sec. 2.2: the weights are then a
-// 1-D integral precomputed by quadrature). Composite Clenshaw-Curtis rule on
-// [0, L]: uniform panels of at most half a period of the highest frequency
-// omega of the table (25 points each); on the first panel [0, h] the
-// substitution r = h u^2 (dr = 2 h u du) turns the factor r^(lambda+2), which
-// is not smooth at 0, into u^(2 lambda + 5) (33 points). Clenshaw-Curtis
+// Plain panel rule: composite Clenshaw-Curtis on [0, L], uniform panels of at
+// most half a period of the highest frequency omega (25 points each); on the
+// first panel [0, h] the substitution r = h u^2 (dr = 2 h u du), 33 points. Clenshaw-Curtis
 // weights on [-1, 1] for n intervals (n even), nodes cos(j pi / n):
 //   w_j = (c_j / n) [1 - sum_{k=1}^{n/2} b_k cos(2 pi j k / n) / (4k^2 - 1)],
 //   c_0 = c_n = 1, c_j = 2 otherwise, b_{n/2} = 1, b_k = 2 otherwise.
@@ -87,8 +85,68 @@ inline RadialRule radial_rule(double L, double omega) {
 
 inline double sinc(double x) { return x == 0.0 ? 1.0 : std::sin(x) / x; }
 
-// I(a, b) by the quadrature rule (any lambda > -3), for checks and for the
-// pairs the closed form cannot take accurately.
+// Radial integrals for any lambda > -3 (Sec. 2.1: hard, Maxwell and variable
+// hard or soft potentials, -3 < lambda <= 1; Sec. 2.2: for lambda other than
+// 0 and 1 a one-dimensional integral done by quadrature). [0, L] splits at
+// h = min(L, 1 / omega), omega >= the largest a + b evaluated:
+// - on [0, h] the integrand's power series is integrated term by term, which
+//   is exact for the factor r^s, s = lambda + 2 > -1, however singular at 0:
+//     sinc(ar) sinc(br) = sum_{i,j} c_i(a) c_j(b) r^(2i+2j),  c_i(a) = (-1)^i a^(2i) / (2i+1)!,
+//     int_0^h r^(s+2k) dr = h^(s+1+2k) / (s+1+2k);
+//   with a h, b h <= 1 the terms fall below 1e-30 before i = kSeriesTerms;
+// - on [h, L], where r^s is smooth, composite Clenshaw-Curtis panels of at most
+//   half a period of omega (25 points each), the weights carrying r^s.
+constexpr int kSeriesTerms = 16;
+struct SeriesRule {
+    double L = 0, s = 0, h = 0, hs1 = 0;  // hs1 = h^(s+1)
+    double inv[2 * kSeriesTerms] = {};   // 1 / (s + 1 + 2k)
+    std::vector<double> r, w;            // [h, L]: nodes, weights times r^s
+};
+
+inline SeriesRule series_rule(double lam, double L, double omega) {
+    SeriesRule R;
+    R.L = L;
+    R.s = lam + 2.0;
+    R.h = omega > 1.0 / L ? 1.0 / omega : L;
+    R.hs1 = std::pow(R.h, R.s + 1.0);
+    for (int k = 0; k < 2 * kSeriesTerms; ++k) R.inv[k] = 1.0 / (R.s + 1.0 + 2.0 * k);
+    if (R.h < L) {
+        const int panels = (int)std::ceil(omega * (L - R.h) / kPi) + 4;
+        const double ph = (L - R.h) / panels;
+        std::vector<double> x, w;
+        cc_rule(24, x, w);
+        for (int p = 0; p < panels; ++p)
+            for (size_t j = 0; j < x.size(); ++j) {
+                const double rr = R.h + p * ph + 0.5 * ph * (x[j] + 1.0);
+                R.r.push_back(rr);
+                R.w.push_back(0.5 * ph * w[j] * std::pow(rr, R.s));
+            }
+    }
+    return R;
+}
+
+// c_i(a) h^(2i) = (-1)^i (a h)^(2i) / (2i+1)!, i < kSeriesTerms
+inline void series_coeffs(double a, double h, double (&c)[kSeriesTerms]) {
+    const double x2 = (a * h) * (a * h);
+    c[0] = 1.0;
+    for (int i = 1; i < kSeriesTerms; ++i) c[i] = -c[i - 1] * x2 / ((2.0 * i) * (2.0 * i + 1.0));
+}
+
+// I(a, b) = int_0^L r^s sinc(ar) sinc(br) dr with the rule (a + b <= omega of the rule)
+inline double I_series(const SeriesRule &R, double a, double b) {
+    double ca[kSeriesTerms], cb[kSeriesTerms];
+    series_coeffs(a, R.h, ca);
+    series_coeffs(b, R.h, cb);
+    double first = 0.0;
+    for (int i = kSeriesTerms - 1; i >= 0; --i)
+        for (int j = kSeriesTerms - 1; j >= 0; --j) first += ca[i] * cb[j] * R.inv[i + j];
+    double rest = 0.0;
+    for (size_t k = 0; k < R.r.size(); ++k) rest += R.w[k] * sinc(a * R.r[k]) * sinc(b * R.r[k]);
+    return R.hs1 * first + rest;
+}
+
+// I(a, b) by the plain panel rule (smooth integrand: lambda = 0, 1), for the
+// inelastic pairs whose closed form would cancel (b L < 0.25).
 inline double I_quad(double lam, double L, double a, double b) {
     const RadialRule Q = radial_rule(L, std::fabs(a) + std::fabs(b));
     double acc = 0.0;

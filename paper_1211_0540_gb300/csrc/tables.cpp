@@ -47,37 +47,53 @@ namespace {
 
 using radial::kPi;
 using radial::Radial;
-using radial::RadialRule;
-using radial::radial_rule;
 using radial::sinc;
 
 // I[p][q] = int_0^L r^(lam+2) sinc(a_p r) sinc(b_q r) dr and J[s] = I[0][4s]
 // (a_p = hz sqrt p, b_q = hz sqrt q) for every p < np, q < nq of the parity of
-// p, by one rule for the whole table: A_p[i] = w_i r_i^(lam+2) sinc(a_p r_i),
-// I[p][q] = sum_i A_p[i] sinc(b_q r_i). J is read off the same sums, so
-// Ghat(xi, 0) = I(0, |xi|) - J(|xi|) is exactly 0.
+// p, by one series-and-panels rule for the whole table (radial.h): on [0, h]
+// I = h^(s+1) sum_j W_p[j] c_j(b_q), W_p[j] = sum_i c_i(a_p) / (s+1+2(i+j));
+// on [h, L] sum_i A_p[i] sinc(b_q r_i), A_p[i] = w_i sinc(a_p r_i). J is read
+// off the same sums, so Ghat(xi, 0) = I(0, |xi|) - J(|xi|) is exactly 0.
 void quadrature_tables(Table &t, double hz) {
+    using radial::kSeriesTerms;
+    constexpr int K = kSeriesTerms;
     const int nrow = std::max(t.nq, 4 * (t.ns - 1) + 1);
-    const RadialRule R = radial_rule(t.L, hz * (std::sqrt((double)(t.np - 1)) + std::sqrt((double)(nrow - 1))));
+    const radial::SeriesRule R =
+        radial::series_rule(t.lam, t.L, hz * (std::sqrt((double)(t.np - 1)) + std::sqrt((double)(nrow - 1))));
     const size_t nn = R.r.size();
-    std::vector<double> S((size_t)nrow * nn), A((size_t)t.np * nn);
+    std::vector<double> S((size_t)nrow * nn), A((size_t)t.np * nn), C((size_t)nrow * K), W((size_t)t.np * K);
 #pragma omp parallel for schedule(static)
-    for (int q = 0; q < nrow; ++q)
-        for (size_t i = 0; i < nn; ++i) S[(size_t)q * nn + i] = sinc(hz * std::sqrt((double)q) * R.r[i]);
+    for (int q = 0; q < nrow; ++q) {
+        const double b = hz * std::sqrt((double)q);
+        for (size_t i = 0; i < nn; ++i) S[(size_t)q * nn + i] = sinc(b * R.r[i]);
+        double c[K];
+        radial::series_coeffs(b, R.h, c);
+        for (int j = 0; j < K; ++j) C[(size_t)q * K + j] = c[j];
+    }
 #pragma omp parallel for schedule(static)
-    for (int p = 0; p < t.np; ++p)
-        for (size_t i = 0; i < nn; ++i)
-            A[(size_t)p * nn + i] = R.w[i] * std::pow(R.r[i], t.lam + 2.0) * S[(size_t)p * nn + i];
-    auto dot = [&](int p, int q) {
+    for (int p = 0; p < t.np; ++p) {
+        for (size_t i = 0; i < nn; ++i) A[(size_t)p * nn + i] = R.w[i] * S[(size_t)p * nn + i];
+        const double *c = &C[(size_t)p * K];  // c_i(a_p): a_p = b_p on this lattice
+        for (int j = 0; j < K; ++j) {
+            double acc = 0.0;
+            for (int i = K - 1; i >= 0; --i) acc += c[i] * R.inv[i + j];
+            W[(size_t)p * K + j] = acc;
+        }
+    }
+    auto value = [&](int p, int q) {
         const double *a = &A[(size_t)p * nn], *b = &S[(size_t)q * nn];
-        double acc = 0.0;
-        for (size_t i = 0; i < nn; ++i) acc += a[i] * b[i];
-        return acc;
+        double rest = 0.0;
+        for (size_t i = 0; i < nn; ++i) rest += a[i] * b[i];
+        const double *wp = &W[(size_t)p * K], *cq = &C[(size_t)q * K];
+        double first = 0.0;
+        for (int j = K - 1; j >= 0; --j) first += wp[j] * cq[j];
+        return R.hs1 * first + rest;
     };
 #pragma omp parallel for schedule(dynamic, 4)
     for (int p = 0; p < t.np; ++p)
-        for (int q = (p & 1); q < t.nq; q += 2) t.I[(size_t)p * t.nq + q] = dot(p, q);
-    for (int s = 0; s < t.ns; ++s) t.J[s] = dot(0, 4 * s);
+        for (int q = (p & 1); q < t.nq; q += 2) t.I[(size_t)p * t.nq + q] = value(p, q);
+    for (int s = 0; s < t.ns; ++s) t.J[s] = value(0, 4 * s);
 }
 
 inline int box_lo(int k, int N) { return std::max(0, k - N / 2 + 1); }
@@ -140,8 +156,9 @@ int build_table(Table &t, std::string &err) {
         err = "L must be finite and > 0";
         return BTE_EINVAL;
     }
-    if (!(t.lam >= 0.0 && t.lam <= 1.0)) {
-        err = "lambda must lie in [0, 1] (Maxwell molecules, variable hard potentials, hard spheres)";
+    if (!(t.lam > -3.0 && t.lam <= 1.0)) {
+        err = "lambda must lie in (-3, 1] (variable soft potentials, Maxwell molecules, variable hard "
+              "potentials, hard spheres)";
         return BTE_EINVAL;
     }
     if (!(t.beta > 0.0 && t.beta <= 1.0)) {

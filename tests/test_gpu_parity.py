@@ -391,7 +391,9 @@ def test_invalid_arguments_rejected(bte):
     with pytest.raises(bte.BteError):
         d.init_weights([(10, L, 1.0)])  # unsupported N
     with pytest.raises(bte.BteError):
-        d.init_weights([(16, L, 1.5)])  # lambda outside [0, 1]
+        d.init_weights([(16, L, 1.5)])  # lambda outside (-3, 1]
+    with pytest.raises(bte.BteError):
+        d.init_weights([(8, L, -3.0)])  # lambda = -3 (Coulomb) is not integrable here
     with pytest.raises(bte.BteError):
         d.init_weights([(8, L, 0.5, 0.8)])  # inelastic weights need lambda = 0 or 1
     with pytest.raises(bte.BteError):
@@ -692,12 +694,14 @@ def test_contexts_on_two_host_threads(bte):
         assert e is not None and e <= TOL32, e
 
 
-@pytest.mark.parametrize("N,ncells,lam", [(8, 40, 0.5), (12, 33, 0.3), (16, 34, 0.75)])
+@pytest.mark.parametrize("N,ncells,lam", [(8, 40, 0.5), (12, 33, 0.3), (16, 34, 0.75), (8, 37, -1.0),
+                                          (12, 35, -2.5), (16, 33, -1.7)])
 def test_non_integer_lambda_matches_oracle(bte, N, ncells, lam):
-    """Variable hard potentials (0 < lambda < 1): the library's weights come from
-    its own Clenshaw-Curtis quadrature, the oracle's from graded Gauss-Legendre
-    (Sec. 2.2: other lambda by a 1-D quadrature). Both paths against the oracle,
-    on every cell at N = 8, 12 and on sampled cells at N = 16."""
+    """Variable hard (0 < lambda < 1) and soft (-3 < lambda < 0, Sec. 2.1)
+    potentials: the library's weights come from its own series-and-panels rule,
+    the oracle's from graded Gauss-Legendre (Sec. 2.2: other lambda by a 1-D
+    quadrature). Both paths against the oracle, on every cell at N = 8, 12 and
+    on sampled cells at N = 16."""
     f = inputs.homogeneous_cells(N, L, ncells, seed=700 + N)
     pick = list(range(ncells)) if N < 16 else [0, 17, ncells - 1]
     Qo = oracle.collide(N, L, lam, f[pick])

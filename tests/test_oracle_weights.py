@@ -99,7 +99,7 @@ def test_ghat_vanishes_at_zeta_zero():
             break
 
 
-@pytest.mark.parametrize("lam", [0.0, 1.0])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.5, -1.5, -2.5])
 def test_weight_table_matches_pair_quadrature(lam):
     N = 8
     G = oracle.ghat_dense(N, L, lam)
@@ -140,17 +140,24 @@ def test_weight_table_symmetries():
         assert abs(G[tuple(s * kp + h) + tuple(s * mp + h)] - base) <= 1e-15 * abs(base) + 1e-300
 
 
-@pytest.mark.parametrize("lam", [0.1, 0.3, 0.5, 0.75])
+@pytest.mark.parametrize("lam", [0.1, 0.3, 0.5, 0.75, -0.5, -1.0, -1.5, -2.0, -2.5, -2.9])
 def test_radial_integrals_for_non_integer_lambda_match_high_precision_quadrature(lam):
     """Sec. 2.2: for non-integer lambda the weights are a 1-D integral evaluated by
-    quadrature. Reference: mpmath's adaptive quadrature at 30 digits (64 panels);
-    the oracle's graded composite Gauss-Legendre rule must agree to FP64 level."""
+    quadrature, here also for the soft potentials -3 < lambda < 0 of Sec. 2.1, whose
+    factor r^(lambda+2) is singular at 0 for lambda < -2. Reference: mpmath at 30
+    digits after r = u^(1/(lambda+3)), which turns r^(lambda+2) dr into
+    du/(lambda+3) (64 panels); the oracle's graded composite Gauss-Legendre rule
+    must agree to FP64 level."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 30
+    s1 = mpmath.mpf(lam) + 3
     for a, b in ((0.0, 0.0), (0.26, 0.26), (1.3, 4.1), (7.2, 13.9), (0.0, 5.0), (3.3, 0.2)):
-        def f(r):
-            return r ** (lam + 2) * (mpmath.sinc(a * r) if a else 1) * (mpmath.sinc(b * r) if b else 1)
-        ref = float(mpmath.quad(f, [0] + [L * i / 64 for i in range(1, 65)]))
+        def g(u):
+            r = u ** (1 / s1) if u > 0 else mpmath.mpf(0)
+            return (mpmath.sinc(a * r) if a else 1) * (mpmath.sinc(b * r) if b else 1)
+        ref = float(mpmath.quad(g, [0] + [(mpmath.mpf(L) * i / 64) ** s1 for i in range(1, 65)]) / s1)
+        if a == 0.0 and b == 0.0:  # int_0^L r^(lambda+2) dr in closed form
+            assert abs(ref - L ** (lam + 3) / (lam + 3)) <= 1e-14 * abs(ref)
         got = oracle.radial_I(lam, L, a, b)
         assert abs(got - ref) <= 1e-13 * abs(ref) + 1e-16, (a, b, got, ref)
         if a == 0.0:
