@@ -32,8 +32,10 @@ BC_NOFLUX = 2
 PINS = {
     "gauss_legendre": "numpy.polynomial.legendre.leggauss; exact on polynomials of degree 2n-1",
     "radial_I/radial_J/ghat_pair": "closed forms of the radial integrals for lambda=0,1 derived "
-                                   "independently in the tests; Ghat(xi,0)=0; symmetries",
-    "weights": "table lookup == per-pair quadrature",
+                                   "independently in the tests; 30-digit mpmath quadrature after "
+                                   "r = u^(1/(lambda+3)) for variable hard and soft potentials "
+                                   "(lambda in 0.1..0.75 and -0.5..-2.9); Ghat(xi,0)=0; symmetries",
+    "weights": "table lookup == per-pair quadrature (lambda = 0, 1, 0.5, -1.5, -2.5)",
     "dft_forward(_direct)": "numpy FFT with centring phases; round trip; direct == separable",
     "dft_inverse": "round trip with dft_forward; numpy inverse FFT",
     "convolve": "Ghat == 1 reduces to scipy linear convolution; bilinearity; xi<->zeta-xi "
