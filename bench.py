@@ -439,9 +439,20 @@ def main():
         t0 = time.perf_counter()
         oracle_strang_step(fs, oracle)
         tcpu = time.perf_counter() - t0
+        cores = oracle.get_threads()
+        # the same oracle on one core: projected collides of 8 cells of the slab
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            oracle.collide(N, L, LAM, f0[:8])
+            t1c = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(cores)
         line["cpu_baseline"] = {"value": EVALS_PER_STEP / tcpu, "unit": UNIT,
-                                "cores": oracle.get_threads(), "kind": "oracle",
-                                "sample": "one whole Strang step of the 128-cell slab (256 evals)"}
+                                "cores": cores, "kind": "oracle",
+                                "sample": "one whole Strang step of the 128-cell slab (256 evals)",
+                                "one_core": {"value": 8 / t1c, "unit": UNIT,
+                                             "sample": "8 projected collides of slab cells, 1 thread"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
