@@ -282,6 +282,10 @@ bte_status bte_graph_count(const bte_ctx *ctx, int64_t *count);
  *                      finishes second adds both halves' sums in a fixed
  *                      order (deterministic); 0 runs every pencil whole;
  *       "learned_tol_ppm" fallback threshold of the learned mode in 1e-6 units;
+ *       "dft_fuse_stages" 1 (default): in an FP32 Heun step the first stage's
+ *                      inverse transform also forms the second stage's forward
+ *                      transform (the intermediate state is not stored), bit
+ *                      for bit the result of separate launches (0);
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
  *                      transforms of N <= 16: 1, 2 or 4 (default 4), one
  *                      thread per pencil; 0: one CTA per cell with four

@@ -557,15 +557,19 @@ enum Post { POST_RAW = 0, POST_PROJECT = 1, POST_STAGE1 = 2, POST_STAGE2 = 3 };
 
 // Enqueue the operator for the batch: f -> Q, then `post`:
 // RAW: Qt;  PROJECT: P Qt;  STAGE1: Q = P Qt and y = x + a Q;  STAGE2: Q = P Qt and
-// y += a (qp + Q). Scratch must be ready (prepare).
+// y += a (qp + Q). Scratch must be ready (prepare). fuse (FP32, Heun stages):
+// FUSE_NEXT_FWD with STAGE1: y is not written; the inverse transform forms the
+// next stage's fhat of x + a Q in SC_F instead; SKIP_FWD: fhat is already in SC_F.
+enum Fuse { FUSE_NONE = 0, FUSE_NEXT_FWD = 1, FUSE_SKIP_FWD = 2 };
 bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int mode, int post,
-                           const double *x, double *y, const double *qp, double a, cudaStream_t st) {
+                           const double *x, double *y, const double *qp, double a, cudaStream_t st,
+                           int fuse = FUSE_NONE) {
     NvtxRange range_collide("bte_collide");
     const bool fp64 = mode == BTE_FP64_PLAIN;
     const ConvCfg cfg = cfg_of(c, B);
     ProfEntry pe_all{}, pe_conv{}, pe_fwd{}, pe_inv{};
     const int on_all = prof_begin(c, PK_COLLIDE, st, &pe_all);
-    {
+    if (!(fuse & FUSE_SKIP_FWD)) {
         NvtxRange range_fwd("bte_forward");
         const int on_fwd = prof_begin(c, PK_FORWARD, st, &pe_fwd);
         for (const Segment &sg : B->segs) {
@@ -654,6 +658,14 @@ bte_status enqueue_collide(bte_ctx *c, Batch *B, const double *f, double *Q, int
         const Table *t = c->tables[sg.table];
         DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
         const double si = std::pow(2.0 * kPi, -1.5) * t->dz * t->dz * t->dz;
+        if (fuse & FUSE_NEXT_FWD) {  // post == POST_STAGE1 (checked by the caller)
+            const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+            launch_dft_inverse_forward_fused((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si,
+                                             Q, proj_args(t), x, a, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
+                                             cfg.split);
+            count_launches(c, 1);
+            continue;
+        }
         if (!fp64 && fused_dft_supported(t->N)) {
             launch_dft_inverse_fused((const float2 *)c->scratch[SC_QH], B->d_slot_off, ds, t->d_root32, si, Q,
                                      proj_args(t), post, x, y, qp, a, st, cfg.split);
@@ -700,9 +712,17 @@ bte_status enqueue_rk2(bte_ctx *c, Batch *B, double *f, double dt, double eps, i
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? BTE_OK : cuda_fail(c, e, "learned step: launch");
     }
-    bte_status s = enqueue_collide(c, B, f, q1, mode, POST_STAGE1, f, fs, nullptr, dt / eps, st);
+    // FP32: the first stage's inverse transform also forms the second stage's
+    // forward transform (f* = f + dt/eps Q1 is then never stored)
+    bool fz = mode == BTE_FP32 && c->dft_fuse_stages;
+    const int split = cfg_of(c, B).split;
+    for (const Segment &sg : B->segs)
+        fz = fz && inverse_forward_fused_supported(c->tables[sg.table]->N, split);
+    bte_status s = enqueue_collide(c, B, f, q1, mode, POST_STAGE1, f, fs, nullptr, dt / eps, st,
+                                   fz ? FUSE_NEXT_FWD : FUSE_NONE);
     if (s != BTE_OK) return s;
-    return enqueue_collide(c, B, fs, q2, mode, POST_STAGE2, nullptr, f, q1, 0.5 * dt / eps, st);
+    return enqueue_collide(c, B, fs, q2, mode, POST_STAGE2, nullptr, f, q1, 0.5 * dt / eps, st,
+                           fz ? FUSE_SKIP_FWD : FUSE_NONE);
 }
 
 // Wall Maxwellian M_w(v) = (2 pi T_w)^{-3/2} exp(-|v|^2 / (2 T_w)) on the grid of table t
@@ -1360,6 +1380,7 @@ static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "batch_cache")) { *lo = 2; *hi = 1 << 20; return &c->batch_cache_max; }
     if (!std::strcmp(name, "graph_cache")) { *lo = 1; *hi = 1 << 20; return &c->graph_cache_max; }
     if (!std::strcmp(name, "learned_tol_ppm")) { *lo = 0; *hi = 1 << 30; return &c->learned_tol_ppm; }
+    if (!std::strcmp(name, "dft_fuse_stages")) { *lo = 0; *hi = 1; return &c->dft_fuse_stages; }
     return nullptr;
 }
 

@@ -181,6 +181,7 @@ struct bte_ctx {
                                // 3 as 2 at 2 CTAs/SM, 4 as 2 with the compensated sums in shared memory
     int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16); 0: one CTA, 4 threads per pencil
     int conv_split = 1;        // variant 4: split the costliest pencil items in two
+    int dft_fuse_stages = 1;   // FP32 Heun step: stage 1's inverse transform also forms stage 2's forward
     int debug_conv_stall = 0;  // testing only: make the convolution's waits run out
     std::string gpu_name;      // device name (key of saved tuning caches)
     std::map<std::string, bte::ConvCfg> tuned;  // autotuned configuration per batch shape

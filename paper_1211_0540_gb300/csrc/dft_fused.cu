@@ -255,12 +255,18 @@ dft_fwd_pencils_kernel(const double *__restrict__ f, const int64_t *__restrict__
 // [r JR, (r+1) JR) of the other two; the second pass reads the first pass's
 // rows from the whole cluster, and the moment partials of the CTAs are added
 // in rank order by every CTA (the same lambda everywhere).
-template <int N, int C_>
+// FWD (mode 2 only): the first Heun stage's state f* = x + a Q is not written;
+// its own slab, narrowed to FP32, is the input of the next stage's forward
+// transform, which the cluster then runs as dft_fwd_fused_kernel would
+// (the same passes on the same values: fhat of f* into Gout, scaled by
+// fscale), in the inverse's shared memory.
+template <int N, int C_, bool FWD = false>
 __global__ void __cluster_dims__(C_, 1, 1) __launch_bounds__(FusedShape<N, C_>::NT)
 dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ slot_off, DftSeg s,
                      const float2 *__restrict__ root, float scale, double *__restrict__ q, ProjArgs pa,
                      int mode, const double *__restrict__ x, double *__restrict__ y,
-                     const double *__restrict__ qp, double a) {
+                     const double *__restrict__ qp, double a, float2 *__restrict__ Gout = nullptr,
+                     float fscale = 0.f, int *status = nullptr) {
     using S = FusedShape<N, C_>;
     constexpr int M = S::M, NN = S::NN, P = S::P, H = S::H, JR = S::JR, C = S::C, NP = S::NP;
     cg::cluster_group cl = cg::this_cluster();
@@ -422,6 +428,7 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
         for (int e = t; e < MS; e += S::NT) qo[e] = fpc::widen(R[(e / N) * P + e % N]);
         return;
     }
+    bool bad = false;  // FWD: a non-finite f*
     if constexpr (PF) {
 #pragma unroll
         for (int i = 0; i < IT; ++i) {
@@ -430,8 +437,15 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
                 const int p = e / N, j3 = e % N;
                 const double v = fpc::widen(R[p * P + j3]) - (base[p] + sg[j3]);
                 qo[e] = v;
-                if (mode == 2) yo[e] = fma(a, v, u[i]);
-                else if (mode == 3) yo[e] = fma(a, w[i] + v, u[i]);
+                if constexpr (FWD) {
+                    const double fs = fma(a, v, u[i]);
+                    bad |= !fpc::finite64(fs);
+                    R[p * P + j3] = fpc::narrow(fs);  // each value is read and rewritten by this thread only
+                } else if (mode == 2) {
+                    yo[e] = fma(a, v, u[i]);
+                } else if (mode == 3) {
+                    yo[e] = fma(a, w[i] + v, u[i]);
+                }
             }
         }
     } else {
@@ -440,9 +454,61 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
             const int p = e / N, j3 = e % N;
             const double v = fpc::widen(R[p * P + j3]) - (base[p] + sg[j3]);
             qo[e] = v;
-            if (mode == 2) yo[e] = fma(a, v, xo[e]);
-            else if (mode == 3) yo[e] = fma(a, qpo[e] + v, yo[e]);
+            if constexpr (FWD) {
+                const double fs = fma(a, v, xo[e]);
+                bad |= !fpc::finite64(fs);
+                R[p * P + j3] = fpc::narrow(fs);
+            } else if (mode == 2) {
+                yo[e] = fma(a, v, xo[e]);
+            } else if (mode == 3) {
+                yo[e] = fma(a, qpo[e] + v, yo[e]);
+            }
         }
+    }
+    (void)bad;
+    if constexpr (FWD) {
+        // the next stage's forward transform of f*: the passes of dft_fwd_fused_kernel
+        // with its regions in this kernel's (same sizes): pencil rows in B, own slab in A
+        if (bad) atomicOr(status, ST_NONFINITE);
+        __syncthreads();
+        float2 *Af = B;  // [jl][j2] rows of P, index k3
+        float2 *Bf = A;  // [jl][k2][k3], read by the cluster (A's remote reads ended several cluster barriers ago)
+        if (act) {  // along j3, pencil (j1, j2) = own pencil t, real input
+            float xr[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) xr[j] = R[t * P + j];
+            float2 yv[N];
+            pencil_rc<N>(xr, yv, rt);
+#pragma unroll
+            for (int k = 0; k < N; ++k) Af[t * P + k] = yv[k];
+        }
+        __syncthreads();
+        if (act) {  // along j2, pencil (j1, k3)
+            const int jl = t / N, k3 = t % N;
+            float2 xx[N], yy[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) xx[j] = Af[(jl * N + j) * P + k3];
+            pencil_cc<N, true>(xx, yy, rt);
+#pragma unroll
+            for (int k = 0; k < N; ++k) Bf[(jl * N + k) * N + k3] = yy[k];
+        }
+        cell_sync<C>(cl);
+        if (act) {  // along j1, pencil (k2, k3), rows from every CTA of the cluster, into the group layout
+            const int k2 = r * JR + t / N, k3 = t % N;
+            const float2 *src[C];
+#pragma unroll
+            for (int o = 0; o < C; ++o) src[o] = cell_smem<C>(cl, Bf, o);
+            float2 xx[N], yy[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) xx[j] = src[j / JR][((j % JR) * N + k2) * N + k3];
+            pencil_cc<N, true>(xx, yy, rt);
+            float2 *go = Gout + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
+            const int pk = k2 * N + k3;
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                go[(int64_t)(k * NN + pk) * kLanes] = make_float2(fscale * yy[k].x, fscale * yy[k].y);
+        }
+        if constexpr (C > 1) cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
     }
 }
 
@@ -751,10 +817,20 @@ void inv_launch(const float2 *G, const int64_t *slot_off, const DftSeg &s, const
                                                                         mode, x, y, qp, a);
 }
 template <int N, int C>
+void inv_fwd_launch(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale,
+                    double *q, const ProjArgs &pa, const double *x, double a, double fscale, float2 *Gout,
+                    int *status, cudaStream_t st) {
+    using S = FusedShape<N, C>;
+    dft_inv_fused_kernel<N, C, true><<<s.nslots * C, S::NT, S::smem_inv, st>>>(
+        G, slot_off, s, root, (float)scale, q, pa, 2, x, nullptr, nullptr, a, Gout, (float)fscale, status);
+}
+template <int N, int C>
 void prepare_one() {
     using S = FusedShape<N, C>;
     cudaFuncSetAttribute(dft_fwd_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_fwd);
     cudaFuncSetAttribute(dft_inv_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_inv);
+    cudaFuncSetAttribute(dft_inv_fused_kernel<N, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)S::smem_inv);
 }
 template <int N>
 void prepare_n() {
@@ -868,6 +944,42 @@ void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const Df
         case 16: BTE_SPLIT_DISPATCH(inv_any, 16, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
         case 24: inv_launch<24, 4>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
         case 32: inv_launch<32, 8>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
+        default: break;
+    }
+}
+bool inverse_forward_fused_supported(int N, int split) {
+    return N == 24 || N == 32 || ((N == 8 || N == 12 || N == 16) && norm_split(split) != 0);
+}
+
+void launch_dft_inverse_forward_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s,
+                                      const float2 *root, double scale, double *q, const ProjArgs &pa,
+                                      const double *x, double a, double fscale, float2 *Gout, int *status,
+                                      cudaStream_t st, int split) {
+    switch (s.N) {
+        case 8:
+        case 12:
+        case 16:
+            switch (norm_split(split)) {
+                case 1:
+                    if (s.N == 8) inv_fwd_launch<8, 1>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else if (s.N == 12) inv_fwd_launch<12, 1>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else inv_fwd_launch<16, 1>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    break;
+                case 2:
+                    if (s.N == 8) inv_fwd_launch<8, 2>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else if (s.N == 12) inv_fwd_launch<12, 2>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else inv_fwd_launch<16, 2>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    break;
+                case 4:
+                    if (s.N == 8) inv_fwd_launch<8, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else if (s.N == 12) inv_fwd_launch<12, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    else inv_fwd_launch<16, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
+                    break;
+                default: break;  // split 0 has no fused form: the caller checks
+            }
+            break;
+        case 24: inv_fwd_launch<24, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st); break;
+        case 32: inv_fwd_launch<32, 8>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st); break;
         default: break;
     }
 }

@@ -105,6 +105,16 @@ void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const Df
 void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
                               const double *qp, double a, cudaStream_t st, int split = 4);
+// The first Heun stage's inverse (mode 2: Q = P Qt into q) fused with the second
+// stage's forward transform: f* = x + a Q is not stored; fhat(f*) (times fscale)
+// goes to Gout in the group layout. Same results as the inverse (mode 2) followed
+// by launch_dft_forward_fused on f*. Supported for N = 24, 32 and, with
+// dft_split 1, 2 or 4, for N = 8, 12, 16.
+bool inverse_forward_fused_supported(int N, int split);
+void launch_dft_inverse_forward_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s,
+                                      const float2 *root, double scale, double *q, const ProjArgs &pa,
+                                      const double *x, double a, double fscale, float2 *Gout, int *status,
+                                      cudaStream_t st, int split = 4);
 
 // Transport (Sec. 3.4) on nx uniform cells of M values. mw_*: wall Maxwellians
 // per velocity (device, M doubles), den_*: sum over the incoming half of |v.n| M_w.

@@ -361,6 +361,64 @@ def test_strang_steps_at_the_benchmark_shape_match_oracle(bte):
         assert abs(got.sum() - f.sum()) * dv3 <= 1e-12 * f.sum() * dv3
 
 
+@pytest.mark.parametrize("N,ncells,split", [(8, 40, 1), (12, 35, 2), (16, 33, 4), (16, 64, 1), (24, 9, 4),
+                                            (32, 5, 4)])
+def test_fused_stage_transforms_equal_separate_launches(bte, N, ncells, split):
+    """FP32 Heun step: the first stage's inverse transform also forms the
+    second stage's forward transform (default) and gives bit for bit the state
+    of separate launches (option dft_fuse_stages 0), homogeneous and with the
+    slab's transport; an uneven batch of two grids too."""
+    f0 = inputs.homogeneous_cells(N, L, ncells, seed=900 + N)
+    c = ctx_for(bte, ((N, L, 1.0),))
+    split0 = c.get_option("dft_split")
+    c.set_option("dft_split", split)
+    s = torch.cuda.Stream()
+    tr = dict(nx=ncells, x0=0.0, x1=1.0, bc_left=bte.BC_DIFFUSE, bc_right=bte.BC_SPECULAR, Tw_left=2.0,
+              Tw_right=1.0)
+    try:
+        for transport in (None, tr):
+            out = []
+            for fused in (1, 0):
+                c.set_option("dft_fuse_stages", fused)
+                ft = torch.from_numpy(f0.copy()).cuda()
+                torch.cuda.synchronize()
+                with torch.cuda.stream(s):
+                    for _ in range(2):
+                        c.step(ft, 0.4 * (1.0 / ncells) / L, 0.1, transport=transport, mode=bte.FP32, stream=s)
+                c.sync_status(s)
+                out.append(ft.cpu().numpy())
+            assert np.array_equal(out[0], out[1]), (transport is not None, np.abs(out[0] - out[1]).max())
+    finally:
+        c.set_option("dft_fuse_stages", 1)
+        c.set_option("dft_split", split0)
+
+
+def test_fused_stage_transforms_on_an_uneven_batch(bte):
+    N1, N2 = 8, 12
+    c = ctx_for(bte, ((N1, L, 1.0), (N2, L, 0.0)))
+    f1 = inputs.homogeneous_cells(N1, L, 7, seed=41)
+    f2 = inputs.homogeneous_cells(N2, L, 5, seed=42)
+    buf = np.concatenate([f1.reshape(-1), f2.reshape(-1)])
+    inst = [(0, i * N1 ** 3) for i in range(7)] + [(1, 7 * N1 ** 3 + i * N2 ** 3) for i in range(5)]
+    s = torch.cuda.Stream()
+    out = []
+    try:
+        for fused in (1, 0):
+            c.set_option("dft_fuse_stages", fused)
+            ft = torch.from_numpy(buf.copy()).cuda()
+            torch.cuda.synchronize()
+            with torch.cuda.stream(s):
+                c.step(ft, 0.01, 1.0, inst=inst, mode=bte.FP32, stream=s)
+            c.sync_status(s)
+            out.append(ft.cpu().numpy())
+    finally:
+        c.set_option("dft_fuse_stages", 1)
+    assert np.array_equal(out[0], out[1])
+    ref = np.concatenate([oracle.rk2_homogeneous(N1, L, 1.0, f1, 0.01, 1.0).reshape(-1),
+                          oracle.rk2_homogeneous(N2, L, 0.0, f2, 0.01, 1.0).reshape(-1)])
+    assert np.abs(out[0] - ref).max() <= 1e-7 * np.abs(buf).max()
+
+
 def test_nonfinite_input_is_reported(bte):
     N = 8
     c = ctx_for(bte, ((N, L, 1.0),))
