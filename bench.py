@@ -342,6 +342,7 @@ def main():
     ctx.profile_read("*", stream)
 
     # end to end through the public API: pinned host state in and out every step
+    # (bte_transfer: the library's copy kernels read and write the pinned buffers)
     fh_in = torch.from_numpy(f.cpu().numpy()).pin_memory()
     fh_out = torch.empty_like(fh_in).pin_memory()
     e2e_ms = []
@@ -351,9 +352,9 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            f.copy_(fh_in, non_blocking=True)
+            ctx.transfer(f, fh_in, stream=stream)
             ctx.step(f, DT, EPS, transport=tr, mode=bte.FP32, stream=stream)
-            fh_out.copy_(f, non_blocking=True)
+            ctx.transfer(fh_out, f, stream=stream)
             e1.record(stream)
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))

@@ -37,6 +37,7 @@
 #ifndef BTE_H
 #define BTE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -213,6 +214,19 @@ bte_status bte_step_ex(bte_ctx *ctx, double *f, const bte_instance *inst, int64_
 /* Synchronise `stream`, read and clear the device status word.
  * Returns BTE_OK, BTE_ETIMEOUT, BTE_ENONFINITE or BTE_ECUDA. */
 bte_status bte_sync_status(bte_ctx *ctx, void *stream);
+
+/* Copy `bytes` between a HOST buffer and DEVICE memory, ordered on `stream`
+ * (the state in and out of a step, e.g.). kind BTE_HOST_TO_DEVICE: src host,
+ * dst device; BTE_DEVICE_TO_HOST: src device, dst host. Where the host buffer
+ * is reachable from the device (page-locked memory on a system with unified
+ * addressing; on GB300 over the chip-to-chip link) a kernel of the library
+ * moves it from every SM; otherwise cudaMemcpyAsync (synchronous for pageable
+ * memory). Both buffers must hold `bytes`; they stay the caller's. No
+ * counterpart in the paper. Errors: BTE_EINVAL (null buffer, unknown kind),
+ * BTE_ECUDA. */
+#define BTE_HOST_TO_DEVICE 0
+#define BTE_DEVICE_TO_HOST 1
+bte_status bte_transfer(bte_ctx *ctx, void *dst, const void *src, size_t bytes, int kind, void *stream);
 
 /* Moments (C f)_i, i = mass, momentum 1..3, energy, per cell: out is a DEVICE
  * array of 5*ninst doubles. FP64. Asynchronous. */

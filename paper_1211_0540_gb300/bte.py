@@ -31,7 +31,7 @@ EXPORTS = ["bte_create", "bte_destroy", "bte_last_error", "bte_init_weights", "b
            "bte_mlp_set_scales", "bte_mlp_fit_scales", "bte_mlp_get_params", "bte_mlp_set_params", "bte_mlp_train",
            "bte_mlp_grads", "bte_mlp_infer", "bte_learned_stats", "bte_learned_sample",
            "bte_learned_indicator", "bte_autotune", "bte_tune_save",
-           "bte_tune_load", "bte_state_save", "bte_state_load", "bte_alu_peak"]
+           "bte_tune_load", "bte_state_save", "bte_state_load", "bte_alu_peak", "bte_transfer"]
 
 
 class Grid(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path=None):
         "bte_step_ex": (c_int, [vp, vp, ctypes.POINTER(Instance), c_i64, c_d, c_d,
                                 ctypes.POINTER(TransportEx), c_int, vp]),
         "bte_sync_status": (c_int, [vp, vp]),
+        "bte_transfer": (c_int, [vp, vp, vp, ctypes.c_size_t, c_int, vp]),
         "bte_moments": (c_int, [vp, vp, vp, ctypes.POINTER(Instance), c_i64, vp]),
         "bte_version": (ctypes.c_char_p, []),
         "bte_profile_enable": (c_int, [vp, c_int]),
@@ -442,6 +443,18 @@ class Context:
         self._rc(self._lib.bte_alu_peak(self._h, int(kind), ctypes.byref(tf), ctypes.byref(ms), _stream(stream)),
                  "bte_alu_peak")
         return tf.value
+
+    def transfer(self, dst, src, stream=None):
+        """Copy tensor src into tensor dst (same size) between host and device
+        memory through bte_transfer; the host tensor should be pinned."""
+        if dst.numel() * dst.element_size() != src.numel() * src.element_size():
+            raise ValueError("transfer: dst and src differ in size")
+        if dst.is_cuda == src.is_cuda:
+            raise ValueError("transfer: one tensor on the host, one on the device")
+        kind = 0 if dst.is_cuda else 1
+        self._rc(self._lib.bte_transfer(self._h, _ptr(dst), _ptr(src), dst.numel() * dst.element_size(), kind,
+                                        _stream(stream)), "bte_transfer")
+        return dst
 
     def sync_status(self, stream=None):
         rc = self._lib.bte_sync_status(self._h, _stream(stream))

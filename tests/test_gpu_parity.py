@@ -419,6 +419,38 @@ def test_fused_stage_transforms_on_an_uneven_batch(bte):
     assert np.abs(out[0] - ref).max() <= 1e-7 * np.abs(buf).max()
 
 
+def test_transfer_round_trips_host_and_device(bte):
+    """bte_transfer: pinned host buffers through the library's copy kernels
+    (16-byte and byte-wise paths) and pageable ones through cudaMemcpyAsync,
+    both directions, ordered on a side stream; bytes must come back unchanged."""
+    c = ctx_for(bte, ((8, L, 1.0),))
+    s = torch.cuda.Stream()
+    rng = np.random.default_rng(3)
+    for n, pin in ((1 << 20, True), (12345, True), (4097, False)):
+        src = torch.from_numpy(rng.standard_normal(n))
+        if pin:
+            src = src.pin_memory()
+        dev = torch.empty(n, dtype=torch.float64, device="cuda")
+        back = torch.empty(n, dtype=torch.float64)
+        if pin:
+            back = back.pin_memory()
+        torch.cuda.synchronize()
+        c.transfer(dev, src, stream=s)
+        with torch.cuda.stream(s):
+            dev.mul_(2.0)
+        c.transfer(back, dev, stream=s)
+        s.synchronize()
+        assert torch.equal(back, 2.0 * src), (n, pin)
+    # odd byte count and offset: the byte-wise kernel
+    src = torch.arange(1001, dtype=torch.uint8).pin_memory()
+    dev = torch.zeros(1001, dtype=torch.uint8, device="cuda")
+    c.transfer(dev[1:], src[:-1], stream=s)
+    s.synchronize()
+    assert torch.equal(dev[1:].cpu(), src[:-1])
+    with pytest.raises(ValueError):
+        c.transfer(dev, src[:10])
+
+
 def test_nonfinite_input_is_reported(bte):
     N = 8
     c = ctx_for(bte, ((N, L, 1.0),))
