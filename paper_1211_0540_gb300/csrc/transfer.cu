@@ -5,6 +5,7 @@
 // it with 16-byte accesses from every SM: many more requests in flight than a
 // copy engine keeps, so more of the link's bandwidth. Otherwise, and for
 // device-to-device copies, cudaMemcpyAsync.
+#include <algorithm>
 #include <cstdint>
 
 #include "bte_internal.h"
@@ -67,7 +68,10 @@ extern "C" bte_status bte_transfer(bte_ctx *c, void *dst, const void *src, size_
         const int grid = 4 * (c->num_sms > 0 ? c->num_sms : 1);
         if ((reinterpret_cast<uintptr_t>(s) & 15u) == 0 && (reinterpret_cast<uintptr_t>(d) & 15u) == 0 &&
             bytes % 16 == 0) {
-            copy16_kernel<<<grid, 256, 0, st>>>(static_cast<const uint4 *>(s), static_cast<uint4 *>(d), bytes / 16);
+            // at least four vectors per thread, so that each keeps four in flight
+            const size_t n = bytes / 16;
+            const int g16 = (int)std::min<size_t>((size_t)grid, std::max<size_t>(1, (n + 1023) / 1024));
+            copy16_kernel<<<g16, 256, 0, st>>>(static_cast<const uint4 *>(s), static_cast<uint4 *>(d), n);
         } else {
             copy1_kernel<<<grid, 256, 0, st>>>(static_cast<const unsigned char *>(s), static_cast<unsigned char *>(d),
                                                bytes);
