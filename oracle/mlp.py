@@ -3,7 +3,7 @@
 The paper has no learned component; this module states the library's
 surrogate (a residual MLP on the normalised distribution) in plain numpy FP64
 so that the GPU training and inference kernels can be checked against it:
-    x = s_in f / rho,  h1 = GELU(W1 x + b1),  h2 = h1 + GELU(W2 h1 + b2),
+    x = s_in f / rho (0 for rho = 0),  h1 = GELU(W1 x + b1),  h2 = h1 + GELU(W2 h1 + b2),
     y = W3 h2 + b3,    t = s_out Q / rho^2,   loss = mean((y - t)^2),
 rho = sum f dv^3, GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
 Parameters are one flat vector W1 [H, M], b1, W2 [H, H], b2, W3 [M, H], b3.
@@ -45,7 +45,9 @@ def nparams(M, H):
 def forward(p, f, dv3, s_in, M, H):
     W1, b1, W2, b2, W3, b3 = split(p, M, H)
     rho = f.sum(axis=1) * dv3
-    x = s_in * f / rho[:, None]
+    # a vacuum cell (rho = 0) gets x = 0 (its output rho^2 y / s_out is 0 whatever y)
+    scale = np.divide(s_in, rho, out=np.zeros_like(rho), where=rho != 0)
+    x = f * scale[:, None]
     z1 = x @ W1.T + b1
     h1 = gelu(z1)
     z2 = h1 @ W2.T + b2

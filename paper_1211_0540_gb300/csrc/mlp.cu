@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kT) prep_kernel(const double *__restrict__ f, 
     }
     __syncthreads();
     const double rho = rho_s;
-    const float a = (float)((double)s_in / rho);
+    const float a = rho != 0.0 ? (float)((double)s_in / rho) : 0.f;  // a vacuum cell (rho = 0) gets x = 0
     for (int j = threadIdx.x; j < M; j += blockDim.x) {
         const __nv_bfloat16 x = __float2bfloat16_rn(xs[j] * a);
         X[(size_t)r * M + j] = x;

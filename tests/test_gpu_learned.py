@@ -100,6 +100,32 @@ def test_learned_mode_thresholds_the_indicator(bte):
     c.close()
 
 
+def test_vacuum_cells_give_zero_in_the_learned_mode(bte):
+    """Cells with f = 0 (rho = 0) beside ordinary ones: the surrogate takes x = 0
+    for them, so Q is exactly 0 with or without the fallback; the ordinary
+    cells get the same values as in a batch without vacuum cells."""
+    N, H = 8, 128
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.mlp_init(0, H, seed=5)
+    c.mlp_set_scales(10.0, 50.0)
+    f = inputs.homogeneous_cells(N, L, 40, seed=8)
+    fz = f.copy()
+    fz[[3, 17, 39]] = 0.0
+    ft = torch.from_numpy(fz).cuda().reshape(-1)
+    for fallback in (False, True):
+        Q = c.collide(ft, mode=bte.LEARNED, fallback=fallback).cpu().numpy().reshape(40, -1)
+        c.sync_status()
+        assert np.all(Q[[3, 17, 39]] == 0.0), fallback
+        assert np.all(np.isfinite(Q))
+    Qs = c.collide(ft, mode=bte.LEARNED, fallback=False).cpu().numpy().reshape(40, -1)
+    Qref = c.collide(torch.from_numpy(f).cuda().reshape(-1), mode=bte.LEARNED,
+                     fallback=False).cpu().numpy().reshape(40, -1)
+    keep = [i for i in range(40) if i not in (3, 17, 39)]
+    assert np.array_equal(Qs[keep], Qref[keep])
+    c.close()
+
+
 @pytest.fixture(scope="module")
 def trained(bte):
     """Width-1024 surrogate at N = 16 trained as config 5 prescribes (200k pairs

@@ -10,6 +10,7 @@ of Ghat only, unprojected), computed by the oracle. Bars:
 Sizes span several 32-cell groups and a ragged tail; the full-size workloads
 are checked on sampled cells.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -477,6 +478,13 @@ def test_invalid_arguments_rejected(bte):
     assert e.value.code == -6
     with pytest.raises(bte.BteError):
         c.step(f, -1.0)
+    with pytest.raises(bte.BteError) as e:  # no cells
+        c.collide(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert e.value.code == -1
+    lib = bte.load()  # more instances than a batch takes: refused before any memory is read
+    rc = lib.bte_collide(c._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(f.data_ptr()), None,
+                         (1 << 24) + 1, bte.FP32, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1
     d = bte.Context(0)
     with pytest.raises(bte.BteError):
         d.init_weights([(10, L, 1.0)])  # unsupported N
