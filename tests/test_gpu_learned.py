@@ -59,8 +59,9 @@ def test_indicator_sample_is_the_published_generator(bte, N):
     c.close()
 
 
-@pytest.mark.parametrize("N,ncells,lam", [(8, 40, 1.0), (16, 37, 1.0), (16, 33, 0.0)])
-def test_indicator_matches_oracle(bte, N, ncells, lam):
+@pytest.mark.parametrize("N,ncells,lam,split", [(8, 40, 1.0, 4), (16, 37, 1.0, 4), (16, 33, 0.0, 4), (12, 35, 1.0, 0),
+                                                (16, 38, 1.0, 1), (8, 41, -1.0, 2)])
+def test_indicator_matches_oracle(bte, N, ncells, lam, split):
     f = inputs.homogeneous_cells(N, L, ncells, seed=600 + N + ncells)
     rng = np.random.default_rng(601 + N)
     Qo = oracle.collide(N, L, lam, f)
@@ -71,6 +72,7 @@ def test_indicator_matches_oracle(bte, N, ncells, lam):
     Q[3::4] = 0.0
     c = bte.Context(0)
     c.init_weights([(N, L, lam)])
+    c.set_option("dft_split", split)  # the indicator's transform of f runs in the batch's configuration
     ind = c.learned_indicator(torch.from_numpy(f).cuda(), torch.from_numpy(np.ascontiguousarray(Q)).cuda())
     c.sync_status()
     got = ind.cpu().numpy()

@@ -221,6 +221,39 @@ def test_learned_step_fallback_varies_between_replays():
     c.close()
 
 
+@pytest.mark.parametrize("split", [0, 1, 2])
+def test_learned_fallback_in_every_transform_configuration(split):
+    """The device-built fallback batch (flagged cells compacted, unused groups
+    marked -2) through the forward transforms of every dft_split: the same
+    flagged cells and, for them, the FP32 operator's values within its rounding
+    of the default configuration's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    bte, c, f = _learned_ctx(ncells=100)
+    q = c.collide(f, mode=bte.LEARNED, fallback=False)
+    ind = c.learned_indicator(f, q).cpu().numpy()
+    # about 70 % of the cells recomputed (several groups, one unused), the threshold in the middle of
+    # a gap between indicator values, so that the transforms' rounding flips no cell
+    srt = np.sort(ind)
+    i0 = int(0.3 * len(srt))
+    j = max(range(i0 - 5, i0 + 5), key=lambda k: srt[k + 1] - srt[k])
+    tol_ppm = int(0.5 * (srt[j] + srt[j + 1]) * 1e6)
+    c.set_option("learned_tol_ppm", tol_ppm)
+    out = {}
+    for sp in (4, split):
+        c.set_option("dft_split", sp)
+        c.learned_stats(reset=True)
+        out[sp] = c.collide(f, mode=bte.LEARNED).cpu().numpy().reshape(100, -1)
+        st = c.learned_stats(reset=True)
+        c.sync_status()
+        assert st["fallbacks"] == int(np.sum(~(ind <= 1e-6 * tol_ppm)))
+    flagged = ~(ind <= 1e-6 * tol_ppm)
+    a, b = out[4][flagged], out[split][flagged]
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+    assert np.array_equal(out[4][~flagged], out[split][~flagged])  # the surrogate's cells are untouched
+    c.close()
+
+
 def test_fit_scales_matches_numpy():
     """bte_mlp_fit_scales: s_out = 1 / sqrt(mean (Q / rho^2)^2), rho = sum f dv^3."""
     if not torch.cuda.is_available():
