@@ -179,6 +179,41 @@ def test_learned_step_is_heun_on_the_learned_operator():
     c.close()
 
 
+def test_learned_strang_step_on_the_refined_grid():
+    """The learned mode inside a Strang step on cells of unequal width with a
+    specular wall and a no-flux boundary (the sudden-heating set-up): at
+    tolerance 0 every cell is recomputed and the step equals the FP32 operator's
+    step bit for bit, replayed from a captured graph; mass sum(dx f) holds."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1211_0540_gb300 import bte
+    N = 8
+    dx = inputs.sudden_heating_grid()
+    nx = dx.size
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    c.mlp_init(0, 128, seed=5)
+    c.mlp_set_scales(10.0, 50.0)
+    c.set_option("conv_split", 0)
+    c.set_option("learned_tol_ppm", 0)
+    f0 = inputs.wall_heating_initial(N, L, nx) * (1.0 + 0.1 * np.sin(np.arange(nx)))[:, None]
+    tr = dict(nx=nx, dx=list(dx), bc_left=bte.BC_SPECULAR, bc_right=bte.BC_NOFLUX)
+    s = torch.cuda.Stream()
+    out = {}
+    for mode in (bte.LEARNED, bte.FP32):
+        ft = torch.from_numpy(f0.copy()).cuda().reshape(-1)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                c.step(ft, 0.01, 1.0, transport=tr, mode=mode, stream=s)
+        c.sync_status(s)
+        out[mode] = ft.cpu().numpy().reshape(nx, -1)
+    assert np.array_equal(out[bte.LEARNED], out[bte.FP32])
+    st = c.learned_stats(reset=True)
+    assert st["fallbacks"] == st["cells"] == 2 * 2 * nx
+    c.close()
+
+
 def test_learned_step_fallback_varies_between_replays():
     """One captured learned step replayed on states whose flagged sets differ:
     the fallback list is built on the device at every replay. Each replay

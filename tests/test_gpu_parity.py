@@ -811,6 +811,27 @@ def test_non_integer_lambda_matches_oracle(bte, N, ncells, lam):
         assert np.all(np.abs(oracle.moments(N, L, Qg)) <= 1e-12 * abs_moment_scale(N, Qg))
 
 
+@pytest.mark.parametrize("N,ncells,lam", [(8, 20, -1.5), (12, 9, 0.5)])
+def test_heun_step_for_soft_and_hard_potentials_matches_oracle(bte, N, ncells, lam):
+    """One Heun step (Sec. 3.1) with weights from the radial quadrature
+    (variable soft and hard potentials): both paths against the oracle's step;
+    mass, momentum and energy kept."""
+    f = inputs.homogeneous_cells(N, L, ncells, seed=850 + N)
+    ref = oracle.rk2_homogeneous(N, L, lam, f, 0.02, 1.0)
+    c = ctx_for(bte, ((N, L, lam),))
+    s = torch.cuda.Stream()
+    for mode, tol in ((bte.FP64_PLAIN, 1e-13), (bte.FP32, 1e-7)):
+        ft = torch.from_numpy(f.copy()).cuda()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            c.step(ft, 0.02, 1.0, mode=mode, stream=s)
+        c.sync_status(s)
+        g = ft.cpu().numpy()
+        assert np.abs(g - ref).max() <= tol * np.abs(f).max(), (mode, np.abs(g - ref).max())
+        m0, m1 = oracle.moments(N, L, f), oracle.moments(N, L, g)
+        assert np.all(np.abs(m1 - m0) <= 1e-12 * np.abs(m0[:, [0, 4]]).max(axis=1)[:, None])
+
+
 @pytest.mark.parametrize("N,ncells,lam,beta", [(8, 40, 1.0, 0.8), (12, 33, 0.0, 0.6), (16, 34, 1.0, 0.9)])
 def test_inelastic_collisions_match_oracle(bte, N, ncells, lam, beta):
     """Inelastic collisions (beta < 1 in Eq. GHat_calc; Sec. 3.3 drops the energy
