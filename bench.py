@@ -89,7 +89,7 @@ def parse():
     ap.add_argument("--conv-warps", type=int, default=None, help="warps per CTA of the convolution (conv_warps)")
     ap.add_argument("--conv-split", type=int, default=None, choices=[0, 1],
                     help="variant 4: cut the costliest pencil items in two (conv_split)")
-    ap.add_argument("--dft-split", type=int, default=None, help="fused transforms: CTAs per cell (1, 2, 4), or 0 for one CTA with four threads per pencil")
+    ap.add_argument("--dft-split", type=int, default=None, help="CTAs per cell in the fused transforms (1, 2, 4)")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="wall-heating",
                     help="wall-heating (the headline line) or one of the secondary workloads")
     ap.add_argument("--cells", type=int, default=256, help="sweep-n32: number of cells (default 256)")

@@ -301,10 +301,7 @@ bte_status bte_graph_count(const bte_ctx *ctx, int64_t *count);
  *                      transform (the intermediate state is not stored), bit
  *                      for bit the result of separate launches (0);
  *       "dft_split"   CTAs (one thread-block cluster) per cell in the fused
- *                      transforms of N <= 16: 1, 2 or 4 (default 4), one
- *                      thread per pencil; 0: one CTA per cell with four
- *                      threads per pencil (each computes a quarter of the
- *                      pencil's outputs: 4 N^2 threads per cell);
+ *                      transforms of N <= 16: 1, 2 or 4 (default 4);
  *       "debug_conv_stall" testing only: 1 makes every warp of the
  *                      cooperative convolution (conv_impl 1..4) skip the
  *                      copies of its first block, so that its bounded wait runs
@@ -340,8 +337,8 @@ bte_status bte_state_load(bte_ctx *ctx, const char *path, double *f, int64_t n, 
  * bte_collide) it runs one projected FP32 collide of f per candidate
  * configuration -- convolution variant 1, 2, 3 or 4, 3 or 4 warps per CTA, 1 or 2
  * blocks in flight per warp, compensated merge every 16 or 32 blocks, for
- * variant 4 with and without split pencil items, and for N <= 16 the fused
- * transforms' dft_split 0, 1, 2 and 4 -- times reps
+ * variant 4 with and without split pencil items, and for N <= 16 one, two or
+ * four CTAs per cell in the fused transforms -- times reps
  * repetitions with CUDA events on `stream`, and keeps the fastest as this
  * context's configuration for batches of the same shape (the same set of
  * grid sizes and number of 32-cell slots); it takes precedence over the

@@ -1370,7 +1370,7 @@ bte_status bte_launch_count(const bte_ctx *c, int64_t *count) {
 
 static int *option_slot(bte_ctx *c, const char *name, int *lo, int *hi) {
     if (!std::strcmp(name, "conv_impl")) { *lo = 0; *hi = 5; return &c->conv_impl; }
-    if (!std::strcmp(name, "dft_split")) { *lo = 0; *hi = 4; return &c->dft_split; }
+    if (!std::strcmp(name, "dft_split")) { *lo = 1; *hi = 4; return &c->dft_split; }
     if (!std::strcmp(name, "debug_conv_stall")) { *lo = 0; *hi = 1; return &c->debug_conv_stall; }
     if (!std::strcmp(name, "profile_mask")) { *lo = 0; *hi = 63; return &c->prof_mask; }
     if (!std::strcmp(name, "conv_warps")) { *lo = 1; *hi = 8; return &c->conv_warps; }
@@ -1512,7 +1512,7 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
         for (int warps : {4, 3})
             for (int stages : {1, 2})
                 for (int merge : {16, 32})
-                    for (int split : {4, 2, 1, 0})
+                    for (int split : {4, 2, 1})
                         for (int csplit : {1, 0}) {
                         if (!small_n && split != 4) continue;
                         if (csplit && (impl != 4 || B->nsplit == 0)) continue;
@@ -1701,7 +1701,7 @@ bte_status bte_tune_load(bte_ctx *c, const char *path, int *loaded) {
             return fail(c, BTE_EINVAL, "bte_tune_load: malformed entry: " + line);
         if (g.impl < 0 || g.impl > 5 || g.warps < 1 || g.warps > 8 || g.stages < 0 || g.stages > 4 || g.merge < 1 ||
             g.csplit < 0 || g.csplit > 1 ||
-            (g.split != 0 && g.split != 1 && g.split != 2 && g.split != 4))
+            (g.split != 1 && g.split != 2 && g.split != 4))
             return fail(c, BTE_EINVAL, "bte_tune_load: out-of-range entry: " + line);
         got[key] = g;
         pos += 10;

@@ -179,7 +179,7 @@ struct bte_ctx {
     int conv_merge = 16;       // blocks per compensated (TwoSum) merge
     int conv_impl = 4;         // 0 warp items, 1 CTA-cooperative, 2 cooperative + packed f32x2,
                                // 3 as 2 at 2 CTAs/SM, 4 as 2 with the compensated sums in shared memory
-    int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16); 0: one CTA, 4 threads per pencil
+    int dft_split = 4;         // CTAs per cell of the fused transforms (N <= 16)
     int conv_split = 1;        // variant 4: split the costliest pencil items in two
     int dft_fuse_stages = 1;   // FP32 Heun step: stage 1's inverse transform also forms stage 2's forward
     int debug_conv_stall = 0;  // testing only: make the convolution's waits run out

@@ -512,294 +512,6 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
     }
 }
 
-// ---------------------------------------------------------------------------
-// Four threads per pencil (N = 8, 12, 16; one CTA per cell, option dft_split 0).
-// Each one-dimensional pass splits a pencil's transform at the first radix-4
-// stage of the decimation in time (fft_reg.cuh): with j = (N/4) j1 + j2 and
-// k = k1 + 4 k2, thread k1 of the pencil forms, for every j2, output k1 of the
-// radix-4 butterfly over j1 (factors +-1, +-i only), twiddles it by
-// w_N^{S j2 k1}, and transforms the N/4 values over j2, which yields
-// y_{k1 + 4 k2}. The centring signs are (-1)^j on the input and (-1)^k =
-// (-1)^k1 on the output. The four threads of a pencil sit at the same lane of
-// four consecutive warps, so k1 is uniform over a warp and a switch runs a
-// pass instantiated per k1 with every index a compile-time constant. A cell
-// thus has 4 N^2 threads instead of N^2, which hides the memory, barrier and
-// FP64 latencies when a batch has about one cell per SM; the forward stages
-// the cell's f and the inverse its Qhat through shared memory in one sweep of
-// the whole cell (16-byte loads of f), before the passes.
-// ---------------------------------------------------------------------------
-template <int N>
-struct R4Shape {
-    static constexpr int NN = N * N, M = N * N * N, H = N / 2, N4 = N / 4;
-    static constexpr int PW = (NN + 31) / 32;  // warps per k1 (32 pencils each)
-    static constexpr int NT = 4 * PW * 32;     // threads per CTA
-    static constexpr int NW = NT / 32;
-    static constexpr int PX = N + 1;           // padded row (against bank conflicts)
-    static constexpr size_t rowbuf = sizeof(float2) * NN * PX;
-    // forward: [0, rowbuf) real f, then the second pass's output; [rowbuf, 2 rowbuf) the first pass's
-    static constexpr size_t smem_fwd = 2 * rowbuf;
-    // inverse: region 0 staged Qhat (M float2), later the second pass's output (NN rows);
-    // region 1 the first pass's output, later Qt (FP32); then the pencils' corrections
-    static constexpr size_t reg0 = sizeof(float2) * M > rowbuf ? sizeof(float2) * M : rowbuf;
-    static constexpr size_t smem_inv = reg0 + rowbuf + sizeof(double) * NN;
-    static_assert(N % 4 == 0 && NW <= 32, "four threads per pencil need N % 4 == 0 and at most 32 warps");
-};
-
-// forward pass 1: along j3 for pencil p = (j1, j2), real input X[p][j] -> A[p][k3]
-template <int N, int Q>
-__device__ __forceinline__ void r4_fwd1(const float *X, float2 *A, int p, const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, -1, Q>([&](int j) { return make_float2(X[p * PX + j], 0.f); }, y, rt);
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) A[p * PX + Q + 4 * i] = y[i];
-}
-// forward pass 2: along j2 for pencil p = (j1, k3): A[(j1, j2)][k3] -> B[(j1, k2)][k3]
-template <int N, int Q>
-__device__ __forceinline__ void r4_fwd2(const float2 *A, float2 *B, int p, const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX;
-    const int j1 = p / N, k3 = p % N;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, -1, Q>([&](int j) { return A[(j1 * N + j) * PX + k3]; }, y, rt);
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) B[(j1 * N + Q + 4 * i) * PX + k3] = y[i];
-}
-// forward pass 3: along j1 for pencil p = (k2, k3): B[(j1, k2)][k3] -> fhat[k1][p] (group layout)
-template <int N, int Q>
-__device__ __forceinline__ void r4_fwd3(const float2 *B, float2 *g, int p, float scale, const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX, NN = N * N;
-    const int k2 = p / N, k3 = p % N;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, -1, Q>([&](int j) { return B[(j * N + k2) * PX + k3]; }, y, rt);
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i)
-        g[(int64_t)((Q + 4 * i) * NN + p) * kLanes] = make_float2(scale * y[i].x, scale * y[i].y);
-}
-
-#define BTE_R4_SWITCH(q, FN, N, ...)       \
-    switch (q) {                           \
-        case 0: FN<N, 0>(__VA_ARGS__); break; \
-        case 1: FN<N, 1>(__VA_ARGS__); break; \
-        case 2: FN<N, 2>(__VA_ARGS__); break; \
-        default: FN<N, 3>(__VA_ARGS__); break; \
-    }
-
-template <int N>
-__global__ void __launch_bounds__(R4Shape<N>::NT)
-dft_fwd_r4_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, DftSeg s, float scale,
-                  float2 *__restrict__ G, int *status) {
-    using S = R4Shape<N>;
-    constexpr int M = S::M, NN = S::NN, PX = S::PX, NT = S::NT;
-    extern __shared__ __align__(16) char smem_raw[];
-    float *X = reinterpret_cast<float *>(smem_raw);                   // [p][j], rows of PX
-    float2 *B = reinterpret_cast<float2 *>(smem_raw);                 // [j1][k2][k3] (after X), rows of PX
-    float2 *A = reinterpret_cast<float2 *>(smem_raw + S::rowbuf);     // [j1][j2][k3], rows of PX
-    const int sl = blockIdx.x, t = threadIdx.x;
-    const int64_t off = slot_off[s.s0 + sl];
-    if (off == -2) return;  // a slot of a group that holds no cell this call (nothing reads it)
-    float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
-    if (off < 0) {  // padding lane of a group: zero fhat
-        for (int e = t; e < M; e += NT) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);
-        return;
-    }
-    // the cell's f, narrowed to FP32 (integer pipes), in one coalesced sweep
-    bool bad = false;
-    const double *fc = f + off;
-    if ((reinterpret_cast<uintptr_t>(fc) & 15u) == 0) {
-        const double2 *f2 = reinterpret_cast<const double2 *>(fc);
-        for (int e2 = t; e2 < M / 2; e2 += NT) {
-            const double2 d = f2[e2];
-            bad |= !fpc::finite64(d.x) || !fpc::finite64(d.y);
-            const int e = 2 * e2, p = e / N, j = e % N;  // N even: j + 1 is in the same row
-            X[p * PX + j] = fpc::narrow(d.x);
-            X[p * PX + j + 1] = fpc::narrow(d.y);
-        }
-    } else {
-        for (int e = t; e < M; e += NT) {
-            const double d = fc[e];
-            bad |= !fpc::finite64(d);
-            X[(e / N) * PX + e % N] = fpc::narrow(d);
-        }
-    }
-    if (bad) atomicOr(status, ST_NONFINITE);
-    __syncthreads();
-    const int w = t >> 5, q = w & 3, p = (w >> 2) * 32 + (t & 31);
-    const bool act = p < NN;
-    const float2(&rt)[N] = CRoot<N>::get();
-    if (act) BTE_R4_SWITCH(q, r4_fwd1, N, X, A, p, rt)
-    __syncthreads();
-    if (act) BTE_R4_SWITCH(q, r4_fwd2, N, A, B, p, rt)
-    __syncthreads();
-    if (act) BTE_R4_SWITCH(q, r4_fwd3, N, B, g, p, scale, rt)
-}
-
-// inverse pass 1: along k1 for pencil p = (k2, k3): Qh[k1][p] -> B[(j1, k2)][k3]
-template <int N, int Q>
-__device__ __forceinline__ void r4_inv1(const float2 *Qh, float2 *B, int p, const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX, NN = N * N;
-    const int k2 = p / N, k3 = p % N;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, 1, Q>([&](int k) { return Qh[k * NN + p]; }, y, rt);
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) B[((Q + 4 * i) * N + k2) * PX + k3] = y[i];
-}
-// inverse pass 2: along k2 for pencil p = (j1, k3): B[(j1, k2)][k3] -> C[(j1, j2)][k3]
-template <int N, int Q>
-__device__ __forceinline__ void r4_inv2(const float2 *B, float2 *C, int p, const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX;
-    const int j1 = p / N, k3 = p % N;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, 1, Q>([&](int k) { return B[(j1 * N + k) * PX + k3]; }, y, rt);
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) C[(j1 * N + Q + 4 * i) * PX + k3] = y[i];
-}
-// inverse pass 3: along k3 for pencil p = (j1, j2): real part of the output,
-// scaled, into R[p][j3]; the thread's moment partials of Qt (double-float)
-template <int N, int Q>
-__device__ __forceinline__ void r4_inv3(const float2 *C, float *R, int p, float scale, Df (&mom)[5],
-                                        const float2 (&rt)[N]) {
-    constexpr int PX = R4Shape<N>::PX, H = N / 2;
-    float2 y[N / 4];
-    fftr::centred_quarter<N, 1, Q>([&](int k) { return C[p * PX + k]; }, y, rt);
-    Df s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < N / 4; ++i) {
-        const int j3 = Q + 4 * i;
-        const float r = scale * y[i].x;
-        R[p * PX + j3] = r;
-        df_add(s0, r);
-        df_add_prod(s1, (float)(j3 - H), r);
-        df_add_prod(s2, (float)((j3 - H) * (j3 - H)), r);
-    }
-    const int w1 = p / N - H, w2 = p % N - H;
-    mom[0] = s0;
-    mom[1] = df_mul_int(s0, (float)w1);
-    mom[2] = df_mul_int(s0, (float)w2);
-    mom[3] = s1;
-    mom[4] = df_add(df_mul_int(s0, (float)(w1 * w1 + w2 * w2)), s2);
-}
-
-// mode: 0 raw Qt; 1 P Qt; 2 P Qt and y = x + a Q; 3 P Qt and y += a (qp + Q)
-template <int N>
-__global__ void __launch_bounds__(R4Shape<N>::NT)
-dft_inv_r4_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ slot_off, DftSeg s, float scale,
-                  double *__restrict__ q, ProjArgs pa, int mode, const double *__restrict__ x,
-                  double *__restrict__ y, const double *__restrict__ qp, double a) {
-    using S = R4Shape<N>;
-    constexpr int M = S::M, NN = S::NN, PX = S::PX, NT = S::NT, NW = S::NW, H = S::H;
-    extern __shared__ __align__(16) char smem_raw[];
-    float2 *Qh = reinterpret_cast<float2 *>(smem_raw);              // [k1][k2 N + k3] (M values)
-    float2 *C = reinterpret_cast<float2 *>(smem_raw);               // [j1][j2][k3] after Qh, rows of PX
-    float2 *B = reinterpret_cast<float2 *>(smem_raw + S::reg0);     // [j1][k2][k3], rows of PX
-    float *R = reinterpret_cast<float *>(smem_raw + S::reg0);       // Qt [p][j3] after B, rows of PX
-    double *base = reinterpret_cast<double *>(smem_raw + S::reg0 + S::rowbuf);
-    __shared__ float red[32][10];
-    __shared__ double sg[N], lam[5];
-    const int sl = blockIdx.x, t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t off = slot_off[s.s0 + sl];
-    if (off < 0) return;
-    // the time-update operands first: their memory latency overlaps the passes
-    constexpr int IT = (M + NT - 1) / NT;
-    const double *xo = x ? x + off : nullptr;
-    double *yo = y ? y + off : nullptr;
-    const double *qpo = qp ? qp + off : nullptr;
-    double u[IT], wv[IT];
-#pragma unroll
-    for (int i = 0; i < IT; ++i) {
-        const int e = t + i * NT;
-        u[i] = 0.0;
-        wv[i] = 0.0;
-        if (e < M) {
-            if (mode == 2) u[i] = xo[e];
-            else if (mode == 3) {
-                u[i] = yo[e];
-                wv[i] = qpo[e];
-            }
-        }
-    }
-    // the cell's Qhat (group layout: one cell's values are 8 bytes of every 256)
-    const float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
-    for (int e = t; e < M; e += NT) Qh[e] = g[(int64_t)e * kLanes];
-    __syncthreads();
-    const int q4 = w & 3, p = (w >> 2) * 32 + lane;
-    const bool act = p < NN;
-    const float2(&rt)[N] = CRoot<N>::get();
-    if (act) BTE_R4_SWITCH(q4, r4_inv1, N, Qh, B, p, rt)
-    __syncthreads();
-    if (act) BTE_R4_SWITCH(q4, r4_inv2, N, B, C, p, rt)
-    __syncthreads();
-    Df mom[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) mom[i] = Df{0.f, 0.f};
-    if (act) BTE_R4_SWITCH(q4, r4_inv3, N, C, R, p, scale, mom, rt)
-    if (mode != 0) {
-        // moments: warp trees, then warp 0 over the warps in order
-#pragma unroll
-        for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
-        if (lane == 0)
-#pragma unroll
-            for (int i = 0; i < 5; ++i) {
-                red[w][2 * i] = mom[i].hi;
-                red[w][2 * i + 1] = mom[i].lo;
-            }
-        __syncthreads();
-        if (w == 0) {
-#pragma unroll
-            for (int i = 0; i < 5; ++i) mom[i] = lane < NW ? Df{red[lane][2 * i], red[lane][2 * i + 1]} : Df{0.f, 0.f};
-#pragma unroll
-            for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
-            double mu = 0.0;
-            if (lane < 5) {
-                Df m{0.f, 0.f};
-#pragma unroll
-                for (int i = 0; i < 5; ++i)
-                    if (i == lane) m = mom[i];
-                // mu = (sum q, dv sum w_d q (d = 1..3), dv^2 sum |w|^2 q), w = j - N/2
-                const double sc = lane == 0 ? 1.0 : (lane == 4 ? pa.dv * pa.dv : pa.dv);
-                mu = ((double)m.hi + (double)m.lo) * sc;
-            }
-            double m5[5];
-#pragma unroll
-            for (int i = 0; i < 5; ++i) m5[i] = __shfl_sync(0xffffffffu, mu, i);
-            if (lane < 5) {
-                double l = 0.0;
-#pragma unroll
-                for (int k = 0; k < 5; ++k) l = fma(pa.ainv[lane * 5 + k], m5[k], l);
-                lam[lane] = l;
-            }
-        }
-        __syncthreads();
-        // correction C^T lambda = base(j1, j2) + sg(j3)
-        const double dv = pa.dv;
-        if (t < N) {
-            const double v = dv * (double)(t - H);
-            sg[t] = fma(lam[3], v, lam[4] * v * v);
-        }
-        if (t < NN) {
-            const double v1 = dv * (double)(t / N - H), v2 = dv * (double)(t % N - H);
-            base[t] = lam[0] + fma(lam[1], v1, fma(lam[2], v2, lam[4] * fma(v1, v1, v2 * v2)));
-        }
-    }
-    __syncthreads();
-    double *qo = q + off;
-#pragma unroll
-    for (int i = 0; i < IT; ++i) {
-        const int e = t + i * NT;
-        if (e < M) {
-            const int pp = e / N, j3 = e % N;
-            if (mode == 0) {
-                qo[e] = fpc::widen(R[pp * PX + j3]);
-                continue;
-            }
-            const double v = fpc::widen(R[pp * PX + j3]) - (base[pp] + sg[j3]);
-            qo[e] = v;
-            if (mode == 2) yo[e] = fma(a, v, u[i]);
-            else if (mode == 3) yo[e] = fma(a, wv[i] + v, u[i]);
-        }
-    }
-}
-#undef BTE_R4_SWITCH
-
 namespace {
 template <int N, int C>
 void fwd_launch(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale,
@@ -837,35 +549,8 @@ void prepare_n() {
     prepare_one<N, 1>();
     prepare_one<N, 2>();
     prepare_one<N, 4>();
-    cudaFuncSetAttribute(dft_fwd_r4_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)R4Shape<N>::smem_fwd);
-    cudaFuncSetAttribute(dft_inv_r4_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)R4Shape<N>::smem_inv);
 }
-// dft_split: 0 (four threads per pencil, one CTA per cell), 1, 2 or 4 CTAs per cell
-int norm_split(int split) { return split == 0 || split == 1 || split == 2 ? split : 4; }
-template <int N, int C>
-void fwd_any(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale, float2 *G,
-             int *status, cudaStream_t st) {
-    if constexpr (C == 0) {
-        using S = R4Shape<N>;
-        dft_fwd_r4_kernel<N><<<s.nslots, S::NT, S::smem_fwd, st>>>(f, slot_off, s, (float)scale, G, status);
-    } else {
-        fwd_launch<N, C>(f, slot_off, s, root, scale, G, status, st);
-    }
-}
-template <int N, int C>
-void inv_any(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale, double *q,
-             const ProjArgs &pa, int mode, const double *x, double *y, const double *qp, double a, cudaStream_t st) {
-    if constexpr (C == 0) {
-        using S = R4Shape<N>;
-        dft_inv_r4_kernel<N><<<s.nslots, S::NT, S::smem_inv, st>>>(G, slot_off, s, (float)scale, q, pa, mode, x, y,
-                                                                   qp, a);
-    } else {
-        inv_launch<N, C>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st);
-    }
-}
-
+int norm_split(int split) { return split == 1 || split == 2 ? split : 4; }
 template <int N>
 void upload_roots(const float2 (&sym)[N]) {
     float2 h[N];
@@ -901,7 +586,6 @@ void fused_dft_prepare(int N) {
 
 #define BTE_SPLIT_DISPATCH(FN, N, ...)                 \
     switch (norm_split(split)) {                       \
-        case 0: FN<N, 0>(__VA_ARGS__); break;          \
         case 1: FN<N, 1>(__VA_ARGS__); break;          \
         case 2: FN<N, 2>(__VA_ARGS__); break;          \
         default: FN<N, 4>(__VA_ARGS__); break;         \
@@ -926,9 +610,9 @@ void launch_dft_forward_pencils(const double *f, const int64_t *slot_off, const 
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, float2 *G, int *status, cudaStream_t st, int split) {
     switch (s.N) {
-        case 8: BTE_SPLIT_DISPATCH(fwd_any, 8, f, slot_off, s, root, scale, G, status, st) break;
-        case 12: BTE_SPLIT_DISPATCH(fwd_any, 12, f, slot_off, s, root, scale, G, status, st) break;
-        case 16: BTE_SPLIT_DISPATCH(fwd_any, 16, f, slot_off, s, root, scale, G, status, st) break;
+        case 8: BTE_SPLIT_DISPATCH(fwd_launch, 8, f, slot_off, s, root, scale, G, status, st) break;
+        case 12: BTE_SPLIT_DISPATCH(fwd_launch, 12, f, slot_off, s, root, scale, G, status, st) break;
+        case 16: BTE_SPLIT_DISPATCH(fwd_launch, 16, f, slot_off, s, root, scale, G, status, st) break;
         case 24: fwd_launch<24, 4>(f, slot_off, s, root, scale, G, status, st); break;
         case 32: fwd_launch<32, 8>(f, slot_off, s, root, scale, G, status, st); break;
         default: break;
@@ -939,17 +623,15 @@ void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const Df
                               double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
                               const double *qp, double a, cudaStream_t st, int split) {
     switch (s.N) {
-        case 8: BTE_SPLIT_DISPATCH(inv_any, 8, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
-        case 12: BTE_SPLIT_DISPATCH(inv_any, 12, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
-        case 16: BTE_SPLIT_DISPATCH(inv_any, 16, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 8: BTE_SPLIT_DISPATCH(inv_launch, 8, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 12: BTE_SPLIT_DISPATCH(inv_launch, 12, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
+        case 16: BTE_SPLIT_DISPATCH(inv_launch, 16, G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st) break;
         case 24: inv_launch<24, 4>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
         case 32: inv_launch<32, 8>(G, slot_off, s, root, scale, q, pa, mode, x, y, qp, a, st); break;
         default: break;
     }
 }
-bool inverse_forward_fused_supported(int N, int split) {
-    return N == 24 || N == 32 || ((N == 8 || N == 12 || N == 16) && norm_split(split) != 0);
-}
+bool inverse_forward_fused_supported(int N, int) { return fused_dft_supported(N); }
 
 void launch_dft_inverse_forward_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s,
                                       const float2 *root, double scale, double *q, const ProjArgs &pa,
@@ -970,12 +652,11 @@ void launch_dft_inverse_forward_fused(const float2 *G, const int64_t *slot_off, 
                     else if (s.N == 12) inv_fwd_launch<12, 2>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
                     else inv_fwd_launch<16, 2>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
                     break;
-                case 4:
+                default:
                     if (s.N == 8) inv_fwd_launch<8, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
                     else if (s.N == 12) inv_fwd_launch<12, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
                     else inv_fwd_launch<16, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st);
                     break;
-                default: break;  // split 0 has no fused form: the caller checks
             }
             break;
         case 24: inv_fwd_launch<24, 4>(G, slot_off, s, root, scale, q, pa, x, a, fscale, Gout, status, st); break;

@@ -108,41 +108,5 @@ __host__ __device__ __forceinline__ void centred(float2 (&y)[N], const float2 (&
     for (int k = 1; k < N; k += 2) y[k] = cneg(y[k]);
 }
 
-// x w_4^{S r}, r in 0..3 (+-1, +-i: no multiplication)
-template <int S>
-__host__ __device__ __forceinline__ float2 rot4(float2 x, int r) {
-    if (r == 0) return x;
-    if (r == 2) return cneg(x);
-    return r == 1 ? cmul_i<S>(x) : cmul_i<-S>(x);
-}
-
-// A quarter of the centred transform (N % 4 == 0): the outputs y[k2] = Y_{Q + 4 k2},
-// k2 < N/4, of Y_k = sum_j x_j w^(S (k - N/2)(j - N/2)), x_j = ld(j). With
-// j = (N/4) j1 + j2 and k = Q + 4 k2 (the first radix-4 stage of fft above):
-//   Y_{Q + 4 k2} = (-1)^Q sum_{j2} w_{N/4}^{S j2 k2} [ w_N^{S j2 Q} sum_{j1} (-1)^j x_j w_4^{S j1 Q} ],
-// so four threads, one per Q, share a pencil's transform.
-template <int N, int S, int Q, class Ld>
-__host__ __device__ __forceinline__ void centred_quarter(const Ld &ld, float2 (&y)[N / 4], const float2 (&rt)[N]) {
-    static_assert(N % 4 == 0 && Q >= 0 && Q < 4, "quarter transform");
-    constexpr int N4 = N / 4;
-#pragma unroll
-    for (int j2 = 0; j2 < N4; ++j2) {
-        float2 v = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int j1 = 0; j1 < 4; ++j1) {
-            const int j = N4 * j1 + j2;
-            float2 xv = ld(j);
-            if (j & 1) xv = cneg(xv);
-            v = cadd(v, rot4<S>(xv, (j1 * Q) & 3));
-        }
-        y[j2] = twiddle<N, S>(v, j2 * Q, rt);
-    }
-    fft<N4, S, N>(y, rt);
-    if (Q & 1) {
-#pragma unroll
-        for (int k2 = 0; k2 < N4; ++k2) y[k2] = cneg(y[k2]);
-    }
-}
-
 }  // namespace fftr
 }  // namespace bte

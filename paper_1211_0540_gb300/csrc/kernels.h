@@ -108,8 +108,7 @@ void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const Df
 // The first Heun stage's inverse (mode 2: Q = P Qt into q) fused with the second
 // stage's forward transform: f* = x + a Q is not stored; fhat(f*) (times fscale)
 // goes to Gout in the group layout. Same results as the inverse (mode 2) followed
-// by launch_dft_forward_fused on f*. Supported for N = 24, 32 and, with
-// dft_split 1, 2 or 4, for N = 8, 12, 16.
+// by launch_dft_forward_fused on f*. Supported wherever the fused transforms are.
 bool inverse_forward_fused_supported(int N, int split);
 void launch_dft_inverse_forward_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s,
                                       const float2 *root, double scale, double *q, const ProjArgs &pa,

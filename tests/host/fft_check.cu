@@ -1,8 +1,7 @@
 // Host check of the register FFT used by the fused transforms: every size the
 // library supports, both signs, plain and centred, against the dense sums
 // y_k = sum_j x_j exp(2 pi i S j k / N) and exp(2 pi i S (k - N/2)(j - N/2) / N)
-// in double precision, and the four quarters of the centred transform.
-// Prints one line per case: N S kind max|error| / max|y|.
+// in double precision. Prints one line per case: N S max|error| / max|y|.
 #include <cmath>
 #include <cstdio>
 #include <random>
@@ -36,53 +35,12 @@ static double check(std::mt19937 &g) {
     return err / mag;
 }
 
-// The four quarters of the centred transform (centred_quarter, one thread per
-// quarter in the fused transforms) against the same dense sum.
-template <int N, int S, int Q>
-static double quarter_err(const float2 (&x)[N], const float2 (&rt)[N], double &mag) {
-    const double pi = 3.14159265358979323846;
-    const int h = N / 2;
-    float2 y[N / 4];
-    centred_quarter<N, S, Q>([&](int j) { return x[j]; }, y, rt);
-    double err = 0.0;
-    for (int k2 = 0; k2 < N / 4; ++k2) {
-        const int k = Q + 4 * k2;
-        double re = 0.0, im = 0.0;
-        for (int j = 0; j < N; ++j) {
-            const double a = 2 * pi * S * (double)((k - h) * (j - h)) / N;
-            re += x[j].x * std::cos(a) - x[j].y * std::sin(a);
-            im += x[j].x * std::sin(a) + x[j].y * std::cos(a);
-        }
-        err = std::fmax(err, std::hypot(re - y[k2].x, im - y[k2].y));
-        mag = std::fmax(mag, std::hypot(re, im));
-    }
-    return err;
-}
-
-template <int N, int S>
-static double check_quarters(std::mt19937 &g) {
-    const double pi = 3.14159265358979323846;
-    float2 rt[N];
-    for (int t = 0; t < N; ++t) rt[t] = make_float2((float)std::cos(2 * pi * t / N), (float)std::sin(2 * pi * t / N));
-    std::uniform_real_distribution<float> u(-1.f, 1.f);
-    float2 x[N];
-    for (int j = 0; j < N; ++j) x[j] = make_float2(u(g), u(g));
-    double mag = 0.0;
-    double err = quarter_err<N, S, 0>(x, rt, mag);
-    err = std::fmax(err, quarter_err<N, S, 1>(x, rt, mag));
-    err = std::fmax(err, quarter_err<N, S, 2>(x, rt, mag));
-    err = std::fmax(err, quarter_err<N, S, 3>(x, rt, mag));
-    return err / mag;
-}
-
 template <int N>
 static void all(std::mt19937 &g) {
     std::printf("%d +1 plain %.3e\n", N, check<N, 1, false>(g));
     std::printf("%d -1 plain %.3e\n", N, check<N, -1, false>(g));
     std::printf("%d +1 centred %.3e\n", N, check<N, 1, true>(g));
     std::printf("%d -1 centred %.3e\n", N, check<N, -1, true>(g));
-    std::printf("%d +1 quarters %.3e\n", N, check_quarters<N, 1>(g));
-    std::printf("%d -1 quarters %.3e\n", N, check_quarters<N, -1>(g));
 }
 
 int main() {

@@ -59,7 +59,7 @@ def test_indicator_sample_is_the_published_generator(bte, N):
     c.close()
 
 
-@pytest.mark.parametrize("N,ncells,lam,split", [(8, 40, 1.0, 4), (16, 37, 1.0, 4), (16, 33, 0.0, 4), (12, 35, 1.0, 0),
+@pytest.mark.parametrize("N,ncells,lam,split", [(8, 40, 1.0, 4), (16, 37, 1.0, 4), (16, 33, 0.0, 4), (12, 35, 1.0, 1),
                                                 (16, 38, 1.0, 1), (8, 41, -1.0, 2)])
 def test_indicator_matches_oracle(bte, N, ncells, lam, split):
     f = inputs.homogeneous_cells(N, L, ncells, seed=600 + N + ncells)

@@ -608,12 +608,11 @@ def test_close_with_unread_profile_entries(bte):
     d.close()
 
 
-@pytest.mark.parametrize("split", [0, 1, 2, 4])
+@pytest.mark.parametrize("split", [1, 2, 4])
 @pytest.mark.parametrize("N,ncells", [(8, 40), (12, 33), (16, 35)])
 def test_fused_transform_cluster_split(bte, N, ncells, split):
-    """The fused transforms with a cell on 1, 2 or 4 CTAs, or on one CTA with
-    four threads per pencil (dft_split 0): raw and projected operator and one
-    Heun step against the oracle."""
+    """The fused transforms with a cell on 1, 2 or 4 CTAs (dft_split): raw and
+    projected operator and one Heun step against the oracle."""
     lam = 1.0
     f = inputs.homogeneous_cells(N, L, ncells, seed=500 + N + split)
     c = ctx_for(bte, ((N, L, lam),))
@@ -649,7 +648,7 @@ def test_autotune_choice_applies_and_round_trips(bte, tmp_path):
     c.init_weights([(N, L, lam)])
     cfg = c.autotune(ft, reps=2)
     assert cfg["conv_impl"] in (1, 2, 3, 4) and cfg["conv_warps"] in (3, 4) and cfg["conv_stages"] in (1, 2)
-    assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (0, 1, 2, 4) and cfg["ms"] > 0.0
+    assert cfg["conv_merge"] in (16, 32) and cfg["dft_split"] in (1, 2, 4) and cfg["ms"] > 0.0
     assert cfg["conv_split"] in (0, 1) and (cfg["conv_split"] == 0 or cfg["conv_impl"] == 4)
     Q = c.collide(ft)
     c.sync_status()
