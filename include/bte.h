@@ -242,7 +242,9 @@ bte_status bte_moments(bte_ctx *ctx, const double *f, double *out, const bte_ins
  * kernel: "conv32" (FP32 convolution), "conv64" (plain FP64 convolution),
  * "forward" (all forward transforms of a collide), "inverse" (all inverse
  * transforms of a collide with the projection and time update fused into
- * them), "transport" (one transport sub-step, two launches), "collide" (a
+ * them; with dft_fuse_stages, the first Heun stage's inverse also runs the
+ * second stage's forward transform, so a Heun step records one "forward"
+ * and two "inverse" launches), "transport" (one transport sub-step, two launches), "collide" (a
  * whole collide call), or "*" (all of them, summed).
  * bte_launch_count returns the number of libbte kernels enqueued by this context
  * so far (a graph replay counts its kernels). */

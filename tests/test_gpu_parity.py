@@ -528,21 +528,26 @@ def test_profiling_and_launch_count_with_graphs(bte):
     c.profile_enable(True)
     f = torch.from_numpy(inputs.homogeneous_cells(N, L, 40, seed=2)).cuda()
     s = torch.cuda.Stream()
-    n0 = c.launch_count()
     torch.cuda.synchronize()
-    with torch.cuda.stream(s):
-        for _ in range(3):
-            c.step(f, 0.01, 1.0, stream=s)
-    n, ms = c.profile_read("conv32", s)
-    assert n == 6 and ms > 0.0
-    # reading one kernel leaves the others pending
-    for name in ("forward", "inverse"):
-        n, ms = c.profile_read(name, s)
-        assert n == 6 and ms > 0.0, name
-    n, ms = c.profile_read("*", s)  # the six collide calls of the three steps
-    assert n == 6 and ms > 0.0
-    # per step: 2 x (fused forward DFT + convolution + fused inverse DFT with projection)
-    assert c.launch_count() - n0 == 3 * 6
+    # with the stage-fused transforms (default) the second Heun stage's forward
+    # transform runs inside the first stage's inverse and is timed with it
+    for fuse, nfwd, per_step in ((1, 3, 5), (0, 6, 6)):
+        c.set_option("dft_fuse_stages", fuse)
+        n0 = c.launch_count()
+        with torch.cuda.stream(s):
+            for _ in range(3):
+                c.step(f, 0.01, 1.0, stream=s)
+        n, ms = c.profile_read("conv32", s)
+        assert n == 6 and ms > 0.0
+        # reading one kernel leaves the others pending
+        for name, want in (("forward", nfwd), ("inverse", 6)):
+            n, ms = c.profile_read(name, s)
+            assert n == want and ms > 0.0, name
+        n, ms = c.profile_read("*", s)  # the six collide calls of the three steps
+        assert n == 6 and ms > 0.0
+        # per step: forward DFT + convolution + inverse DFT with projection (and the
+        # next stage's forward DFT) + convolution + inverse DFT with projection
+        assert c.launch_count() - n0 == 3 * per_step
     c.collide(f, stream=s)
     n, ms = c.profile_read("collide", s)
     assert n == 1 and ms > 0.0
