@@ -235,7 +235,9 @@ bte_status bte_moments(bte_ctx *ctx, const double *f, double *out, const bte_ins
 
 /* Kernel timing for benchmarks. When enabled, CUDA events are recorded on the
  * launching stream around every launch of the kernels named below (also inside
- * the graphs bte_step captures while enabled). bte_profile_read synchronises
+ * the graphs bte_step captures; switching profiling on or off drops the
+ * captured step graphs, so that the next steps capture again with or without
+ * the events). bte_profile_read synchronises
  * `stream`, returns the number of launches of `kernel` completed since they
  * were last read and their summed device time in milliseconds, and forgets
  * them (entries of other kernels stay pending).

@@ -1319,6 +1319,7 @@ bte_status bte_graph_count(const bte_ctx *c, int64_t *count) {
 
 bte_status bte_profile_enable(bte_ctx *c, int enable) {
     if (!c) return BTE_EINVAL;
+    if (c->prof != (enable != 0)) drop_graphs(c);  // step graphs are captured again, with or without events
     c->prof = enable != 0;
     return BTE_OK;
 }

@@ -558,6 +558,35 @@ def test_profiling_and_launch_count_with_graphs(bte):
     c.close()
 
 
+def test_profiling_switched_on_after_graph_capture(bte):
+    """Step graphs captured while profiling was off are captured again once it
+    is on (and again once it is off): the next steps record their events, and
+    none after it is switched off."""
+    N = 8
+    c = bte.Context(0)
+    c.init_weights([(N, L, 1.0)])
+    f = torch.from_numpy(inputs.homogeneous_cells(N, L, 40, seed=4)).cuda()
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            c.step(f, 0.01, 1.0, stream=s)
+    c.profile_enable(True)
+    with torch.cuda.stream(s):
+        for _ in range(2):
+            c.step(f, 0.01, 1.0, stream=s)
+    n, ms = c.profile_read("conv32", s)
+    assert n == 4 and ms > 0.0
+    c.profile_read("*", s)
+    c.profile_enable(False)
+    with torch.cuda.stream(s):
+        c.step(f, 0.01, 1.0, stream=s)
+    n, _ = c.profile_read("*", s)
+    assert n == 0
+    c.sync_status(s)
+    c.close()
+
+
 @pytest.mark.gpu
 def test_collide_matches_golden_fixture(bte):
     """Both GPU paths against the stored oracle fixture (tests/golden)."""
