@@ -853,7 +853,7 @@ bte_status enqueue_indicator(bte_ctx *c, Batch *B, const double *f, const double
     DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
     const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
     launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
-                             cfg_of(c, B).split);  // the batch's tuned split, else the option
+                             cfg_of(c, B).split, true);  // the batch's tuned split, else the option; sector order
     launch_dft_forward_pencils(Q, B->d_slot_off, ds, sf, c->ind->d_kk, c->ind->S, (float2 *)c->scratch[SC_QH],
                                c->d_status, st);  // only the sampled pencils are compared
     float *e2 = (float *)c->scratch[SC_MISC];

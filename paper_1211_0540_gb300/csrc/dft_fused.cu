@@ -144,7 +144,9 @@ __device__ __forceinline__ void load_pencil_f64(const double *__restrict__ fp, f
 // Cell = cluster of C CTAs; CTA r owns the slab j1 in [r JR, (r+1) JR) of the
 // first two passes and the slab k2 in [r JR, (r+1) JR) of the last one, whose
 // pencils it reads from the owners' shared memory (distributed shared memory).
-template <int N, int C_>
+// SECTOR: fhat in the sector order of the group (sector_index) instead of the
+// convolution's group layout.
+template <int N, int C_, bool SECTOR = false>
 __global__ void __cluster_dims__(C_, 1, 1) __launch_bounds__(FusedShape<N, C_>::NT)
 dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ slot_off, DftSeg s,
                      const float2 *__restrict__ root, float scale, float2 *__restrict__ G, int *status) {
@@ -157,9 +159,11 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
     const int r = (int)cl.block_rank(), sl = blockIdx.x / C, t = threadIdx.x;
     const int64_t off = slot_off[s.s0 + sl];
     if (off == -2) return;  // a slot of a group that holds no cell this call (nothing reads it)
-    float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes + (sl % kLanes);
+    float2 *g = G + s.eoff + (int64_t)(sl / kLanes) * M * kLanes;
+    const int ln = sl % kLanes;
+    auto gi = [ln](int e) -> int64_t { return SECTOR ? sector_index(e, ln) : (int64_t)e * kLanes + ln; };
     if (off < 0) {  // padding lane of a group (the whole cluster leaves here): zero fhat
-        for (int e = r * (M / C) + t; e < (r + 1) * (M / C); e += S::NT) g[(int64_t)e * kLanes] = make_float2(0.f, 0.f);
+        for (int e = r * (M / C) + t; e < (r + 1) * (M / C); e += S::NT) g[gi(e)] = make_float2(0.f, 0.f);
         return;
     }
     const float2(&rt)[N] = CRoot<N>::get();
@@ -197,7 +201,7 @@ dft_fwd_fused_kernel(const double *__restrict__ f, const int64_t *__restrict__ s
         pencil_cc<N, true>(x, y, rt);
         const int pk = k2 * N + k3;
 #pragma unroll
-        for (int k = 0; k < N; ++k) g[(int64_t)(k * NN + pk) * kLanes] = make_float2(scale * y[k].x, scale * y[k].y);
+        for (int k = 0; k < N; ++k) g[gi(k * NN + pk)] = make_float2(scale * y[k].x, scale * y[k].y);
     }
     if constexpr (C > 1) cluster_barrier_relaxed();  // no CTA leaves while its slab may still be read
 }
@@ -515,8 +519,15 @@ dft_inv_fused_kernel(const float2 *__restrict__ G, const int64_t *__restrict__ s
 namespace {
 template <int N, int C>
 void fwd_launch(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root, double scale,
-                float2 *G, int *status, cudaStream_t st) {
+                float2 *G, int *status, cudaStream_t st, bool sector) {
     using S = FusedShape<N, C>;
+    if constexpr (N <= 16) {
+        if (sector) {
+            dft_fwd_fused_kernel<N, C, true><<<s.nslots * C, S::NT, S::smem_fwd, st>>>(f, slot_off, s, root,
+                                                                                      (float)scale, G, status);
+            return;
+        }
+    }
     dft_fwd_fused_kernel<N, C><<<s.nslots * C, S::NT, S::smem_fwd, st>>>(f, slot_off, s, root, (float)scale, G,
                                                                         status);
 }
@@ -540,6 +551,9 @@ template <int N, int C>
 void prepare_one() {
     using S = FusedShape<N, C>;
     cudaFuncSetAttribute(dft_fwd_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_fwd);
+    if constexpr (N <= 16)
+        cudaFuncSetAttribute(dft_fwd_fused_kernel<N, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)S::smem_fwd);
     cudaFuncSetAttribute(dft_inv_fused_kernel<N, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::smem_inv);
     cudaFuncSetAttribute(dft_inv_fused_kernel<N, C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)S::smem_inv);
@@ -608,13 +622,13 @@ void launch_dft_forward_pencils(const double *f, const int64_t *slot_off, const 
 }
 
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
-                              double scale, float2 *G, int *status, cudaStream_t st, int split) {
+                              double scale, float2 *G, int *status, cudaStream_t st, int split, bool sector) {
     switch (s.N) {
-        case 8: BTE_SPLIT_DISPATCH(fwd_launch, 8, f, slot_off, s, root, scale, G, status, st) break;
-        case 12: BTE_SPLIT_DISPATCH(fwd_launch, 12, f, slot_off, s, root, scale, G, status, st) break;
-        case 16: BTE_SPLIT_DISPATCH(fwd_launch, 16, f, slot_off, s, root, scale, G, status, st) break;
-        case 24: fwd_launch<24, 4>(f, slot_off, s, root, scale, G, status, st); break;
-        case 32: fwd_launch<32, 8>(f, slot_off, s, root, scale, G, status, st); break;
+        case 8: BTE_SPLIT_DISPATCH(fwd_launch, 8, f, slot_off, s, root, scale, G, status, st, sector) break;
+        case 12: BTE_SPLIT_DISPATCH(fwd_launch, 12, f, slot_off, s, root, scale, G, status, st, sector) break;
+        case 16: BTE_SPLIT_DISPATCH(fwd_launch, 16, f, slot_off, s, root, scale, G, status, st, sector) break;
+        case 24: fwd_launch<24, 4>(f, slot_off, s, root, scale, G, status, st, false); break;
+        case 32: fwd_launch<32, 8>(f, slot_off, s, root, scale, G, status, st, false); break;
         default: break;
     }
 }

@@ -99,9 +99,20 @@ void fused_dft_prepare(int N);  // outside stream capture
 // forward transform of N <= 16 cells at the modes of npen zeta pencils kks[] (k1 N + k2) only
 void launch_dft_forward_pencils(const double *f, const int64_t *slot_off, const DftSeg &s, double scale,
                                 const int *kks, int npen, float2 *G, int *status, cudaStream_t st);
-// split: CTAs (a thread-block cluster) per cell, 1, 2 or 4 (other values: 4)
+// Sector order of a group of fhat (the fallback indicator's input, N <= 16):
+// mode e of lane l at (e / 4) 128 + 4 l + e mod 4, so that four consecutive
+// modes of one cell fill one 32-byte sector and the forward transform, which
+// holds one cell per CTA, stores whole sectors (the group layout of the
+// convolution, 32 e + l, takes one 8-byte piece of a sector per store).
+__host__ __device__ __forceinline__ int64_t sector_index(int64_t e, int lane) {
+    return ((e >> 2) << 7) + ((int64_t)lane << 2) + (e & 3);
+}
+// split: CTAs (a thread-block cluster) per cell, 1, 2 or 4 (other values: 4);
+// sector: fhat in the sector order (N <= 16) instead of the convolution's
+// group layout
 void launch_dft_forward_fused(const double *f, const int64_t *slot_off, const DftSeg &s, const float2 *root,
-                              double scale, float2 *G, int *status, cudaStream_t st, int split = 4);
+                              double scale, float2 *G, int *status, cudaStream_t st, int split = 4,
+                              bool sector = false);
 void launch_dft_inverse_fused(const float2 *G, const int64_t *slot_off, const DftSeg &s, const float2 *root,
                               double scale, double *q, const ProjArgs &pa, int mode, const double *x, double *y,
                               const double *qp, double a, cudaStream_t st, int split = 4);

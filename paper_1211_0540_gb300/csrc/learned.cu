@@ -46,7 +46,7 @@ indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, co
     const int p = blockIdx.x, g = blockIdx.y, half = blockIdx.z, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const IndPencil pen = pens[p];
     const int k1 = pen.kk / N, k2 = pen.kk % N;
-    const float2 *Fg = F + eoff + (int64_t)g * M * kLanes + lane;
+    const float2 *Fg = F + eoff + (int64_t)g * M * kLanes;  // fhat in the sector order of the group
     float acc[4 * N];  // full (re, im) per k3, then loss (re, im) per k3
 #pragma unroll
     for (int i = 0; i < 4 * N; ++i) acc[i] = 0.f;
@@ -56,9 +56,13 @@ indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, co
         const int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16), n1 = k1 - m1 + H, n2 = k2 - m2 + H;
         float2 av[N], bv[N];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            av[i] = Fg[(int64_t)((m1 * N + m2) * N + i) * kLanes];
-            bv[i] = Fg[(int64_t)((n1 * N + n2) * N + i) * kLanes];
+        for (int i = 0; i < N; i += 2) {  // two modes of the lane per 16-byte load (rows start on a sector)
+            const float4 a2 = *reinterpret_cast<const float4 *>(Fg + sector_index((m1 * N + m2) * N + i, lane));
+            const float4 b2 = *reinterpret_cast<const float4 *>(Fg + sector_index((n1 * N + n2) * N + i, lane));
+            av[i] = make_float2(a2.x, a2.y);
+            av[i + 1] = make_float2(a2.z, a2.w);
+            bv[i] = make_float2(b2.x, b2.y);
+            bv[i + 1] = make_float2(b2.z, b2.w);
         }
         const float4 *wf = reinterpret_cast<const float4 *>(Wfull + pen.wofs_full + (size_t)b * cpad);
         const float4 *wl = reinterpret_cast<const float4 *>(Wloss + pen.wofs_loss + (size_t)b * cpad);

@@ -30,7 +30,9 @@ void free_indicator_table(IndicatorTable &t);
 // Q = P_N(rho^2 Y / s_out) for B contiguous cells of N^3 values (N <= 16).
 void launch_post_project(const float *Y, const double *rho, int B, int N, float s_out, const ProjArgs &pa, double *Q,
                          cudaStream_t st);
-// ind[slot] for the slots of one segment (eoff: its offset in the group buffers);
+// ind[slot] for the slots of one segment (eoff: its offset in the group buffers;
+// F: fhat of f in the sector order of each group (sector_index), QN: fhat of
+// the projected surrogate output at the sampled pencils, group layout);
 // err2, den2: S * nslots floats of scratch each, ind: nslots floats followed by
 // the kernel's own scratch (indicator_scratch_floats counts all of it).
 size_t indicator_scratch_floats(const IndicatorTable &it, int N, int nslots);
