@@ -160,8 +160,14 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
     double *q = Q + (size_t)r * M;
     __shared__ float red[NW][10];
     __shared__ float2 base[NN], sg[N];
-    __shared__ double lam[5];
-    const double c = rho[r] * rho[r] / (double)s_out;
+    __shared__ double lam[5], c_s;
+    __shared__ float2 c_hl;
+    if (t == 0) {  // the output scale, once per cell (an FP64 division), and its double-float split
+        const double c = rho[r] * rho[r] / (double)s_out;
+        const float hi = fpc::narrow(c);
+        c_s = c;
+        c_hl = make_float2(hi, fpc::narrow(c - fpc::widen(hi)));
+    }
     Df mom[5];
     if (t < NN) {
         Df s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
@@ -198,6 +204,7 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
 #pragma unroll
         for (int i = 0; i < 5; ++i) mom[i] = df_warp_sum(mom[i]);
         double mu = 0.0;
+        const double c = c_s;
 #pragma unroll
         for (int i = 0; i < 5; ++i)
             if (lane == i) mu = ((double)mom[i].hi + (double)mom[i].lo) * c;
@@ -231,8 +238,8 @@ post_project_kernel(const float *__restrict__ Y, const double *__restrict__ rho,
         const float hi = fpc::narrow(b);
         base[t] = make_float2(hi, fpc::narrow(b - fpc::widen(hi)));
     }
-    const float c_hi = fpc::narrow(c), c_lo = fpc::narrow(c - fpc::widen(c_hi));
     __syncthreads();
+    const float c_hi = c_hl.x, c_lo = c_hl.y;
     for (int e = t; e < M; e += NT) {
         const float yv = y[e];
         const float p = c_hi * yv;

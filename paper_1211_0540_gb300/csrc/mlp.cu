@@ -53,8 +53,20 @@ __global__ void __launch_bounds__(kT) prep_kernel(const double *__restrict__ f, 
     __shared__ float red[kT / 32][2];
     __shared__ double rho_s;
     Df s{0.f, 0.f};
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        const float v = fpc::narrow(fr[j]);  // integer pipes, not the FP64 unit
+    int j = threadIdx.x;
+    for (; j + 3 * kT < M; j += 4 * kT) {  // four loads in flight per thread, summed in the same order
+        double d[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u] = fr[j + u * kT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float v = fpc::narrow(d[u]);  // integer pipes, not the FP64 unit
+            xs[j + u * kT] = v;
+            df_add(s, v);
+        }
+    }
+    for (; j < M; j += kT) {
+        const float v = fpc::narrow(fr[j]);
         xs[j] = v;
         df_add(s, v);
     }
