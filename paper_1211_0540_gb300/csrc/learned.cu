@@ -24,34 +24,70 @@ namespace bte {
 namespace {
 
 // One CTA of kIndWarps warps per (sampled pencil, group), lane = cell: the
-// warps take the pencil's kept (m1, m2) blocks in turn (the block layout of the
-// FP32 table: unordered pairs, weights Ghat(k,m) + Ghat(k,n)); each block's a
-// and b rows are loaded once into registers and serve all N outputs k3, with
-// the full and the loss weights side by side. Partial sums are added across
-// the warps in a fixed order, then compared with the transform of the
-// projected surrogate output.
+// warps work in pairs, each pair takes the pencil's kept (m1, m2) blocks in
+// turn (the block layout of the FP32 table: unordered pairs, weights
+// Ghat(k,m) + Ghat(k,n)) and each warp of a pair half of the N outputs k3,
+// with the full and the loss weights side by side: the a and b rows of a block
+// are loaded into registers by both warps of its pair. Half the outputs per
+// warp keep the kernel at two CTAs per SM. Partial sums are added across the
+// pairs in a fixed order, then compared with the transform of the projected
+// surrogate output.
 constexpr int kIndWarps = 8;
+constexpr int kIndPairs = kIndWarps / 2;
+
+// The pair sums of one block for the outputs k3 in [JH N/2, (JH + 1) N/2):
+// acc = full (re, im) per output, then loss (re, im). The weight of the pair
+// (m3, k3) sits at its rank among the block's valid pairs (m3 major, k3 minor),
+// a compile-time index after unrolling.
+template <int N, int JH>
+__device__ __forceinline__ void indicator_block(const float2 (&av)[N], const float2 (&bv)[N], const float4 *wf,
+                                                const float4 *wl, float (&acc)[2 * N]) {
+    constexpr int H = N / 2, J0 = JH * H;
+    int wi = 0;
+#pragma unroll
+    for (int m3 = 0; m3 < N; ++m3)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const int n3 = j - m3 + H;
+            if (n3 < 0 || n3 >= N) continue;
+            if (j >= J0 && j < J0 + H) {
+                const float4 f4 = wf[wi >> 2], l4 = wl[wi >> 2];
+                const int q = wi & 3;
+                const float wF = q == 0 ? f4.x : q == 1 ? f4.y : q == 2 ? f4.z : f4.w;
+                const float wL = q == 0 ? l4.x : q == 1 ? l4.y : q == 2 ? l4.z : l4.w;
+                const float pr = av[m3].x * bv[n3].x - av[m3].y * bv[n3].y;
+                const float pi = av[m3].x * bv[n3].y + av[m3].y * bv[n3].x;
+                const int o = j - J0;
+                acc[2 * o] = fmaf(wF, pr, acc[2 * o]);
+                acc[2 * o + 1] = fmaf(wF, pi, acc[2 * o + 1]);
+                acc[N + 2 * o] = fmaf(wL, pr, acc[N + 2 * o]);
+                acc[N + 2 * o + 1] = fmaf(wL, pi, acc[N + 2 * o + 1]);
+            }
+            ++wi;
+        }
+}
 
 // The pencil's blocks are split between two CTAs (blockIdx.z = half) so that
-// the S x groups items fill the GPU; each half reduces its warps in a fixed
+// the S x groups items fill the GPU; each half reduces its pairs in a fixed
 // order into part[], and the half that finishes second (an atomic count, no
 // waiting) adds half 0 and half 1 in that order and forms the errors.
 template <int N>
-__global__ void __launch_bounds__(32 * kIndWarps)
+__global__ void __launch_bounds__(32 * kIndWarps, 2)
 indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, const float *__restrict__ Wfull,
                  const float *__restrict__ Wloss, const uint32_t *__restrict__ desc, const IndPencil *__restrict__ pens,
                  int cpad, int64_t eoff, int nslots, float *err2, float *den2, float *part, unsigned *cnt) {
     constexpr int M = N * N * N, H = N / 2;
-    extern __shared__ __align__(16) float red[];  // [kIndWarps][4 N][32]
+    extern __shared__ __align__(16) float red[];  // [kIndPairs][4 N][32]
     const int p = blockIdx.x, g = blockIdx.y, half = blockIdx.z, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pair = warp >> 1, jh = warp & 1;
     const IndPencil pen = pens[p];
     const int k1 = pen.kk / N, k2 = pen.kk % N;
     const float2 *Fg = F + eoff + (int64_t)g * M * kLanes;  // fhat in the sector order of the group
-    float acc[4 * N];  // full (re, im) per k3, then loss (re, im) per k3
+    float acc[2 * N];  // this warp's outputs: full (re, im) per k3, then loss (re, im)
 #pragma unroll
-    for (int i = 0; i < 4 * N; ++i) acc[i] = 0.f;
+    for (int i = 0; i < 2 * N; ++i) acc[i] = 0.f;
     const int bmid = pen.nblocks / 2, bend = half ? pen.nblocks : bmid;
-    for (int b = (half ? bmid : 0) + warp; b < bend; b += kIndWarps) {
+    for (int b = (half ? bmid : 0) + pair; b < bend; b += kIndPairs) {
         const uint32_t d = desc[pen.desc_off + b];
         const int m1 = (int)(d & 0xffffu), m2 = (int)(d >> 16), n1 = k1 - m1 + H, n2 = k2 - m2 + H;
         float2 av[N], bv[N];
@@ -66,40 +102,25 @@ indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, co
         }
         const float4 *wf = reinterpret_cast<const float4 *>(Wfull + pen.wofs_full + (size_t)b * cpad);
         const float4 *wl = reinterpret_cast<const float4 *>(Wloss + pen.wofs_loss + (size_t)b * cpad);
-        float4 f4 = make_float4(0.f, 0.f, 0.f, 0.f), l4 = f4;
-        int wi = 0;
-#pragma unroll
-        for (int m3 = 0; m3 < N; ++m3)
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-                const int n3 = j - m3 + H;
-                if (n3 >= 0 && n3 < N) {
-                    if ((wi & 3) == 0) {
-                        f4 = wf[wi >> 2];
-                        l4 = wl[wi >> 2];
-                    }
-                    const int q = wi & 3;
-                    const float wF = q == 0 ? f4.x : q == 1 ? f4.y : q == 2 ? f4.z : f4.w;
-                    const float wL = q == 0 ? l4.x : q == 1 ? l4.y : q == 2 ? l4.z : l4.w;
-                    ++wi;
-                    const float pr = av[m3].x * bv[n3].x - av[m3].y * bv[n3].y;
-                    const float pi = av[m3].x * bv[n3].y + av[m3].y * bv[n3].x;
-                    acc[2 * j] = fmaf(wF, pr, acc[2 * j]);
-                    acc[2 * j + 1] = fmaf(wF, pi, acc[2 * j + 1]);
-                    acc[2 * N + 2 * j] = fmaf(wL, pr, acc[2 * N + 2 * j]);
-                    acc[2 * N + 2 * j + 1] = fmaf(wL, pi, acc[2 * N + 2 * j + 1]);
-                }
-            }
+        if (jh == 0) indicator_block<N, 0>(av, bv, wf, wl, acc);
+        else indicator_block<N, 1>(av, bv, wf, wl, acc);
     }
+    // the pair's 4 N sums: full (re, im) of output k3 at 2 k3, loss at 2 N + 2 k3
 #pragma unroll
-    for (int i = 0; i < 4 * N; ++i) red[(warp * 4 * N + i) * kLanes + lane] = acc[i];
+    for (int o = 0; o < H; ++o) {
+        const int k3 = jh * H + o;
+        red[(pair * 4 * N + 2 * k3) * kLanes + lane] = acc[2 * o];
+        red[(pair * 4 * N + 2 * k3 + 1) * kLanes + lane] = acc[2 * o + 1];
+        red[(pair * 4 * N + 2 * N + 2 * k3) * kLanes + lane] = acc[N + 2 * o];
+        red[(pair * 4 * N + 2 * N + 2 * k3 + 1) * kLanes + lane] = acc[N + 2 * o + 1];
+    }
     __syncthreads();
     if (warp != 0) return;
     const size_t item = (size_t)p * gridDim.y + g;
     float *mine = part + (item * 2 + half) * (4 * N * kLanes) + lane;
     for (int i = 0; i < 4 * N; ++i) {
         float v = 0.f;
-        for (int w = 0; w < kIndWarps; ++w) v += red[((size_t)w * 4 * N + i) * kLanes + lane];
+        for (int w = 0; w < kIndPairs; ++w) v += red[((size_t)w * 4 * N + i) * kLanes + lane];
         mine[i * kLanes] = v;
     }
     __threadfence();  // this half's sums before the count
@@ -129,7 +150,7 @@ indicator_kernel(const float2 *__restrict__ F, const float2 *__restrict__ QN, co
 
 template <int N>
 constexpr size_t ind_smem() {
-    return sizeof(float) * kIndWarps * 4 * N * kLanes;
+    return sizeof(float) * kIndPairs * 4 * N * kLanes;
 }
 
 __global__ void indicator_reduce_kernel(const float *__restrict__ err2, const float *__restrict__ den2, int S,
