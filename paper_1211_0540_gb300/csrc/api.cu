@@ -852,8 +852,11 @@ bte_status enqueue_indicator(bte_ctx *c, Batch *B, const double *f, const double
         return s;
     DftSeg ds{t->N, sg.s0, sg.nslots, sg.eoff};
     const double sf = std::pow(2.0 * kPi, -1.5) * t->dv * t->dv * t->dv;
+    // sector order; one CTA per cell once the cells fill the SMs (the fastest for
+    // this transform alone), else the batch's tuned split
+    const int split = B->nslots >= c->num_sms ? 1 : cfg_of(c, B).split;
     launch_dft_forward_fused(f, B->d_slot_off, ds, t->d_root32, sf, (float2 *)c->scratch[SC_F], c->d_status, st,
-                             cfg_of(c, B).split, true);  // the batch's tuned split, else the option; sector order
+                             split, true);
     launch_dft_forward_pencils(Q, B->d_slot_off, ds, sf, c->ind->d_kk, c->ind->S, (float2 *)c->scratch[SC_QH],
                                c->d_status, st);  // only the sampled pencils are compared
     float *e2 = (float *)c->scratch[SC_MISC];
