@@ -60,7 +60,7 @@ def test_indicator_sample_is_the_published_generator(bte, N):
 
 
 @pytest.mark.parametrize("N,ncells,lam,split", [(8, 40, 1.0, 4), (16, 37, 1.0, 4), (16, 33, 0.0, 4), (12, 35, 1.0, 1),
-                                                (16, 38, 1.0, 1), (8, 41, -1.0, 2)])
+                                                (16, 38, 1.0, 1), (8, 41, -1.0, 2), (16, 160, 1.0, 4)])
 def test_indicator_matches_oracle(bte, N, ncells, lam, split):
     f = inputs.homogeneous_cells(N, L, ncells, seed=600 + N + ncells)
     rng = np.random.default_rng(601 + N)
@@ -72,7 +72,9 @@ def test_indicator_matches_oracle(bte, N, ncells, lam, split):
     Q[3::4] = 0.0
     c = bte.Context(0)
     c.init_weights([(N, L, lam)])
-    c.set_option("dft_split", split)  # the indicator's transform of f runs in the batch's configuration
+    # the indicator's transform of f runs in the batch's configuration, or with one
+    # CTA per cell once the cells fill the SMs (160 cells)
+    c.set_option("dft_split", split)
     ind = c.learned_indicator(torch.from_numpy(f).cuda(), torch.from_numpy(np.ascontiguousarray(Q)).cuda())
     c.sync_status()
     got = ind.cpu().numpy()
