@@ -580,14 +580,15 @@ def run_homog1(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler):
 def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler, n=32):
     """256 bi-Maxwellian cells at N = 32 (means ~ U(-1.5, 1.5)^3), FP32 operator;
     oracle on 16 seeded cells; plain FP64 operator timed once. With n = 48 (the
-    sweep-n48 workload): 64 cells, weights on the fly (the stored table would
-    be 10 GB), oracle on 2 cells, no FP64 comparator (its table: 41 GB)."""
+    sweep-n48 workload): 64 cells, the stored FP32 table (10 GB, built on first
+    use in a few seconds; --conv-impl 5 builds the weights on the fly instead),
+    oracle on 2 cells, no FP64 comparator (its table: 41 GB)."""
     lam, nc = 1.0, args.cells if n == 32 else min(args.cells, 64)
     ctx.init_weights([(n, L, lam)])
     if n > 32:
-        ctx.set_option("conv_impl", 5)
+        ctx.set_option("conv_impl", 4 if args.conv_impl is None else args.conv_impl)
         if args.conv_warps is None:
-            ctx.set_option("conv_warps", 3)  # 2 CTAs per SM with the 27 KB stages of N = 48 (measured best of 2-4)
+            ctx.set_option("conv_warps", 3)  # 2 CTAs per SM with the 27 KB stages of N = 48 (measured best of 3-4)
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
     Q = torch.empty_like(f)
@@ -637,7 +638,8 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler, n
     achieved = 10.0 * pairs * nc / (conv_ms * 1e-3) / 1e12
     wl = ("precision sweep: %d bi-Maxwellian cells (means ~ U(-1.5,1.5)^3, T ~ U(0.5,2), seed 3), "
           "N=%d, L=6, hard spheres; one projected collision evaluation of all cells per step%s"
-          % (nc, n, "; weights built on the fly (conv_impl 5)" if n > 32 or args.conv_impl == 5 else ""))
+          % (nc, n, "; weights built on the fly (conv_impl 5)" if args.conv_impl == 5 else
+             ("; stored FP32 weight table (10 GB)" if n > 32 else "")))
     return _line(args, "cell-collision evals/s at N=%d (FP32 operator)" % n, value, UNIT, tot / args.steps, wl, {
         "roofline": {"bound": "alu", "kernel": "conv32 (FP32 weighted convolution)", "achieved": achieved,
                      "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

@@ -9,9 +9,9 @@
  * - Velocity grid (Sec. 3.1, Eq. meshpoints): N points per dimension on [-L, L)^3,
  *   v_j = dv (j - N/2), dv = 2L/N; Fourier grid zeta_k = dz (k - N/2), dz = pi/L.
  *   N must be even; the library supports N in {8, 12, 16, 24, 32, 48}. At N = 48
- *   the FP32 weights are best built on the fly (option conv_impl 5): the stored
- *   table (10 GB) is built only when a variant that streams it runs, and the
- *   plain FP64 operator and the transport step take N <= 32.
+ *   the stored FP32 weight table (10 GB) is built on first use by a variant that
+ *   streams it (option conv_impl 5 builds the weights on the fly instead, with
+ *   no table), and the plain FP64 operator and the transport step take N <= 32.
  * - A "cell" is one distribution f on that grid: M = N^3 doubles, index
  *   (j1*N + j2)*N + j3 (j3 fastest). Arrays of cells are cell-major.
  * - f and Q pointers are DEVICE pointers (cudaMalloc / torch tensors) owned by
