@@ -581,18 +581,17 @@ def run_sweep32(args, ctx, torch, bte, inputs, oracle, stream, flush, sampler, n
     """256 bi-Maxwellian cells at N = 32 (means ~ U(-1.5, 1.5)^3), FP32 operator;
     oracle on 16 seeded cells; plain FP64 operator timed once. With n = 48 (the
     sweep-n48 workload): 64 cells, the stored FP32 table (10 GB, built on first
-    use in a few seconds; --conv-impl 5 builds the weights on the fly instead),
-    oracle on 2 cells, no FP64 comparator (its table: 41 GB)."""
+    use in a few seconds) with the autotuned variant (--conv-impl 5 builds the
+    weights on the fly instead), oracle on 2 cells, no FP64 comparator (its
+    table: 41 GB)."""
     lam, nc = 1.0, args.cells if n == 32 else min(args.cells, 64)
     ctx.init_weights([(n, L, lam)])
-    if n > 32:
-        ctx.set_option("conv_impl", 4 if args.conv_impl is None else args.conv_impl)
-        if args.conv_warps is None:
-            ctx.set_option("conv_warps", 3)  # 2 CTAs per SM with the 27 KB stages of N = 48 (measured best of 3-4)
+    if n > 32 and args.conv_impl is not None:
+        ctx.set_option("conv_impl", args.conv_impl)
     fn = inputs.precision_sweep_cells(n, L, nc, seed=3)
     f = torch.from_numpy(fn).cuda().reshape(-1)
     Q = torch.empty_like(f)
-    explicit = args.conv_impl is not None or args.conv_warps is not None or n > 32
+    explicit = args.conv_impl is not None or args.conv_warps is not None
     tuned = None if explicit else tune(args, ctx, f, stream, reps=2)
     ctx.profile_enable(True)
     with torch.cuda.stream(stream):

@@ -282,7 +282,9 @@ bte_status bte_graph_count(const bte_ctx *ctx, int64_t *count);
  *                      pair-symmetrised weights from the radial integrals
  *                      I(|k'|^2, |2m' - k'|^2) and J(|m'|^2) (FP32 tables of
  *                      0.5 MB at N = 16, 9 MB at N = 32) instead of streaming
- *                      the stored weight table (elastic tables only);
+ *                      the stored weight table (elastic tables only). Kinds of
+ *                      N = 48 run on 4 and 5, and on 3 when they are the
+ *                      batch's only kinds (its four warps per CTA fit there);
  *       "conv_warps"  warps per CTA (1..8 for impl 0, 1..4 otherwise);
  *       "conv_stages" blocks in flight per warp (1..4; 0 = automatic, the
  *                      default: the deepest ring up to 2 that keeps the

@@ -1520,6 +1520,9 @@ bte_status bte_autotune(bte_ctx *c, const double *f, const bte_instance *inst, i
                         for (int csplit : {1, 0}) {
                         if (!small_n && split != 4) continue;
                         if (csplit && (impl != 4 || B->nsplit == 0)) continue;
+                        // kinds of N = 48: variant 4, and 3 when they are the only kinds
+                        if ((B->kinds_mask >> 7) && impl != 4 && !(impl == 3 && B->kinds_mask == (128u | 256u | 512u)))
+                            continue;
                         ConvCfg g;
                         g.impl = impl;
                         g.warps = warps;

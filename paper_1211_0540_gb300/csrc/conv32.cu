@@ -10,6 +10,7 @@ namespace bte {
 
 // conv32_wide.cu: the variant-4/5 kernels whose kind sets include N = 48
 void (*conv32_sums_wide(unsigned mask, bool otf))(ConvParams);
+void (*conv32_coop_wide())(ConvParams);  // variant 3, N = 48 alone
 
 int conv_stage_bytes(int kind) {
     switch (kind) {
@@ -87,14 +88,19 @@ cudaError_t conv32_configure(unsigned kinds_mask, int num_sms, int warps_per_cta
            : impl == 3 ? conv32_coop_kernel<M, true, 2>                                        \
                        : (packed ? conv32_coop_kernel<M, true> : conv32_coop_kernel<M, false>)
 #define BTE_PICK4(M) L.fn = conv32_sums_wide(M, impl == 5)
-        if (impl < 4 && (kinds_mask >> 7)) return cudaErrorInvalidValue;  // N = 48: variants 4 and 5 only
+        // N = 48: variants 4 and 5, and 3 for the N = 48 kinds alone
+        if (impl < 4 && (kinds_mask >> 7) && !(impl == 3 && kinds_mask == (128u | 256u | 512u)))
+            return cudaErrorInvalidValue;
         switch (kinds_mask) {
             case 1u: BTE_PICK(1u); break;
             case 2u: BTE_PICK(2u); break;
             case 4u: BTE_PICK(4u); break;
             case 8u | 16u: BTE_PICK(24u); break;
             case 32u | 64u: BTE_PICK(96u); break;
-            case 128u | 256u | 512u: BTE_PICK4(896u); break;
+            case 128u | 256u | 512u:
+                if (impl == 3) L.fn = conv32_coop_wide();
+                else BTE_PICK4(896u);
+                break;
             default:
                 if (kinds_mask >> 7) BTE_PICK4(1023u);
                 else BTE_PICK(127u);
