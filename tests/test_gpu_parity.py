@@ -997,7 +997,7 @@ def test_weights_on_the_fly_match_oracle(bte, N, ncells, nsample, lam):
 def test_weights_on_the_fly_at_n48_match_oracle(bte):
     """N = 48 (three k3 tiles of 16), the weights built on the fly (no stored
     table) and then streamed from the stored FP32 table (10 GB, built on first
-    use) by variants 4 and 3: 33 cells (a ragged second group), the oracle on the first and the last
+    use) by variants 4 and 3, and the autotuner's choice among them: 33 cells (a ragged second group), the oracle on the first and the last
     cell; the plain FP64 operator and the transport step refuse N = 48 with
     BTE_EINVAL."""
     N, lam, ncells = 48, 1.0, 33
@@ -1006,8 +1006,12 @@ def test_weights_on_the_fly_at_n48_match_oracle(bte):
     c.init_weights([(N, L, lam)])
     pick = [0, ncells - 1]
     Qo = oracle.collide(N, L, lam, f[pick])
-    for impl in (5, 4, 3):
-        c.set_option("conv_impl", impl)
+    for impl in (5, 4, 3, None):
+        if impl is None:  # the autotuner's choice among the variants built for N = 48
+            cfg = c.autotune(torch.from_numpy(f).cuda(), reps=1)
+            assert cfg["conv_impl"] in (3, 4), cfg
+        else:
+            c.set_option("conv_impl", impl)
         Qg = c.collide(torch.from_numpy(f).cuda(), mode=bte.FP32).cpu().numpy()
         c.sync_status()
         err = np.linalg.norm(Qg[pick] - Qo, axis=1) / loss_norm(N, lam, f[pick])
