@@ -90,8 +90,9 @@ __device__ __forceinline__ float gelu_f(float x) {
 
 // STAGES: depth of the TMA ring. With one CTA per SM the ring is what keeps
 // the copies in flight against the L2 latency, so a grid that fits in one
-// wave takes the deepest ring that fits (192 KB).
-template <int BN, int STAGES>
+// wave takes the deepest ring that fits (192 KB). KB: 64-wide K boxes per
+// stage and operand (a k-step of KB * 64).
+template <int BN, int STAGES, int KB = 1>
 __global__ void __launch_bounds__(128, 1)
 gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmEpi g,
                     int M, int N, int K, int *status) {
@@ -101,13 +102,14 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     __shared__ int abort_flag, n_issued, n_consumed;
     // 1024-byte alignment for the 128-byte swizzle atoms
     uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    // a stage holds KB boxes of 64 K values for each operand (one k-step: KB * 64)
+    constexpr int A_BOX = BM * BK * 2, B_BOX = BN * BK * 2, A_BYTES = KB * A_BOX, B_BYTES = KB * B_BOX;
     uint8_t *sA = base;
     uint8_t *sB = base + STAGES * A_BYTES;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tile_n = blockIdx.x * BN, tile_m = blockIdx.y * BM;
-    const int nk = K / BK;
+    const int nk = K / (BK * KB);
 
     if (threadIdx.x == 0) {
         abort_flag = 0;
@@ -142,16 +144,20 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                          "r"((uint32_t)(A_BYTES + B_BYTES))
                          : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-                    "r"(su32(sA + s * A_BYTES)),
-                "l"((uint64_t)&tmA), "r"(kt * BK), "r"(tile_m), "r"(fb)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-                    "r"(su32(sB + s * B_BYTES)),
-                "l"((uint64_t)&tmB), "r"(kt * BK), "r"(tile_n), "r"(fb)
-                : "memory");
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb) {
+                const int kc = (kt * KB + kb) * BK;
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+                        "r"(su32(sA + s * A_BYTES + kb * A_BOX)),
+                    "l"((uint64_t)&tmA), "r"(kc), "r"(tile_m), "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+                        "r"(su32(sB + s * B_BYTES + kb * B_BOX)),
+                    "l"((uint64_t)&tmB), "r"(kc), "r"(tile_n), "r"(fb)
+                    : "memory");
+            }
             n_issued = kt + 1;
         }
     } else if (threadIdx.x == 32) {
@@ -164,10 +170,11 @@ gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(a0 + kk * 32);
-                const uint64_t bd = smem_desc_sw128(b0 + kk * 32);
-                const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+            for (int kq = 0; kq < KB * (BK / 16); ++kq) {
+                const int kb = kq / (BK / 16), kk = kq % (BK / 16);
+                const uint64_t ad = smem_desc_sw128(a0 + kb * A_BOX + kk * 32);
+                const uint64_t bd = smem_desc_sw128(b0 + kb * B_BOX + kk * 32);
+                const uint32_t acc = (kt > 0 || kq > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
@@ -282,15 +289,15 @@ bool make_map(CUtensorMap *m, const void *ptr, int rows, int cols, int box_rows)
     return r == CUDA_SUCCESS;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int KB = 1>
 size_t smem_bytes() {
-    return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024;
+    return (size_t)STAGES * KB * (BM * BK * 2 + BN * BK * 2) + 1024;
 }
 
-template <int BN, int STAGES>
+template <int BN, int STAGES, int KB = 1>
 cudaError_t set_smem() {
-    return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_bytes<BN, STAGES>());
+    return cudaFuncSetAttribute(gemm_bf16_tc_kernel<BN, STAGES, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_bytes<BN, STAGES, KB>());
 }
 
 int sm_count() {
@@ -312,6 +319,7 @@ cudaError_t gemm_bf16_prepare() {
     if (e == cudaSuccess) e = set_smem<128, 6>();
     if (e == cudaSuccess) e = set_smem<64, 4>();
     if (e == cudaSuccess) e = set_smem<64, 8>();
+    if (e == cudaSuccess) e = set_smem<64, 4, 2>();
     sm_count();
     return e;
 }
@@ -338,7 +346,11 @@ int gemm_bf16(const void *A, const void *B, int M, int N, int K, const GemmEpi &
         if (deep) gemm_bf16_tc_kernel<128, 6><<<grid, 128, smem_bytes<128, 6>(), st>>>(ma, mb, g, M, N, K, status);
         else gemm_bf16_tc_kernel<128, 4><<<grid, 128, smem_bytes<128, 4>(), st>>>(ma, mb, g, M, N, K, status);
     } else {
-        if (deep) gemm_bf16_tc_kernel<64, 8><<<grid, 128, smem_bytes<64, 8>(), st>>>(ma, mb, g, M, N, K, status);
+        // long K: stages of two 64-wide K boxes (4 of them), half the k-steps (each
+        // step's round trip through the ring costs more than its bytes there)
+        if (deep && K % (2 * BK) == 0 && K / BK >= 32)
+            gemm_bf16_tc_kernel<64, 4, 2><<<grid, 128, smem_bytes<64, 4, 2>(), st>>>(ma, mb, g, M, N, K, status);
+        else if (deep) gemm_bf16_tc_kernel<64, 8><<<grid, 128, smem_bytes<64, 8>(), st>>>(ma, mb, g, M, N, K, status);
         else gemm_bf16_tc_kernel<64, 4><<<grid, 128, smem_bytes<64, 4>(), st>>>(ma, mb, g, M, N, K, status);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
