@@ -264,6 +264,55 @@ def test_uneven_batch_with_all_grid_sizes_matches_oracle(bte):
     assert np.all(Qg[mask] == 3.0)
 
 
+def test_uneven_batch_with_n48_matches_oracle(bte):
+    """One launch over instances of N = 16 and N = 48 (the kernels built over every
+    kind, the three k3 tiles of N = 48 beside the single tile of N = 16), with the
+    stored weight tables (variant 4) and with the weights built on the fly
+    (variant 5); oracle on every N = 16 instance and on one N = 48 instance."""
+    grids = ((16, L, 1.0), (48, L, 1.0))
+    c = bte.Context(0)  # its own context: the 10 GB table of N = 48 goes with it
+    c.init_weights(list(grids))
+    kinds = [0, 1, 0, 0, 1, 0]
+    rng = np.random.default_rng(48)
+    inst, chunks = [], []
+    off = 0
+    for i, t in enumerate(kinds):
+        N = grids[t][0]
+        f = inputs.precision_sweep_cells(N, L, 1, seed=1200 + i)[0]
+        off += int(rng.integers(0, 3)) * 16
+        inst.append((t, off))
+        chunks.append((off, f))
+        off += N ** 3
+    buf = np.zeros(off)
+    for o, f in chunks:
+        buf[o:o + f.size] = f
+    fb = torch.from_numpy(buf).cuda()
+    ref = {}
+    for t in range(2):
+        N, _, lam = grids[t]
+        idx = [k for k in range(len(inst)) if kinds[k] == t][: (None if N <= 16 else 1)]
+        f = np.stack([chunks[k][1] for k in idx])
+        ref[t] = (idx, f, oracle.collide(N, L, lam, f))
+    for impl in (4, 5):
+        c.set_option("conv_impl", impl)
+        Qt = torch.full_like(fb, 3.0)
+        c.collide(fb, Qt, inst=inst, mode=bte.FP32)
+        c.sync_status()
+        Qg = Qt.cpu().numpy()
+        for t in range(2):
+            N, _, lam = grids[t]
+            idx, f, Qo = ref[t]
+            got = np.stack([Qg[inst[k][1]:inst[k][1] + N ** 3] for k in idx])
+            err = np.linalg.norm(got - Qo, axis=1) / loss_norm(N, lam, f)
+            assert err.max() <= TOL32, (impl, N, err.max())
+            assert np.all(np.abs(oracle.moments(N, L, got)) <= 1e-12 * abs_moment_scale(N, got))
+        mask = np.ones(off, bool)
+        for o, f in chunks:
+            mask[o:o + f.size] = False
+        assert np.all(Qg[mask] == 3.0)
+    c.close()
+
+
 def test_batch_cache_evicts_least_recently_used(bte):
     """At most "batch_cache" instance layouts are kept; a layout beyond that
     evicts the least recently used one, and an evicted layout used again is
